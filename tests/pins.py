@@ -1,0 +1,233 @@
+"""Pins of the oracle against facts that do not come from the oracle itself.
+
+Each check returns normally when it holds and raises AssertionError when it
+does not. They are collected by ``test_oracle_pins.py`` and re-run against
+deliberately broken copies of the oracle by ``test_oracle_mutants.py``, which
+shows that a plausible slip in the oracle trips at least one of them.
+
+The independent references used here:
+  * brute force with a different formula: Pearson correlation from
+    ``numpy.corrcoef`` and d = sqrt(2 m (1 - rho)), with the argmin taken by a
+    stable sort (equivalent to the z-normalised Euclidean distance for
+    non-constant windows, population std);
+  * closed forms (affine images, sine vs cosine over a full period, constant
+    windows);
+  * invariants (range [0, 2 sqrt(m)], affine invariance, planted copies, the
+    segment-boundary rule of Def. 8, the per-segment decomposition of
+    Algorithm 2);
+  * the paper's guarantees for a dictionary cut from T_B: Lemma 1
+    (P_hat >= P) and Lemma 2 (P_hat - P <= e_max, e_max by its definition in
+    Sec. 3.3).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+import synthetic
+
+TOL = 1e-9
+
+
+def _valid_windows(offsets, m):
+    gs = []
+    for s in range(len(offsets) - 1):
+        for o in range(0, int(offsets[s + 1] - offsets[s]) - m + 1):
+            gs.append(int(offsets[s]) + o)
+    return np.array(gs, dtype=np.int64)
+
+
+def brute_force(query, dict_samples, offsets, m):
+    """Independent all-pairs join via numpy.corrcoef (non-constant windows only)."""
+    q = np.asarray(query, dtype=np.float64)
+    b = np.asarray(dict_samples, dtype=np.float64)
+    gs = _valid_windows(offsets, m)
+    nq = len(q) - m + 1
+    D = np.empty((nq, len(gs)))
+    for r in range(nq):
+        for c, g in enumerate(gs):
+            rho = np.corrcoef(q[r : r + m], b[g : g + m])[0, 1]
+            D[r, c] = math.sqrt(max(0.0, 2 * m * (1 - rho)))
+    order = np.argsort(D, axis=1, kind="stable")  # stable: lowest g among equals
+    best = D[np.arange(nq), order[:, 0]]
+    second = D[np.arange(nq), order[:, 1]] if len(gs) > 1 else np.full(nq, np.inf)
+    return best, gs[order[:, 0]], second
+
+
+def pin_brute_force(lib, seeds=range(6)):
+    for seed in seeds:
+        rng = np.random.default_rng(1000 + seed)
+        m = int(rng.choice([3, 4, 8]))
+        na = int(rng.integers(m, 48))
+        nseg = int(rng.integers(1, 4))
+        lens = rng.integers(max(1, m - 2), 20, nseg)
+        offs = np.concatenate(([0], np.cumsum(lens))).astype(np.int64)
+        q = rng.standard_normal(na)
+        b = rng.standard_normal(int(offs[-1]))
+        d, i, d2 = oracle.ab_join(q, b, offs, m, lib=lib)
+        if len(_valid_windows(offs, m)) == 0:
+            assert np.all(np.isinf(d)) and np.all(i == -1)
+            continue
+        bd, bi, bd2 = brute_force(q, b, offs, m)
+        np.testing.assert_allclose(d, bd, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(d2, bd2, rtol=0, atol=1e-9)
+        uniq = (bd2 - bd) > 1e-9
+        assert np.array_equal(i[uniq], bi[uniq])
+
+
+def pin_closed_forms(lib):
+    m = 32
+    t = np.arange(m)
+    x = np.sin(2 * np.pi * t / m) + 0.3 * np.cos(6 * np.pi * t / m) + 0.01 * t
+    # affine image with positive scale: the same z-normalised shape
+    assert oracle.pair_distance(x, 3.5 * x - 7.0, lib=lib) < 1e-6
+    # negative scale: z(y) = -z(x), so d = |2 z(x)| = 2 sqrt(m)
+    assert abs(oracle.pair_distance(x, -0.5 * x + 1.0, lib=lib) - 2 * math.sqrt(m)) < 1e-9
+    # sine and cosine over one full period are orthogonal: rho = 0, d = sqrt(2m)
+    s = np.sin(2 * np.pi * t / m)
+    c = np.cos(2 * np.pi * t / m)
+    assert abs(oracle.pair_distance(s, c, lib=lib) - math.sqrt(2 * m)) < 1e-9
+    # constant windows: zero z-vector
+    k = np.full(m, 4.25)
+    assert abs(oracle.pair_distance(k, x, lib=lib) - math.sqrt(m)) < 1e-12
+    assert abs(oracle.pair_distance(x, k, lib=lib) - math.sqrt(m)) < 1e-12
+    assert oracle.pair_distance(k, np.full(m, -1.0), lib=lib) == 0.0
+    # a window of equal values whose float mean is not exactly that value is
+    # still constant
+    assert oracle.pair_distance(np.full(m, 0.1), np.full(m, 0.7), lib=lib) == 0.0
+    # m = 2: two non-constant windows are either the same (+) or opposite (-) shape
+    assert oracle.pair_distance([0.0, 1.0], [5.0, 9.0], lib=lib) < 1e-12
+    assert abs(oracle.pair_distance([0.0, 1.0], [9.0, 5.0], lib=lib) - 2 * math.sqrt(2)) < 1e-12
+    # a hand-computed value: x = [0, 0, 3], y = [0, 3, 0]; z(x) = [-1, -1, 2]/sqrt(2),
+    # z(y) = [-1, 2, -1]/sqrt(2); difference [0, -3, 3]/sqrt(2); squared norm 9
+    assert abs(oracle.pair_distance([0.0, 0.0, 3.0], [0.0, 3.0, 0.0], lib=lib) - 3.0) < 1e-12
+
+
+def pin_stats(lib):
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(200) * 3 + 100
+    m = 17
+    mu, sd, cst = oracle.window_stats(x, m, lib=lib)
+    from numpy.lib.stride_tricks import sliding_window_view
+
+    W = sliding_window_view(x, m)
+    np.testing.assert_allclose(mu, W.mean(axis=1), rtol=1e-13)
+    np.testing.assert_allclose(sd, W.std(axis=1, ddof=0), rtol=1e-10)
+    assert not cst.any()
+    y = np.concatenate([np.full(20, 2.0), rng.standard_normal(10)])
+    _, _, cst = oracle.window_stats(y, 8, lib=lib)
+    assert cst[:13].all() and not cst[13:].any()
+
+
+def pin_invariants(lib):
+    w = synthetic.workload("rw_fp64_4k", scale=0.125)
+    q, b, offs, m = w.query, w.dict_samples, w.offsets, 32
+    d, i, d2 = oracle.ab_join(q, b, offs, m, lib=lib)
+    # range
+    assert np.all(d >= 0) and np.all(d <= 2 * math.sqrt(m) + 1e-12)
+    uniq = (d2 - d) > 1e-7
+    # affine invariance of the query
+    da, ia, _ = oracle.ab_join(2.5 * q + 40.0, b, offs, m, lib=lib)
+    np.testing.assert_allclose(da, d, atol=1e-7)
+    assert np.array_equal(ia[uniq], i[uniq])
+    # per-segment affine maps of the dictionary
+    b2 = b.copy()
+    for s in range(len(offs) - 1):
+        b2[offs[s] : offs[s + 1]] = (0.5 + s) * b2[offs[s] : offs[s + 1]] - 3.0 * s
+    db, ib, _ = oracle.ab_join(q, b2, offs, m, lib=lib)
+    np.testing.assert_allclose(db, d, atol=1e-7)
+    assert np.array_equal(ib[uniq], i[uniq])
+    # Algorithm 2: per-segment joins merged by an element-wise minimum
+    best = np.full(len(d), np.inf)
+    arg = np.full(len(d), -1, dtype=np.int64)
+    for s in range(len(offs) - 1):
+        seg = b[offs[s] : offs[s + 1]]
+        if len(seg) < m:
+            continue
+        ds, is_, _ = oracle.ab_join(q, seg, np.array([0, len(seg)]), m, lib=lib)
+        better = ds < best
+        best = np.where(better, ds, best)
+        arg = np.where(better, is_ + offs[s], arg)
+    np.testing.assert_array_equal(best, d)
+    np.testing.assert_array_equal(arg, i)
+
+
+def pin_planted_and_boundary(lib):
+    rng = np.random.default_rng(11)
+    m = 24
+    b = rng.standard_normal(3 * 100).cumsum()
+    offs = np.array([0, 100, 200, 300], dtype=np.int64)
+    q = rng.standard_normal(400).cumsum()
+    # exact copy of dictionary window (segment 1, offset 37) planted at row 150
+    g = int(offs[1]) + 37
+    q[150 : 150 + m] = b[g : g + m]
+    # a window straddling the junction between segments 1 and 2 planted at row 300
+    j = int(offs[2]) - m // 2
+    q[300 : 300 + m] = b[j : j + m]
+    d, i, d2 = oracle.ab_join(q, b, offs, m, lib=lib)
+    assert d[150] <= 1e-6 and i[150] == g
+    # the straddling window is not a dictionary window (Def. 8), so it is not found...
+    assert d[300] > 0.05 and i[300] != j
+    # ...but it is found once the two segments are one element
+    d1, i1, _ = oracle.ab_join(q, b, np.array([0, 100, 300], dtype=np.int64), m, lib=lib)
+    assert d1[300] <= 1e-6 and i1[300] == j
+    # a single segment equal to T_B is the exact AB join; index is a window of T_B
+    dx, ix, _ = oracle.ab_join(q, b, np.array([0, len(b)]), m, lib=lib)
+    assert np.all(dx <= d + 1e-12)
+
+
+def pin_lemmas(lib):
+    """Lemma 1 and Lemma 2 for a dictionary cut from T_B (Proposition 1 holds)."""
+    for name, m in (("ecg", 64), ("rw", 32)):
+        if name == "ecg":
+            tb = synthetic.ecg_like(6000, 21)
+            ta = synthetic.ecg_like(1500, 22, n_malformed=3)
+        else:
+            tb = synthetic.random_walk(6000, 23)
+            ta = synthetic.random_walk(1500, 24)
+        db, offs = synthetic.cut_dictionary(tb, 12, 200)
+        P, _, _ = oracle.ab_join(ta, tb, np.array([0, len(tb)]), m, lib=lib)
+        Ph, _, _ = oracle.ab_join(ta, db, offs, m, lib=lib)
+        # e_max = max over windows of T_B of NNDist(window, D_{B,m})
+        e, _, _ = oracle.ab_join(tb, db, offs, m, lib=lib)
+        e_max = e.max()
+        assert np.all(Ph >= P - 1e-9), "Lemma 1 (no false negatives) violated"
+        assert np.all(Ph - P <= e_max + 1e-9), "Lemma 2 (max error) violated"
+        assert e_max > 0 and (Ph - P).max() > 0  # the dictionary really is lossy here
+
+
+def pin_empty(lib):
+    q = np.arange(10.0)
+    d, i, d2 = oracle.ab_join(q, np.arange(9.0), np.array([0, 3, 6, 9]), 4, lib=lib)
+    assert np.all(np.isinf(d)) and np.all(i == -1) and np.all(np.isinf(d2))
+    # one window only: the second-best is +inf
+    d, i, d2 = oracle.ab_join(q, np.arange(9.0) ** 2, np.array([0, 4]), 4, lib=lib)
+    assert np.all(i == 0) and np.all(np.isinf(d2))
+
+
+def pin_constant_rows(lib):
+    m = 8
+    b = np.concatenate([np.arange(20.0) ** 1.5, np.full(12, 3.0), np.sin(np.arange(20.0))])
+    offs = np.array([0, 20, 32, 52], dtype=np.int64)
+    q = np.concatenate([np.full(10, -2.0), np.cos(np.arange(30.0))])
+    d, i, _ = oracle.ab_join(q, b, offs, m, lib=lib)
+    # row 0..2 are constant query windows: nearest is the first constant dictionary window
+    assert np.all(d[:3] == 0.0) and np.all(i[:3] == 20)
+    # without constant dictionary windows, a constant query window is sqrt(m) from everything,
+    # and the lowest index wins the tie
+    d, i, _ = oracle.ab_join(q, b[:20], np.array([0, 20]), m, lib=lib)
+    assert np.allclose(d[:3], math.sqrt(m), atol=1e-12) and np.all(i[:3] == 0)
+
+
+ALL_PINS = (
+    pin_brute_force,
+    pin_closed_forms,
+    pin_stats,
+    pin_invariants,
+    pin_planted_and_boundary,
+    pin_lemmas,
+    pin_empty,
+    pin_constant_rows,
+)
