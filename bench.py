@@ -1,0 +1,402 @@
+"""Benchmark of the dictionary AB-join on GB300.
+
+Headline workload: ECG-like query of 2^20 samples (seed 2, 20 malformed beats)
+against a dictionary of 64 segments x 1024 samples (seed 3), m = 256, float32
+samples with FP64 window statistics. A step is one whole join (window
+statistics, join kernel, finalisation with the exact distance of each pick).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--kernel plain|bf16x3|tf32|auto] [--serving-requests R]
+
+Prints one JSON line (rank 0). With N > 1 (launched by torchrun) every rank
+joins its own query of the same size (weak scaling, no data-path collective);
+the value is the total pairs of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ecg_1m_m256"
+WORKLOAD_DESC = ("query 2^20 ECG-like samples (seed 2, 20 malformed beats) vs dictionary 64 segments x 1024 "
+                 "samples (seed 3), m=256, float32 samples, FP64 window statistics")
+METRIC = "AB-join pairs/s at m=256 (tensor-core vs plain kernel); p50/p99 serving latency"
+L2_BYTES = 129 * 2**20
+# The plain kernel's algorithmic work per (query window, dictionary window)
+# pair: 2 FMAs of the covariance recurrence, 1 FMA for the score, 1
+# compare-and-keep of the running maximum = 4 FP32-pipe lane instructions.
+PLAIN_OPS_PER_PAIR = 4
+SMS, LANES_PER_SM = 152, 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, target_s: float = 15.0):
+    """Time the oracle (as it is) on a bounded sample of query windows."""
+    import oracle
+
+    oracle.build()
+    nq = w.n_rows
+    # calibrate on a few rows, then size the sample for ~target_s seconds
+    rows = np.arange(0, nq, nq // 16)[:16]
+    t0 = time.perf_counter()
+    oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)
+    dt = time.perf_counter() - t0
+    n_rows = int(max(16, min(nq, len(rows) * target_s / max(dt, 1e-6))))
+    rows = np.linspace(0, nq - 1, n_rows).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)
+    dt = time.perf_counter() - t0
+    pairs = n_rows * w.n_dict_windows
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_rows} evenly spaced of {nq} query windows, all {w.n_dict_windows} dictionary windows, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, timed on this host's cores."""
+    import synthetic
+
+    if rank != 0:
+        return
+    w = synthetic.workload(WORKLOAD)
+    import oracle
+
+    oracle.build()
+    nq = w.n_rows
+    rows_per_step = 256
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = (np.arange(rows_per_step) * (nq // rows_per_step) + s) % nq
+        t0 = time.perf_counter()
+        oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    pairs = rows_per_step * w.n_dict_windows
+    ms = 1e3 * float(np.mean(times))
+    value = pairs / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "sample_rows_per_step": rows_per_step},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{rows_per_step} query windows per step, all {w.n_dict_windows} "
+                                       "dictionary windows"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def kernel_id(mp, name):
+    return {"plain": mp.MP_KERNEL_PLAIN, "bf16x3": mp.MP_KERNEL_TC_BF16X3, "tf32": mp.MP_KERNEL_TC_TF32,
+            "auto": mp.MP_KERNEL_AUTO}[name]
+
+
+def time_device_join(mp, ctx, d, w, steps, warmup, flush):
+    """Per-step CUDA-event time of the whole join and per-phase event time."""
+    import torch
+
+    qt = torch.from_numpy(w.query).cuda()
+    nq = w.n_rows
+    dd = torch.empty(nq, dtype=torch.float64, device="cuda")
+    di = torch.empty(nq, dtype=torch.int64, device="cuda")
+    # A dedicated (non-default) stream: the library launches on it, and the
+    # timing events are recorded on it.
+    stream = torch.cuda.Stream()
+    assert stream.cuda_stream != 0
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.zero_()
+            mp.mp_ab_join_device(ctx, d, qt.data_ptr(), mp.MP_F32, len(w.query), w.m, dd.data_ptr(), di.data_ptr(),
+                                 stream.cuda_stream)
+        stream.synchronize()
+        mp.mp_profile(ctx, True)
+        mp.mp_profile_read(ctx, reset=True)
+        step_ms = []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps (outside the timed events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mp.mp_ab_join_device(ctx, d, qt.data_ptr(), mp.MP_F32, len(w.query), w.m, dd.data_ptr(),
+                                 di.data_ptr(), stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    phase_ms, phase_n = mp.mp_profile_read(ctx, reset=True)
+    mp.mp_profile(ctx, False)
+    return step_ms, phase_ms, phase_n, (dd, di)
+
+
+def time_e2e(mp, ctx, d, w, steps, warmup):
+    """End to end through mp_ab_join: pinned host query in, host result out, every step."""
+    import torch
+
+    q_pin = torch.from_numpy(w.query).pin_memory()
+    nq = w.n_rows
+    od = torch.empty(nq, dtype=torch.float64).pin_memory()
+    oi = torch.empty(nq, dtype=torch.int64).pin_memory()
+    qa, da, ia = q_pin.numpy(), od.numpy(), oi.numpy()
+    import ctypes
+
+    def once():
+        rc = mp.lib.mp_ab_join(ctx, d, qa.ctypes.data, mp.MP_F32, len(qa), w.m, da.ctypes.data, ia.ctypes.data)
+        if rc != 0:
+            raise mp.MPError(rc, mp.mp_last_error())
+
+    for _ in range(warmup):
+        once()
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        once()
+        t.append(time.perf_counter() - t0)
+    return t, len(qa) * 4, nq * 16
+
+
+def serving_run(mp, n_requests, seed=7):
+    """A short serving run: Poisson arrivals of mixed requests; p50/p99 latency and throughput."""
+    import synthetic
+
+    if n_requests <= 0:
+        return None
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=8, max_batch=16)
+    try:
+        dicts = synthetic.serving_dictionaries(n_dicts=16, seed=100)
+        handles = [mp.mp_dict_load(ctx, b, offs, [64, 128, 256]) for b, offs in dicts]
+        reqs = synthetic.serving_requests(n_requests, rate_hz=1.0, seed=seed, n_dicts=16, max_log2=18)
+        # 1) capacity: everything submitted at once
+        outs, tickets, pairs = [], [], 0
+        t0 = time.perf_counter()
+        for r in reqs:
+            nq = len(r.query) - r.m + 1
+            od, oi = np.empty(nq), np.empty(nq, dtype=np.int64)
+            outs.append((od, oi))
+            tickets.append(mp.mp_submit(ctx, handles[r.dict_id], r.query, r.m, od, oi))
+            pairs += nq * mp.mp_dict_windows(handles[r.dict_id], r.m)
+        mp.mp_drain(ctx, 600.0)
+        cap_s = time.perf_counter() - t0
+        for t in tickets:
+            mp.mp_poll(ctx, t)
+        capacity_rps = len(reqs) / cap_s
+        # 2) offered load at 0.5x capacity, Poisson arrivals
+        rate = 0.5 * capacity_rps
+        rng = np.random.default_rng(seed + 1)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        outs, tickets = [], []
+        t0 = time.perf_counter()
+        for a, r in zip(arrivals, reqs):
+            while time.perf_counter() - t0 < a:
+                time.sleep(0.0001)
+            nq = len(r.query) - r.m + 1
+            od, oi = np.empty(nq), np.empty(nq, dtype=np.int64)
+            outs.append((od, oi))
+            tickets.append(mp.mp_submit(ctx, handles[r.dict_id], r.query, r.m, od, oi))
+        lats = []
+        pending = set(tickets)
+        while pending:
+            for t in list(pending):
+                st, lat = mp.mp_poll(ctx, t)
+                if st != mp.MP_PENDING:
+                    lats.append(lat)
+                    pending.discard(t)
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        for h in handles:
+            mp.mp_dict_free(ctx, h)
+        lats = np.array(lats) * 1e3
+        return {"requests": len(reqs), "offered_rps": rate, "p50_ms": float(np.percentile(lats, 50)),
+                "p99_ms": float(np.percentile(lats, 99)), "throughput_rps": len(reqs) / wall,
+                "capacity_rps": capacity_rps, "capacity_pairs_per_s": pairs / cap_s,
+                "mix": "query 2^U samples U~U(10,18), random walk / ECG 50:50, m in {64,128,256}, "
+                       "16 resident dictionaries of 2^14..2^18 samples"}
+    finally:
+        mp.mp_shutdown(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "auto"])
+    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the query (profiling captures of a small case); 1.0 = the full workload")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2112_12965_gb300 as mp
+    import synthetic
+
+    w = synthetic.workload(WORKLOAD, scale=args.scale)
+    if rank > 0:  # weak scaling: each rank joins its own query of the same size
+        w.query = synthetic.ecg_like(len(w.query), 2 + 1000 * rank, n_malformed=min(20, len(w.query) // 400)).astype(np.float32)
+    ctx = mp.mp_init(device=local_rank, kernel=kernel_id(mp, args.kernel))
+    d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        step_ms, phase_ms, phase_n, _ = time_device_join(mp, ctx, d, w, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    pairs = w.pairs
+    value = world * pairs * args.steps / (total_ms / 1e3)
+
+    e2e_t, h2d, d2h = time_e2e(mp, ctx, d, w, max(3, args.steps // 2), 1)
+    e2e_value = pairs / float(np.mean(e2e_t))
+
+    peaks, peak_src = load_peaks()
+    join_ms = phase_ms[mp.MP_PHASE_JOIN] / max(1, phase_n[mp.MP_PHASE_JOIN])
+    clock = clk.summary()
+    if args.kernel in ("plain",):
+        peak_ops = SMS * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
+        achieved = pairs * PLAIN_OPS_PER_PAIR / (join_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": None, "kernel": "k_plain",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
+                               f"({peak_src} max clock)",
+                "ops_per_pair": PLAIN_OPS_PER_PAIR}
+    else:
+        tflops_peak = peaks.get("bf16_tflops", 1900.0)
+        mult = 3 if args.kernel == "bf16x3" else 1
+        if args.kernel == "tf32":
+            tflops_peak /= 2.0
+        achieved = pairs * 2 * w.m * mult / (join_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tflops_peak, "unit": "TFLOP/s",
+                "frac": achieved / tflops_peak, "traffic": None, "kernel": "k_tc",
+                "peak_source": f"{peak_src} bf16 burst" + (" / 2 (tf32 nominal ratio)" if args.kernel == "tf32" else "")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "n_query_windows": w.n_rows, "n_dict_windows": w.n_dict_windows,
+                   "pairs_per_step_per_gpu": pairs, "kernel": args.kernel, "scale": args.scale,
+                   "l2": "flushed between timed steps (512 MB write outside the timed events)",
+                   "parallelism": f"{world} independent queries (weak scaling)" if world > 1 else "1 GPU"},
+        "phases_ms": {"stats": phase_ms[0] / max(1, phase_n[0]), "join": join_ms,
+                      "finalize": phase_ms[2] / max(1, phase_n[2])},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(np.sum(phase_n)),
+        "clocks": clock,
+    }
+    mp.mp_dict_free(ctx, d)
+    mp.mp_shutdown(ctx)
+    if rank == 0:
+        serving = serving_run(mp, args.serving_requests)
+        if serving:
+            line["serving"] = serving
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

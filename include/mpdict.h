@@ -1,0 +1,202 @@
+/*
+ * mpdict -- dictionary AB-join of time series on one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the approximate inter-time-series similarity join of
+ * Yeh et al., "Error-bounded Approximate Time Series Joins Using Compact
+ * Dictionary Representations of Time Series" (SDM 2022):
+ *
+ *   P_hat[i] = min over dictionary windows g of d(T_A[i : i+m], D_B[g : g+m])
+ *   I_hat[i] = the g that attains it
+ *
+ * for every length-m window i of a query series T_A (Def. 2, Def. 3), where d
+ * is the z-normalised Euclidean distance (Sec. 2.1) and the dictionary windows
+ * slide inside each dictionary element (segment) and never cross a segment
+ * boundary (Def. 8). This is Algorithm 2 (Sec. 3.2): the profile starts at
+ * +inf and each segment's 1NN join is merged in by an element-wise minimum.
+ * The inputs follow the problem statement (Sec. 2.1): the query T_A, the
+ * dictionary D_B and the window length m.
+ *
+ * Conventions shared by every call:
+ *   - Indices are 0-based (the paper's are 1-based).
+ *   - The neighbour index is the global window index g: the start offset of
+ *     the window in the concatenated segment buffer. Its segment s is the one
+ *     with seg_offsets[s] <= g < seg_offsets[s+1].
+ *   - The standard deviation is the population one (divide by m), so
+ *     0 <= d <= 2 sqrt(m).
+ *   - A window whose m samples all compare equal is constant. It normalises
+ *     to the zero vector, so d(constant, non-constant) = sqrt(m) and
+ *     d(constant, constant) = 0 (the paper leaves this case open).
+ *   - On equal distances the lowest g wins.
+ *   - A dictionary with no window of length m (every segment shorter than m)
+ *     is not an error: every row gets +inf and index -1, the initial value of
+ *     Algorithm 2.
+ *   - Query and dictionary must have the same sample type. F32 data is joined
+ *     in FP32 arithmetic with FP64 window statistics; F64 data in FP64.
+ *
+ * Errors: every call returns MP_OK (0) or a negative MP_E_* code and, on
+ * error, leaves a message for mp_last_error(). Invalid arguments (null
+ * pointers, m < 2, n < m, NaN or Inf samples, unsorted offsets, unknown dtype)
+ * give MP_E_ARG and change nothing. A CUDA failure gives MP_E_CUDA.
+ *
+ * Threads: a context may be used from several host threads; calls on one
+ * context are serialised internally. Distinct contexts are independent.
+ */
+#ifndef MPDICT_H
+#define MPDICT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MP_OK 0
+#define MP_E_ARG (-1)      /* invalid argument */
+#define MP_E_NOMEM (-2)    /* device or host allocation failed, or request larger than the memory budget */
+#define MP_E_CUDA (-3)     /* a CUDA call failed */
+#define MP_E_NOTFOUND (-4) /* unknown ticket */
+#define MP_E_BUSY (-5)     /* object still referenced by requests in flight */
+#define MP_E_TIMEOUT (-6)  /* a bounded wait ran out */
+#define MP_E_INTERNAL (-7) /* a device-side consistency check failed */
+
+/* sample types */
+#define MP_F32 0
+#define MP_F64 1
+
+/* join forms (mp_config.kernel, mp_set_kernel) */
+#define MP_KERNEL_AUTO 0      /* the autotuner's choice for (m, dictionary size, dtype) */
+#define MP_KERNEL_PLAIN 1     /* diagonal recurrence on the FP32 (F64 data: FP64) pipes */
+#define MP_KERNEL_TC_BF16X3 2 /* tcgen05 Hankel tiles, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+#define MP_KERNEL_TC_TF32 3   /* tcgen05 Hankel tiles, one TF32 product, FP32 accumulation */
+
+/* request states (mp_poll) */
+#define MP_PENDING 0
+#define MP_DONE 1
+#define MP_FAILED 2
+
+typedef struct mp_ctx mp_ctx;
+typedef struct mp_dict mp_dict;
+
+/* Context configuration. Fill with mp_config_default() and override fields. */
+typedef struct mp_config {
+    int32_t device;        /* CUDA device ordinal */
+    int32_t kernel;        /* MP_KERNEL_*; F64 data always uses MP_KERNEL_PLAIN */
+    int32_t max_inflight;  /* serving: requests whose work may be on the device at once */
+    int32_t max_batch;     /* serving: requests merged into one persistent launch */
+    size_t mem_budget;     /* serving: device bytes that admitted requests may hold; 0 = half the free memory at init */
+    const char *tune_cache;/* autotune cache file (JSON lines), or NULL for none */
+} mp_config;
+
+/* Default configuration (device 0, AUTO kernel, 8 in flight, batch 64). */
+int mp_config_default(mp_config *cfg);
+
+/* Create a context on cfg->device (NULL cfg: defaults). *ctx receives the handle. */
+int mp_init(mp_ctx **ctx, const mp_config *cfg);
+
+/* Destroy a context: waits for requests in flight, frees dictionaries and
+ * device memory it owns. */
+int mp_shutdown(mp_ctx *ctx);
+
+/* Message of the last error on the calling thread ("" if none). The pointer
+ * stays valid until the thread's next library call. */
+const char *mp_last_error(void);
+
+/* Select the join form used by later calls on this context (MP_KERNEL_*). */
+int mp_set_kernel(mp_ctx *ctx, int32_t kernel);
+
+/*
+ * Load a dictionary D_B (Sec. 3.1 output, Algorithm 2 input) onto the device.
+ *   samples      host pointer, seg_offsets[n_segments] samples of type dtype
+ *   seg_offsets  host, n_segments + 1 non-decreasing int64 offsets starting at 0;
+ *                segment s is samples[seg_offsets[s] .. seg_offsets[s+1])
+ *   ms, n_ms     window lengths whose statistics are computed now (others are
+ *                computed on first use); may be NULL / 0
+ *   out          receives the handle
+ * The samples are copied; the caller may free its buffers on return. The
+ * total sample count must be below 2^31.
+ */
+int mp_dict_load(mp_ctx *ctx, const void *samples, int32_t dtype, const int64_t *seg_offsets, int32_t n_segments,
+                 const int32_t *ms, int32_t n_ms, mp_dict **out);
+
+/* Free a dictionary. MP_E_BUSY while submitted requests still reference it. */
+int mp_dict_free(mp_ctx *ctx, mp_dict *dict);
+
+/* Number of valid dictionary windows W for window length m (windows inside one segment). */
+int mp_dict_windows(const mp_dict *dict, int32_t m, int64_t *n_windows);
+
+/*
+ * Synchronous join with host buffers (Algorithm 2).
+ *   query     host, n samples of type dtype (must match the dictionary's)
+ *   out_dist  host, n - m + 1 doubles: P_hat
+ *   out_idx   host, n - m + 1 int64: global window index g, or -1
+ * Copies the query to the device, joins, copies the result back and returns.
+ */
+int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+               double *out_dist, int64_t *out_idx);
+
+/*
+ * The same join on device buffers, enqueued on `stream` (a cudaStream_t; NULL
+ * = the context's own stream). d_query, d_out_dist and d_out_idx are device
+ * pointers with the sizes of mp_ab_join. The call returns once the work is
+ * enqueued; the outputs are ready when the stream reaches that point. The
+ * query buffer must stay unchanged until then. Scratch memory comes from the
+ * context's workspace, so calls on one context must not overlap on the GPU
+ * (the context serialises them on the host; use one context per concurrent
+ * stream).
+ */
+int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int32_t dtype, int64_t n, int32_t m,
+                      double *d_out_dist, int64_t *d_out_idx, void *stream);
+
+/*
+ * Window statistics (the first pass of the join) of a device series:
+ * mean, 1/std (0 for a constant window) and the constant flag of each of the
+ * n - m + 1 windows, in FP64, enqueued on `stream`.
+ */
+int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int32_t m, double *d_mean,
+                    double *d_invstd, uint8_t *d_const, void *stream);
+
+/*
+ * Serving: submit a join request. The query is copied before the call
+ * returns. out_dist / out_idx are host buffers (n - m + 1 entries) that must
+ * stay valid until mp_poll reports MP_DONE or MP_FAILED. Requests are admitted
+ * to the device as slots and memory free up and are batched with other
+ * requests into persistent launches; each result is identical to what
+ * mp_ab_join returns for the same inputs. *ticket receives the request id.
+ */
+int mp_submit(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+              double *out_dist, int64_t *out_idx, uint64_t *ticket);
+
+/*
+ * Non-blocking state of a request: *state = MP_PENDING, MP_DONE or MP_FAILED;
+ * *latency_s (may be NULL) = submit-to-completion time once done. A ticket
+ * can be polled until it has been reported done or failed once; later polls
+ * give MP_E_NOTFOUND.
+ */
+int mp_poll(mp_ctx *ctx, uint64_t ticket, int32_t *state, double *latency_s);
+
+/* Block until every submitted request has finished or timeout_s passes (MP_E_TIMEOUT). */
+int mp_drain(mp_ctx *ctx, double timeout_s);
+
+/* Phases of a join, for mp_profile_read. */
+#define MP_PHASE_STATS 0    /* window statistics of the query (K1) */
+#define MP_PHASE_JOIN 1     /* the join kernel: plain (K2) or tensor-core (K3) */
+#define MP_PHASE_FINALIZE 2 /* reduction, constant-window rule and exact distance of the pick (K4) */
+#define MP_PHASE_COUNT 3
+
+/*
+ * Tracing: with enable = 1, synchronous and device joins on this context
+ * record a CUDA event pair around each phase, on the stream the phase runs
+ * on. mp_profile_read waits for the recorded work and returns the summed
+ * device milliseconds and launch counts per phase (arrays of MP_PHASE_COUNT;
+ * either may be NULL); reset = 1 clears the sums.
+ */
+int mp_profile(mp_ctx *ctx, int32_t enable);
+int mp_profile_read(mp_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPDICT_H */

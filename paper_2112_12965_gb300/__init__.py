@@ -1,0 +1,235 @@
+"""Python binding of libmpdict (include/mpdict.h): the dictionary AB-join on a GB300.
+
+The functions carry the C ABI's names and only marshal arguments: every step of
+the join runs in the library's CUDA kernels. There is no CPU fallback; if the
+shared library has not been built, importing this package raises.
+
+Host arrays are numpy arrays; device arrays are passed as raw pointers (for
+example ``tensor.data_ptr()`` of a CUDA torch tensor) together with a stream
+handle (``torch.cuda.current_stream().cuda_stream``) or 0 for the context's own
+stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpdict.so")
+
+MP_OK = 0
+MP_E_ARG = -1
+MP_E_NOMEM = -2
+MP_E_CUDA = -3
+MP_E_NOTFOUND = -4
+MP_E_BUSY = -5
+MP_E_TIMEOUT = -6
+MP_E_INTERNAL = -7
+
+MP_F32 = 0
+MP_F64 = 1
+
+MP_KERNEL_AUTO = 0
+MP_KERNEL_PLAIN = 1
+MP_KERNEL_TC_BF16X3 = 2
+MP_KERNEL_TC_TF32 = 3
+
+MP_PHASE_STATS = 0
+MP_PHASE_JOIN = 1
+MP_PHASE_FINALIZE = 2
+MP_PHASE_COUNT = 3
+
+MP_PENDING = 0
+MP_DONE = 1
+MP_FAILED = 2
+
+_CODES = {
+    MP_E_ARG: "MP_E_ARG",
+    MP_E_NOMEM: "MP_E_NOMEM",
+    MP_E_CUDA: "MP_E_CUDA",
+    MP_E_NOTFOUND: "MP_E_NOTFOUND",
+    MP_E_BUSY: "MP_E_BUSY",
+    MP_E_TIMEOUT: "MP_E_TIMEOUT",
+    MP_E_INTERNAL: "MP_E_INTERNAL",
+}
+
+
+class MPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mp_config(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("max_inflight", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("mem_budget", ctypes.c_size_t),
+        ("tune_cache", ctypes.c_char_p),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()'). "
+            "There is no CPU fallback."
+        )
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "mp_config_default": ([ctypes.POINTER(mp_config)], ctypes.c_int),
+        "mp_init": ([ctypes.POINTER(P), ctypes.POINTER(mp_config)], ctypes.c_int),
+        "mp_shutdown": ([P], ctypes.c_int),
+        "mp_last_error": ([], ctypes.c_char_p),
+        "mp_set_kernel": ([P, i32], ctypes.c_int),
+        "mp_dict_load": ([P, P, i32, P, i32, P, i32, ctypes.POINTER(P)], ctypes.c_int),
+        "mp_dict_free": ([P, P], ctypes.c_int),
+        "mp_dict_windows": ([P, i32, ctypes.POINTER(i64)], ctypes.c_int),
+        "mp_ab_join": ([P, P, P, i32, i64, i32, P, P], ctypes.c_int),
+        "mp_ab_join_device": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
+        "mp_window_stats": ([P, P, i32, i64, i32, P, P, P, P], ctypes.c_int),
+        "mp_submit": ([P, P, P, i32, i64, i32, P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "mp_poll": ([P, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "mp_drain": ([P, ctypes.c_double], ctypes.c_int),
+        "mp_profile": ([P, i32], ctypes.c_int),
+        "mp_profile_read": ([P, P, P, i32], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def mp_last_error() -> str:
+    return lib.mp_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != MP_OK:
+        raise MPError(rc, mp_last_error())
+
+
+def _dtype_of(x: np.ndarray) -> int:
+    if x.dtype == np.float32:
+        return MP_F32
+    if x.dtype == np.float64:
+        return MP_F64
+    raise TypeError(f"samples must be float32 or float64, not {x.dtype}")
+
+
+def _ptr(x: np.ndarray) -> int:
+    return x.ctypes.data
+
+
+def mp_config_default() -> mp_config:
+    cfg = mp_config()
+    _check(lib.mp_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def mp_init(cfg: Optional[mp_config] = None, **overrides) -> ctypes.c_void_p:
+    """Create a context. Keyword overrides set fields of the default config."""
+    if cfg is None:
+        cfg = mp_config_default()
+    for k, v in overrides.items():
+        setattr(cfg, k, v.encode() if isinstance(v, str) else v)
+    ctx = ctypes.c_void_p()
+    _check(lib.mp_init(ctypes.byref(ctx), ctypes.byref(cfg)))
+    return ctx
+
+
+def mp_shutdown(ctx) -> None:
+    _check(lib.mp_shutdown(ctx))
+
+
+def mp_set_kernel(ctx, kernel: int) -> None:
+    _check(lib.mp_set_kernel(ctx, kernel))
+
+
+def mp_dict_load(ctx, samples: np.ndarray, seg_offsets: Sequence[int], ms: Sequence[int] = ()) -> ctypes.c_void_p:
+    """Upload a dictionary: samples (float32/float64) cut by seg_offsets (len = n_segments + 1)."""
+    samples = np.ascontiguousarray(samples)
+    dt = _dtype_of(samples)
+    offs = np.ascontiguousarray(seg_offsets, dtype=np.int64)
+    msa = np.ascontiguousarray(ms, dtype=np.int32)
+    d = ctypes.c_void_p()
+    _check(lib.mp_dict_load(ctx, _ptr(samples) if samples.size else None, dt, _ptr(offs), len(offs) - 1,
+                            _ptr(msa) if msa.size else None, len(msa), ctypes.byref(d)))
+    return d
+
+
+def mp_dict_free(ctx, d) -> None:
+    _check(lib.mp_dict_free(ctx, d))
+
+
+def mp_dict_windows(d, m: int) -> int:
+    w = ctypes.c_int64()
+    _check(lib.mp_dict_windows(d, m, ctypes.byref(w)))
+    return w.value
+
+
+def mp_ab_join(ctx, d, query: np.ndarray, m: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Synchronous join with host buffers; returns (distance, index) arrays of length n - m + 1."""
+    q = np.ascontiguousarray(query)
+    nq = max(len(q) - m + 1, 0)
+    dist = np.empty(nq, dtype=np.float64)
+    idx = np.empty(nq, dtype=np.int64)
+    _check(lib.mp_ab_join(ctx, d, _ptr(q), _dtype_of(q), len(q), m, _ptr(dist), _ptr(idx)))
+    return dist, idx
+
+
+def mp_ab_join_device(ctx, d, d_query: int, dtype: int, n: int, m: int, d_dist: int, d_idx: int,
+                      stream: int = 0) -> None:
+    """Join on device pointers, enqueued on `stream` (0: the context's stream)."""
+    _check(lib.mp_ab_join_device(ctx, d, d_query, dtype, n, m, d_dist, d_idx, stream or None))
+
+
+def mp_window_stats(ctx, d_x: int, dtype: int, n: int, m: int, d_mean: int, d_invstd: int, d_const: int,
+                    stream: int = 0) -> None:
+    _check(lib.mp_window_stats(ctx, d_x, dtype, n, m, d_mean, d_invstd, d_const, stream or None))
+
+
+def mp_submit(ctx, d, query: np.ndarray, m: int, out_dist: np.ndarray, out_idx: np.ndarray) -> int:
+    """Queue a request; out_dist / out_idx (length n - m + 1) must stay alive until it is done."""
+    q = np.ascontiguousarray(query)
+    nq = len(q) - m + 1
+    assert out_dist.dtype == np.float64 and out_idx.dtype == np.int64
+    assert out_dist.flags.c_contiguous and out_idx.flags.c_contiguous
+    assert len(out_dist) >= nq and len(out_idx) >= nq
+    t = ctypes.c_uint64()
+    _check(lib.mp_submit(ctx, d, _ptr(q), _dtype_of(q), len(q), m, _ptr(out_dist), _ptr(out_idx), ctypes.byref(t)))
+    return t.value
+
+
+def mp_poll(ctx, ticket: int) -> Tuple[int, float]:
+    st = ctypes.c_int32()
+    lat = ctypes.c_double(-1.0)
+    _check(lib.mp_poll(ctx, ticket, ctypes.byref(st), ctypes.byref(lat)))
+    return st.value, lat.value
+
+
+def mp_drain(ctx, timeout_s: float = 60.0) -> None:
+    _check(lib.mp_drain(ctx, timeout_s))
+
+
+def mp_profile(ctx, enable: bool) -> None:
+    _check(lib.mp_profile(ctx, 1 if enable else 0))
+
+
+def mp_profile_read(ctx, reset: bool = False) -> Tuple[np.ndarray, np.ndarray]:
+    """Per-phase device milliseconds and launch counts recorded since the last reset."""
+    ms = np.zeros(MP_PHASE_COUNT, dtype=np.float64)
+    n = np.zeros(MP_PHASE_COUNT, dtype=np.int64)
+    _check(lib.mp_profile_read(ctx, _ptr(ms), _ptr(n), 1 if reset else 0))
+    return ms, n

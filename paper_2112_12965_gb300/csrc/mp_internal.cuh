@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of libmpdict.
+// Nothing here is part of the public C ABI (include/mpdict.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpd {
+
+// Vector types holding the per-window recurrence statistics.
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = dvec4; };
+template <typename T> using vec4_t = typename Vec4<T>::type;
+
+// A run of consecutive valid dictionary windows inside one segment:
+// global windows g0 .. g0 + ncols - 1.
+struct Span {
+    int64_t g0;
+    int32_t ncols;
+    int32_t pad;
+};
+
+// Launch geometry of the plain diagonal kernel.
+constexpr int kPlainRowsPerLane = 16;  // query windows owned by one lane
+constexpr int kPlainColBlock = 256;    // dictionary windows staged per block
+
+// Per-window statistics of a series for one window length m (kernel K1).
+//   mean[i], invstd[i]   FP64 mean and 1/population-std (0 for a constant window)
+//   cflag[i]             1 if the window's samples all compare equal
+//   rs[i]                recurrence terms for the diagonal kernel, in the join's
+//                        arithmetic type T:
+//                          x = df[i] = (x[i+m-1] - x[i-1]) / 2          (0 for i = 0)
+//                          y = dg[i] = (x[i+m-1] - mean[i]) + (x[i-1] - mean[i-1])  (0 for i = 0)
+//                          z = invstd[i] rounded to T
+//                          w = 0, or -inf for a constant window (excludes it from
+//                              the maximum of the correlation score)
+template <typename T>
+cudaError_t launch_window_stats(const T *x, int64_t n, int32_t m, double *mean, double *invstd, uint8_t *cflag,
+                                vec4_t<T> *rs, cudaStream_t st);
+
+// Checks every sample is finite; sets *bad to 1 otherwise (bad must be zeroed).
+template <typename T>
+cudaError_t launch_check_finite(const T *x, int64_t n, int32_t *bad, cudaStream_t st);
+
+// Lowest constant window and lowest valid window among the spans (int64 out[2], -1 if none).
+cudaError_t launch_dict_specials(const Span *spans, int32_t n_spans, const uint8_t *cflag, int64_t *out,
+                                 cudaStream_t st);
+
+// Partial result of one column group for one query window: the largest
+// correlation score q = cov * invstd_b over the group's non-constant windows
+// and the lowest global window index attaining it (-1 if none).
+template <typename T> struct Partial {
+    T q;
+    int32_t g;
+};
+
+struct PlainLaunch {
+    int64_t nq;            // query windows
+    int32_t m;
+    int32_t n_row_blocks;
+    int32_t n_groups;      // column groups
+    int32_t warps;         // warps per CTA (rows per CTA = warps * 32 * kPlainRowsPerLane)
+};
+
+// Plain diagonal-recurrence join (kernel K2). Writes part[group * nq + row].
+// spans[group_start[k] .. group_start[k+1]) are the spans of column group k.
+template <typename T>
+cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const double *mean_a,
+                         const T *b, int64_t nb, const vec4_t<T> *rs_b, const double *mean_b, const Span *spans,
+                         const int32_t *group_start, Partial<T> *part, cudaStream_t st);
+template <typename T> size_t plain_smem_bytes(int warps, int m);
+
+// Serving: one request of a persistent batched launch (FP32 data). The layout
+// mirrors the kernel's parameter block.
+struct PlainRequest {
+    const float *a;
+    int64_t na;
+    int64_t nq;
+    int32_t m;
+    int32_t n_groups;
+    const float4 *rs_a;
+    const double *mean_a;
+    const float *b;
+    int64_t nb;
+    const float4 *rs_b;
+    const double *mean_b;
+    const Span *spans;
+    const int32_t *group_start;
+    Partial<float> *part;
+};
+struct BatchItem {
+    int32_t req;  // index into the request array
+    int32_t grp;  // column group
+    int64_t rb;   // row block
+};
+// Launch `grid` persistent CTAs of `warps` warps over items[0 .. n_items);
+// *counter must be 0. Every request in the batch must have m <= max_m and use
+// `warps` warps per row block.
+cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *items, int32_t n_items,
+                                 int32_t *counter, int warps, int max_m, int grid, cudaStream_t st);
+template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
+
+// Finalisation (kernel K4): reduce the column groups, apply the constant-window
+// convention, recompute the chosen pair's distance exactly and write the output.
+//   g_const  lowest constant valid dictionary window, or -1
+//   g_first  lowest valid dictionary window, or -1 (no window at all)
+template <typename T>
+cudaError_t launch_finalize(int64_t nq, int32_t m, int32_t n_groups, const Partial<T> *part, const T *a,
+                            const double *mean_a, const double *invstd_a, const uint8_t *cflag_a, const T *b,
+                            const double *mean_b, const double *invstd_b, int64_t g_const, int64_t g_first,
+                            double *out_dist, int64_t *out_idx, cudaStream_t st);
+
+}  // namespace mpd

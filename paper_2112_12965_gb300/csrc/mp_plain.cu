@@ -1,0 +1,319 @@
+// K2: the plain form of the dictionary AB-join -- a diagonal recurrence on the
+// FP32 pipes (FP64 for float64 data).
+//
+// Algorithm 2 (Sec. 3.2) joins the query with every dictionary segment and
+// keeps the element-wise minimum. For one segment the join is an exact AB-join
+// (the paper uses the method of its ref. "Matrix Profile XIV" for it): along a
+// diagonal (i, g) -> (i+1, g+1) the centred covariance
+//     C(i, g) = sum_k (a[i+k] - mean_a[i]) * (b[g+k] - mean_b[g])
+// changes by O(1) work:
+//     C(i, g) = C(i-1, g-1) + df_a[i] * dg_b[g] + df_b[g] * dg_a[i]
+// with df[i] = (x[i+m-1] - x[i-1]) / 2 and
+//      dg[i] = (x[i+m-1] - mean[i]) + (x[i-1] - mean[i-1])
+// (expanding both means around the previous window proves it). The distance
+// follows from the Pearson correlation rho = C * invstd_a * invstd_b / m as
+// d^2 = 2 m (1 - rho), so for one query window the nearest non-constant
+// dictionary window is the one with the largest q = C * invstd_b.
+//
+// Layout of the work. A CTA owns a block of consecutive query windows (rows);
+// each lane owns kRows consecutive rows and keeps their C values in registers.
+// The CTA walks the dictionary windows (columns) of a column group in
+// increasing g. Moving one column to the right moves every diagonal one row
+// down, so each lane shifts its registers by one row and takes the top one
+// from the lane above with a warp shuffle. The first row of each warp has no
+// row above inside the warp: its value comes from a "top seed", a direct dot
+// product computed per column block. At the first column of each span (a run
+// of columns inside one segment) every row gets a "left seed", also a direct
+// dot product. Dictionary windows never cross a segment (Def. 8) because spans
+// never do. Each lane keeps the running maximum of q and the lowest g that
+// attains it for its rows; the partial result per (row, column group) is
+// reduced by the finalisation kernel.
+//
+// Seeds are computed on shifted samples (query minus a per-CTA constant,
+// dictionary minus a per-block constant), which keeps the FP32 products small
+// for series with large offsets; the exact mean correction m * da * db is
+// applied afterwards from the FP64 means.
+#include <math.h>
+
+#include "mp_internal.cuh"
+
+namespace mpd {
+namespace {
+
+template <typename T> struct PlainParams {
+    const T *a;
+    int64_t na;
+    int64_t nq;
+    int32_t m;
+    int32_t n_groups;
+    const vec4_t<T> *rs_a;
+    const double *mean_a;
+    const T *b;
+    int64_t nb;
+    const vec4_t<T> *rs_b;
+    const double *mean_b;
+    const Span *spans;
+    const int32_t *group_start;
+    Partial<T> *part;
+};
+
+// Padded shared-memory index: one pad slot every P elements, so that lanes
+// reading with a stride of P (or P+...) hit distinct banks.
+template <int P> __device__ __forceinline__ int pad(int e) { return e + e / P; }
+
+// One work item: query rows [rb * rows_cta, (rb + 1) * rows_cta) against the
+// spans of column group grp.
+template <typename T, int kRows>
+__device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, int grp, unsigned char *smem_raw)
+{
+    constexpr int CB = kPlainColBlock;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int rows_cta = nwarps * 32 * kRows;
+    const int64_t R0 = rb * rows_cta;
+    const int m = p.m;
+    const int m_up8 = (m + 7) & ~7;
+    const int m_up16 = (m + 15) & ~15;
+
+    // sa: shifted query samples a[R0 + e] - shift_a, e in [0, NA)
+    const int NA = rows_cta + m_up16 + 32;
+    T *sa = reinterpret_cast<T *>(smem_raw);
+    const int NA_pad = pad<16>(NA) + 1;
+    // sb: shifted dictionary samples of the current column block
+    const int NB = CB + m_up8 + 16;
+    T *sb = sa + NA_pad;
+    const int NB_pad = pad<8>(NB) + 1;
+    // stop: top seeds, one per (warp, column of the block)
+    T *stop = sb + NB_pad;
+
+    const T shift_a = (T)p.mean_a[R0 < p.nq ? R0 : p.nq - 1];
+    for (int e = threadIdx.x; e < NA; e += blockDim.x) {
+        const int64_t j = R0 + e;
+        sa[pad<16>(e)] = (j < p.na) ? (p.a[j] - shift_a) : T(0);
+    }
+
+    const int64_t r_w = R0 + (int64_t)warp * 32 * kRows;  // first row of this warp
+    const int64_t r0 = r_w + (int64_t)lane * kRows;       // first row of this lane
+    T dfa[kRows], dga[kRows], C[kRows], best[kRows];
+    int32_t bidx[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+        const int64_t r = r0 + j;
+        if (r < p.nq) {
+            const vec4_t<T> v = p.rs_a[r];
+            dfa[j] = v.x;
+            dga[j] = v.y;
+        } else {
+            dfa[j] = T(0);
+            dga[j] = T(0);
+        }
+        C[j] = T(0);
+        best[j] = T(-INFINITY);
+        bidx[j] = -1;
+    }
+    const T da_w = (T)(p.mean_a[r_w < p.nq ? r_w : p.nq - 1] - (double)shift_a);
+    const int sa_w = warp * 32 * kRows;      // sa index of this warp's first row
+    const int sa_l = sa_w + lane * kRows;    // sa index of this lane's first row
+
+    const int s_lo = p.group_start[grp], s_hi = p.group_start[grp + 1];
+    for (int s = s_lo; s < s_hi; ++s) {
+        const Span sp = p.spans[s];
+        for (int cb = 0; cb < sp.ncols; cb += CB) {
+            const int ncb = min(CB, sp.ncols - cb);
+            const int64_t gblk = sp.g0 + cb;
+            const T shift_b = (T)p.mean_b[gblk];
+            __syncthreads();  // previous block's sb / stop no longer in use
+            for (int e = threadIdx.x; e < NB; e += blockDim.x) {
+                const int64_t j = gblk + e;
+                sb[pad<8>(e)] = (j < p.nb) ? (p.b[j] - shift_b) : T(0);
+            }
+            __syncthreads();
+
+            // ---- top seeds: C(r_w, gblk + c) for c in [8*lane, 8*lane + 8) ----
+            {
+                T acc[8], bw[8];
+                const int c0 = 8 * lane;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    acc[t] = T(0);
+                    bw[t] = sb[pad<8>(c0 + t)];
+                }
+                for (int k0 = 0; k0 < m_up8; k0 += 8) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = k0 + u;
+                        const T xk = (k < m) ? sa[pad<16>(sa_w + k)] : T(0);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) acc[t] = fma(xk, bw[(t + u) & 7], acc[t]);
+                        bw[u] = sb[pad<8>(c0 + 8 + k)];
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int c = c0 + t;
+                    if (c < ncb) {
+                        const T db = (T)(p.mean_b[gblk + c] - (double)shift_b);
+                        stop[warp * CB + c] = acc[t] - T(m) * da_w * db;
+                    }
+                }
+            }
+
+            // ---- left seeds at the first column of the span ----
+            if (cb == 0) {
+                T aw[16];
+#pragma unroll
+                for (int j = 0; j < kRows; ++j) C[j] = T(0);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) aw[t] = sa[pad<16>(sa_l + t)];
+                for (int k0 = 0; k0 < m_up16; k0 += 16) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int k = k0 + u;
+                        const T bk = (k < m) ? sb[pad<8>(k)] : T(0);
+#pragma unroll
+                        for (int j = 0; j < kRows; ++j) C[j] = fma(aw[(j + u) & 15], bk, C[j]);
+                        aw[u] = sa[pad<16>(sa_l + 16 + k)];
+                    }
+                }
+                const T db0 = (T)(p.mean_b[gblk] - (double)shift_b);
+#pragma unroll
+                for (int j = 0; j < kRows; ++j) {
+                    const int64_t r = r0 + j;
+                    const T da = (T)(p.mean_a[r < p.nq ? r : p.nq - 1] - (double)shift_a);
+                    C[j] -= T(m) * da * db0;
+                }
+            }
+            __syncwarp();
+
+            // ---- main loop: one dictionary window (column) per step ----
+            vec4_t<T> cs = p.rs_b[gblk];
+            for (int c = 0; c < ncb; ++c) {
+                const int64_t g = gblk + c;
+                const vec4_t<T> cs_next = p.rs_b[(c + 1 < ncb) ? g + 1 : g];
+                if (cb > 0 || c > 0) {
+                    const T up = __shfl_up_sync(0xffffffffu, C[kRows - 1], 1);
+#pragma unroll
+                    for (int j = kRows - 1; j >= 1; --j) C[j] = fma(dfa[j], cs.y, fma(cs.x, dga[j], C[j - 1]));
+                    const T c0v = fma(dfa[0], cs.y, fma(cs.x, dga[0], up));
+                    C[0] = (lane == 0) ? stop[warp * CB + c] : c0v;
+                }
+#pragma unroll
+                for (int j = 0; j < kRows; ++j) {
+                    const T q = fma(C[j], cs.z, cs.w);
+                    if (q > best[j]) {
+                        best[j] = q;
+                        bidx[j] = (int32_t)g;
+                    }
+                }
+                cs = cs_next;
+            }
+        }
+    }
+
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+        const int64_t r = r0 + j;
+        if (r < p.nq) {
+            Partial<T> v;
+            v.q = best[j];
+            v.g = bidx[j];
+            p.part[(int64_t)grp * p.nq + r] = v;
+        }
+    }
+}
+
+template <typename T, int kRows>
+__global__ void __launch_bounds__(128) k_plain(PlainParams<T> p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    plain_item<T, kRows>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
+}
+
+// Persistent batched form for serving: the CTAs walk a list of work items that
+// may belong to different requests (different query, dictionary and m). Items
+// are claimed in list order with a global counter.
+template <typename T, int kRows>
+__global__ void __launch_bounds__(128) k_plain_batched(const PlainParams<T> *__restrict__ reqs,
+                                                       const BatchItem *__restrict__ items, int32_t n_items,
+                                                       int32_t *__restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t next;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous `next`
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int32_t it = next;
+        if (it >= n_items) break;
+        const BatchItem bi = items[it];
+        const PlainParams<T> p = reqs[bi.req];
+        plain_item<T, kRows>(p, bi.rb, bi.grp, smem_raw);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+size_t plain_smem_bytes(int warps, int m)
+{
+    const int rows_cta = warps * 32 * plain_rows_per_lane<T>();
+    const int m_up8 = (m + 7) & ~7, m_up16 = (m + 15) & ~15;
+    const int NA = rows_cta + m_up16 + 32;
+    const int NB = kPlainColBlock + m_up8 + 16;
+    return sizeof(T) * ((size_t)(NA + NA / 16 + 1) + (size_t)(NB + NB / 8 + 1) + (size_t)warps * kPlainColBlock);
+}
+
+template <typename T>
+cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const double *mean_a,
+                         const T *b, int64_t nb, const vec4_t<T> *rs_b, const double *mean_b, const Span *spans,
+                         const int32_t *group_start, Partial<T> *part, cudaStream_t st)
+{
+    PlainParams<T> p;
+    p.a = a;
+    p.na = na;
+    p.nq = L.nq;
+    p.m = L.m;
+    p.n_groups = L.n_groups;
+    p.rs_a = rs_a;
+    p.mean_a = mean_a;
+    p.b = b;
+    p.nb = nb;
+    p.rs_b = rs_b;
+    p.mean_b = mean_b;
+    p.spans = spans;
+    p.group_start = group_start;
+    p.part = part;
+    const size_t smem = plain_smem_bytes<T>(L.warps, L.m);
+    constexpr int R = plain_rows_per_lane<T>();
+    auto kern = k_plain<T, R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (int64_t)L.n_row_blocks * L.n_groups;
+    kern<<<(unsigned)grid, 32 * L.warps, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *items, int32_t n_items,
+                                 int32_t *counter, int warps, int max_m, int grid, cudaStream_t st)
+{
+    static_assert(sizeof(PlainRequest) == sizeof(PlainParams<float>), "request layout");
+    const size_t smem = plain_smem_bytes<float>(warps, max_m);
+    auto kern = k_plain_batched<float, kPlainRowsPerLane>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 32 * warps, smem, st>>>(reinterpret_cast<const PlainParams<float> *>(reqs_dev), items, n_items,
+                                         counter);
+    return cudaGetLastError();
+}
+
+template size_t plain_smem_bytes<float>(int, int);
+template size_t plain_smem_bytes<double>(int, int);
+template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *, const double *,
+                                         const float *, int64_t, const float4 *, const double *, const Span *,
+                                         const int32_t *, Partial<float> *, cudaStream_t);
+template cudaError_t launch_plain<double>(const PlainLaunch &, const double *, int64_t, const dvec4 *,
+                                          const double *, const double *, int64_t, const dvec4 *, const double *,
+                                          const Span *, const int32_t *, Partial<double> *, cudaStream_t);
+
+}  // namespace mpd

@@ -1,0 +1,1093 @@
+// Host runtime of libmpdict: the C ABI of include/mpdict.h.
+//
+//   * mp_ctx   -- one device, one stream for synchronous calls, a growable
+//                 workspace, the resident dictionaries and the serving
+//                 scheduler.
+//   * mp_dict  -- dictionary samples resident in HBM plus, per window length
+//                 m, the cached window statistics (kernel K1), the spans of
+//                 valid windows (windows never cross a segment, Def. 8) and
+//                 the two special windows used by the constant-window rule.
+//   * join     -- K1 on the query, then the join form (plain K2 or tensor K3),
+//                 then K4 (reduction over column groups + exact distance of
+//                 the picked pair), all enqueued on one stream.
+//   * serving  -- mp_submit queues a request; a scheduler thread admits
+//                 requests while slots and the memory budget allow, stages
+//                 them, and runs every admitted request's join work in one
+//                 persistent batched launch; completion is detected with
+//                 events, so batches overlap on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/mpdict.h"
+#include "mp_internal.cuh"
+#include "mp_tc.cuh"
+
+using namespace mpd;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) return fail(MP_E_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
+                                           __FILE__, __LINE__);                                     \
+    } while (0)
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+struct DictStats {
+    int32_t m = 0;
+    double *mean = nullptr;     // per window position of the concatenated buffer
+    double *invstd = nullptr;
+    uint8_t *cflag = nullptr;
+    void *rs = nullptr;         // float4 / dvec4 recurrence terms
+    std::vector<Span> seg_spans;  // one span per segment with at least one window
+    int64_t n_windows = 0;        // W
+    int64_t g_const = -1, g_first = -1;
+    // column grouping cache: n_groups -> (device spans, device group_start)
+    struct Grouping {
+        Span *spans = nullptr;
+        int32_t *group_start = nullptr;
+        int32_t n_spans = 0;
+    };
+    std::map<int, Grouping> groupings;
+    void *tc_pack = nullptr;   // tensor-core operand cache (owned by the tc module)
+};
+
+struct mp_dict {
+    mp_ctx *ctx = nullptr;
+    int32_t dtype = MP_F32;
+    int64_t nb = 0;
+    std::vector<int64_t> offs;
+    void *d_samples = nullptr;
+    std::map<int, std::unique_ptr<DictStats>> stats;
+    std::atomic<int> refs{0};
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    mp_dict *dict = nullptr;
+    int32_t dtype = MP_F32;
+    int64_t n = 0;
+    int32_t m = 0;
+    std::vector<unsigned char> query;  // host copy
+    double *out_dist = nullptr;
+    int64_t *out_idx = nullptr;
+    double t_submit = 0, t_done = 0;
+    int32_t state = MP_PENDING;
+    // device side
+    size_t bytes = 0;
+    void *dmem = nullptr;
+};
+
+struct Batch {
+    std::vector<std::shared_ptr<Request>> reqs;
+    cudaEvent_t done = nullptr;
+    cudaStream_t stream = nullptr;
+    void *dmem = nullptr;  // batch-level buffers (request table, items, counter)
+};
+
+struct mp_ctx {
+    int32_t device = 0;
+    int32_t sm_count = 0;
+    int32_t kernel = MP_KERNEL_AUTO;
+    mp_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::mutex mu;  // serialises synchronous calls and dictionary changes
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    std::set<mp_dict *> dicts;
+
+    // serving
+    std::mutex smu;
+    std::condition_variable scv;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
+    std::vector<Batch> inflight;
+    size_t mem_budget = 0, mem_used = 0;
+    int32_t n_inflight_reqs = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    cudaStream_t sstreams[2] = {nullptr, nullptr};
+    int next_stream = 0;
+
+    // tracing
+    bool profiling = false;
+    struct Mark {
+        int phase;
+        cudaEvent_t t0, t1;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[MP_PHASE_COUNT] = {0, 0, 0};
+    int64_t prof_n[MP_PHASE_COUNT] = {0, 0, 0};
+};
+
+// Event pair around one phase of a join (no-op unless tracing is on).
+struct PhaseTimer {
+    mp_ctx *ctx;
+    int phase;
+    cudaStream_t st;
+    cudaEvent_t t0 = nullptr;
+    static cudaEvent_t take(mp_ctx *c)
+    {
+        if (!c->ev_pool.empty()) {
+            cudaEvent_t e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    PhaseTimer(mp_ctx *c, int ph, cudaStream_t s) : ctx(c), phase(ph), st(s)
+    {
+        if (ctx->profiling) {
+            t0 = take(ctx);
+            cudaEventRecord(t0, st);
+        }
+    }
+    ~PhaseTimer()
+    {
+        if (t0) {
+            cudaEvent_t t1 = take(ctx);
+            cudaEventRecord(t1, st);
+            ctx->marks.push_back(mp_ctx::Mark{phase, t0, t1});
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int dtype_size(int32_t dtype) { return dtype == MP_F64 ? 8 : 4; }
+
+static bool host_all_finite(const void *x, int32_t dtype, int64_t n)
+{
+    if (dtype == MP_F64) {
+        const double *p = (const double *)x;
+        for (int64_t i = 0; i < n; ++i)
+            if (!isfinite(p[i])) return false;
+    } else {
+        const float *p = (const float *)x;
+        for (int64_t i = 0; i < n; ++i)
+            if (!isfinite(p[i])) return false;
+    }
+    return true;
+}
+
+static int check_join_args(mp_ctx *ctx, const mp_dict *dict, const void *q, int32_t dtype, int64_t n, int32_t m)
+{
+    if (!ctx || !dict || !q) return fail(MP_E_ARG, "null argument");
+    if (dtype != MP_F32 && dtype != MP_F64) return fail(MP_E_ARG, "unknown dtype %d", dtype);
+    if (dtype != dict->dtype) return fail(MP_E_ARG, "query dtype differs from the dictionary's");
+    if (m < 2 || m > 8192) return fail(MP_E_ARG, "m=%d outside [2, 8192]", m);
+    if (n < m) return fail(MP_E_ARG, "query length %lld shorter than m=%d", (long long)n, m);
+    if (n >= ((int64_t)1 << 40)) return fail(MP_E_ARG, "query too long");
+    if (dict->ctx != ctx) return fail(MP_E_ARG, "dictionary belongs to another context");
+    return MP_OK;
+}
+
+// Grow the context workspace to at least `bytes` (synchronises the stream).
+static int ensure_ws(mp_ctx *ctx, size_t bytes)
+{
+    if (ctx->ws_size >= bytes) return MP_OK;
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+    size_t sz = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc(&ctx->ws, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MP_E_NOMEM, "workspace of %zu bytes", sz);
+    }
+    ctx->ws_size = sz;
+    return MP_OK;
+}
+
+// Statistics of the dictionary for window length m (computed on first use).
+static int get_stats(mp_ctx *ctx, mp_dict *d, int32_t m, DictStats **out)
+{
+    auto it = d->stats.find(m);
+    if (it != d->stats.end()) {
+        *out = it->second.get();
+        return MP_OK;
+    }
+    std::unique_ptr<DictStats> s(new DictStats());
+    s->m = m;
+    for (size_t k = 0; k + 1 < d->offs.size(); ++k) {
+        const int64_t L = d->offs[k + 1] - d->offs[k];
+        if (L >= m) {
+            Span sp;
+            sp.g0 = d->offs[k];
+            sp.ncols = (int32_t)(L - m + 1);
+            sp.pad = 0;
+            s->seg_spans.push_back(sp);
+            s->n_windows += sp.ncols;
+        }
+    }
+    const int64_t npos = d->nb - m + 1;
+    if (npos > 0) {
+        const size_t rs_sz = (size_t)npos * (d->dtype == MP_F64 ? sizeof(dvec4) : sizeof(float4));
+        if (cudaMalloc(&s->mean, npos * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&s->invstd, npos * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&s->cflag, npos) != cudaSuccess || cudaMalloc(&s->rs, rs_sz) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(s->mean);
+            cudaFree(s->invstd);
+            cudaFree(s->cflag);
+            cudaFree(s->rs);
+            return fail(MP_E_NOMEM, "dictionary statistics for m=%d", m);
+        }
+        cudaError_t e;
+        if (d->dtype == MP_F64)
+            e = launch_window_stats<double>((const double *)d->d_samples, d->nb, m, s->mean, s->invstd, s->cflag,
+                                            (dvec4 *)s->rs, ctx->stream);
+        else
+            e = launch_window_stats<float>((const float *)d->d_samples, d->nb, m, s->mean, s->invstd, s->cflag,
+                                           (float4 *)s->rs, ctx->stream);
+        CUDA_TRY(e);
+        if (!s->seg_spans.empty()) {
+            Span *dsp = nullptr;
+            int64_t *dsv = nullptr;
+            CUDA_TRY(cudaMalloc(&dsp, s->seg_spans.size() * sizeof(Span)));
+            CUDA_TRY(cudaMalloc(&dsv, 2 * sizeof(int64_t)));
+            CUDA_TRY(cudaMemcpyAsync(dsp, s->seg_spans.data(), s->seg_spans.size() * sizeof(Span),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+            CUDA_TRY(cudaMemsetAsync(dsv, 0xFF, 2 * sizeof(int64_t), ctx->stream));
+            CUDA_TRY(launch_dict_specials(dsp, (int32_t)s->seg_spans.size(), s->cflag, dsv, ctx->stream));
+            int64_t hv[2];
+            CUDA_TRY(cudaMemcpyAsync(hv, dsv, sizeof hv, cudaMemcpyDeviceToHost, ctx->stream));
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            cudaFree(dsp);
+            cudaFree(dsv);
+            s->g_const = hv[0];
+            s->g_first = hv[1];
+        }
+    }
+    *out = s.get();
+    d->stats[m] = std::move(s);
+    return MP_OK;
+}
+
+// Cut the dictionary's valid windows into n_groups column groups of nearly
+// equal size; a span never crosses a segment. Cached per n_groups.
+static int get_grouping(mp_ctx *ctx, DictStats *s, int n_groups, DictStats::Grouping **out)
+{
+    auto it = s->groupings.find(n_groups);
+    if (it != s->groupings.end()) {
+        *out = &it->second;
+        return MP_OK;
+    }
+    std::vector<Span> spans;
+    std::vector<int32_t> gstart(1, 0);
+    const int64_t target = (s->n_windows + n_groups - 1) / n_groups;
+    int64_t fill = 0;
+    for (const Span &seg : s->seg_spans) {
+        int64_t off = 0;
+        while (off < seg.ncols) {
+            const int64_t take = std::min<int64_t>(seg.ncols - off, target - fill);
+            Span sp;
+            sp.g0 = seg.g0 + off;
+            sp.ncols = (int32_t)take;
+            sp.pad = 0;
+            spans.push_back(sp);
+            off += take;
+            fill += take;
+            if (fill == target) {
+                gstart.push_back((int32_t)spans.size());
+                fill = 0;
+            }
+        }
+    }
+    if (fill > 0) gstart.push_back((int32_t)spans.size());
+    while ((int)gstart.size() < n_groups + 1) gstart.push_back((int32_t)spans.size());
+    DictStats::Grouping g;
+    g.n_spans = (int32_t)spans.size();
+    CUDA_TRY(cudaMalloc(&g.spans, std::max<size_t>(1, spans.size()) * sizeof(Span)));
+    CUDA_TRY(cudaMalloc(&g.group_start, gstart.size() * sizeof(int32_t)));
+    if (!spans.empty())
+        CUDA_TRY(cudaMemcpyAsync(g.spans, spans.data(), spans.size() * sizeof(Span), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(g.group_start, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    s->groupings[n_groups] = g;
+    *out = &s->groupings[n_groups];
+    return MP_OK;
+}
+
+static void free_stats(DictStats *s)
+{
+    cudaFree(s->mean);
+    cudaFree(s->invstd);
+    cudaFree(s->cflag);
+    cudaFree(s->rs);
+    for (auto &kv : s->groupings) {
+        cudaFree(kv.second.spans);
+        cudaFree(kv.second.group_start);
+    }
+    tc_free_pack(s->tc_pack);
+}
+
+// Launch geometry of the plain kernel for nq rows and W columns.
+struct Geometry {
+    int warps, n_row_blocks, n_groups;
+};
+
+static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int rows_per_lane)
+{
+    Geometry g;
+    const int64_t rows_warp = 32 * rows_per_lane;
+    g.warps = nq <= rows_warp ? 1 : (nq <= 2 * rows_warp ? 2 : 4);
+    const int64_t rows_cta = rows_warp * g.warps;
+    g.n_row_blocks = (int)((nq + rows_cta - 1) / rows_cta);
+    // Enough CTAs for several waves, while keeping each column group long
+    // enough (>= 4096 windows) to amortise its seeds.
+    const int64_t want = (int64_t)ctx->sm_count * 12;
+    int64_t ng = (want + g.n_row_blocks - 1) / g.n_row_blocks;
+    const int64_t max_g = std::max<int64_t>(1, W / 4096);
+    ng = std::max<int64_t>(1, std::min(ng, max_g));
+    g.n_groups = (int)ng;
+    return g;
+}
+
+// Workspace layout of one join.
+struct JoinWs {
+    size_t off_mean, off_inv, off_cflag, off_rs, off_part, total;
+};
+
+static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front)
+{
+    JoinWs w;
+    const size_t e = dtype == MP_F64 ? 8 : 4;
+    size_t o = align_up(extra_front, 256);
+    w.off_mean = o;
+    o = align_up(o + nq * 8, 256);
+    w.off_inv = o;
+    o = align_up(o + nq * 8, 256);
+    w.off_cflag = o;
+    o = align_up(o + nq, 256);
+    w.off_rs = o;
+    o = align_up(o + nq * 4 * e, 256);
+    w.off_part = o;
+    o = align_up(o + (size_t)n_groups * nq * (e == 8 ? sizeof(Partial<double>) : sizeof(Partial<float>)), 256);
+    w.total = o;
+    return w;
+}
+
+// The join on device buffers; `base` is a device workspace of at least
+// join_ws_layout(...).total bytes. Everything is enqueued on `st`.
+static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, int32_t dtype, int64_t n, int32_t m,
+                       double *d_dist, int64_t *d_idx, cudaStream_t st, unsigned char *base, int kernel)
+{
+    const int64_t nq = n - m + 1;
+    if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
+    const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
+    const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl);
+    JoinWs w = join_ws_layout(nq, dtype, geo.n_groups, 0);
+    double *mean_a = (double *)(base + w.off_mean);
+    double *inv_a = (double *)(base + w.off_inv);
+    uint8_t *cf_a = (uint8_t *)(base + w.off_cflag);
+    DictStats::Grouping *gr = nullptr;
+    int rc = get_grouping(ctx, s, geo.n_groups, &gr);
+    if (rc) return rc;
+    PlainLaunch L;
+    L.nq = nq;
+    L.m = m;
+    L.n_row_blocks = geo.n_row_blocks;
+    L.n_groups = geo.n_groups;
+    L.warps = geo.warps;
+    if (dtype == MP_F64) {
+        const double *a = (const double *)dq;
+        dvec4 *rs_a = (dvec4 *)(base + w.off_rs);
+        Partial<double> *part = (Partial<double> *)(base + w.off_part);
+        {
+            PhaseTimer t(ctx, MP_PHASE_STATS, st);
+            CUDA_TRY(launch_window_stats<double>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
+        }
+        {
+            PhaseTimer t(ctx, MP_PHASE_JOIN, st);
+            CUDA_TRY(launch_plain<double>(L, a, n, rs_a, mean_a, (const double *)d->d_samples, d->nb,
+                                          (const dvec4 *)s->rs, s->mean, gr->spans, gr->group_start, part, st));
+        }
+        {
+            PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
+            CUDA_TRY(launch_finalize<double>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a,
+                                             (const double *)d->d_samples, s->mean, s->invstd, s->g_const,
+                                             s->g_first, d_dist, d_idx, st));
+        }
+    } else {
+        const float *a = (const float *)dq;
+        float4 *rs_a = (float4 *)(base + w.off_rs);
+        {
+            PhaseTimer t(ctx, MP_PHASE_STATS, st);
+            CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
+        }
+        if (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32) {
+            return tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
+                           (const float *)d->d_samples, d->nb, s->seg_spans.data(), (int32_t)s->seg_spans.size(),
+                           s->mean, s->invstd, s->rs, a, n, m, mean_a, inv_a, cf_a, s->g_const, s->g_first, d_dist,
+                           d_idx, st, fail);
+        }
+        Partial<float> *part = (Partial<float> *)(base + w.off_part);
+        {
+            PhaseTimer t(ctx, MP_PHASE_JOIN, st);
+            CUDA_TRY(launch_plain<float>(L, a, n, rs_a, mean_a, (const float *)d->d_samples, d->nb,
+                                         (const float4 *)s->rs, s->mean, gr->spans, gr->group_start, part, st));
+        }
+        {
+            PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
+            CUDA_TRY(launch_finalize<float>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a,
+                                            (const float *)d->d_samples, s->mean, s->invstd, s->g_const,
+                                            s->g_first, d_dist, d_idx, st));
+        }
+    }
+    return MP_OK;
+}
+
+static size_t join_ws_bytes(const mp_ctx *ctx, const DictStats *s, int32_t dtype, int64_t n, int32_t m)
+{
+    const int64_t nq = n - m + 1;
+    const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
+    const Geometry geo = plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl);
+    return join_ws_layout(nq, dtype, geo.n_groups, 0).total;
+}
+
+static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s)
+{
+    if (dtype == MP_F64) return MP_KERNEL_PLAIN;
+    int k = ctx->kernel;
+    if (k == MP_KERNEL_AUTO) k = tc_autotune_choice(m, s->n_windows);
+    if ((k == MP_KERNEL_TC_BF16X3 || k == MP_KERNEL_TC_TF32) && !tc_supported(m)) k = MP_KERNEL_PLAIN;
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// serving scheduler
+// ---------------------------------------------------------------------------
+static size_t request_bytes(const mp_ctx *ctx, const Request &r, const DictStats *s)
+{
+    const int64_t nq = r.n - r.m + 1;
+    return align_up((size_t)r.n * dtype_size(r.dtype), 256) + align_up(nq * 16, 256) +
+           join_ws_bytes(ctx, s, r.dtype, r.n, r.m);
+}
+
+static void finish_request(mp_ctx *ctx, Request &r, int32_t state, cudaStream_t st)
+{
+    r.t_done = now_s();
+    r.state = state;
+    // stream-ordered free: no device-wide synchronisation in the serving loop
+    if (r.dmem) cudaFreeAsync(r.dmem, st);
+    r.dmem = nullptr;
+    ctx->mem_used -= r.bytes;
+    ctx->n_inflight_reqs -= 1;
+    r.dict->refs.fetch_sub(1);
+}
+
+// Stage and launch one batch of admitted requests on stream `st`. Called by
+// the scheduler thread with ctx->mu held (dictionary statistics may be built).
+static int launch_batch(mp_ctx *ctx, Batch &bt)
+{
+    cudaStream_t st = bt.stream;
+    std::vector<PlainRequest> preqs;
+    std::vector<BatchItem> items;
+    int max_m = 0;
+    struct Post {
+        Request *r;
+        DictStats *s;
+        int n_groups;
+        unsigned char *base;
+        float *a;
+        double *dist;
+        int64_t *idx;
+    };
+    std::vector<Post> post;
+    for (auto &rp : bt.reqs) {
+        Request &r = *rp;
+        DictStats *s = nullptr;
+        int rc = get_stats(ctx, r.dict, r.m, &s);
+        if (rc) return rc;
+        const int64_t nq = r.n - r.m + 1;
+        unsigned char *p = (unsigned char *)r.dmem;
+        unsigned char *q = p;
+        p += align_up((size_t)r.n * dtype_size(r.dtype), 256);
+        double *dist = (double *)p;
+        int64_t *idx = (int64_t *)(p + nq * 8);
+        p += align_up(nq * 16, 256);
+        CUDA_TRY(cudaMemcpyAsync(q, r.query.data(), (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
+        if (s->n_windows == 0 || r.dtype == MP_F64 || resolve_kernel(ctx, r.dtype, r.m, s) != MP_KERNEL_PLAIN) {
+            // Requests that do not fit the batched FP32 plain kernel run alone.
+            if (s->n_windows == 0) {
+                std::vector<double> inf(nq, INFINITY);
+                std::vector<int64_t> neg(nq, -1);
+                memcpy(r.out_dist, inf.data(), nq * 8);
+                memcpy(r.out_idx, neg.data(), nq * 8);
+                continue;
+            }
+            rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p,
+                             resolve_kernel(ctx, r.dtype, r.m, s));
+            if (rc) return rc;
+            CUDA_TRY(cudaMemcpyAsync(r.out_dist, dist, nq * 8, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(r.out_idx, idx, nq * 8, cudaMemcpyDeviceToHost, st));
+            continue;
+        }
+        const Geometry geo0 = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane);
+        Geometry geo = geo0;
+        geo.warps = 4;
+        geo.n_row_blocks = (int)((nq + 4 * 32 * kPlainRowsPerLane - 1) / (4 * 32 * kPlainRowsPerLane));
+        DictStats::Grouping *gr = nullptr;
+        rc = get_grouping(ctx, s, geo.n_groups, &gr);
+        if (rc) return rc;
+        JoinWs w = join_ws_layout(nq, r.dtype, geo.n_groups, 0);
+        const float *a = (const float *)q;
+        double *mean_a = (double *)(p + w.off_mean);
+        double *inv_a = (double *)(p + w.off_inv);
+        uint8_t *cf_a = (uint8_t *)(p + w.off_cflag);
+        float4 *rs_a = (float4 *)(p + w.off_rs);
+        Partial<float> *part = (Partial<float> *)(p + w.off_part);
+        CUDA_TRY(launch_window_stats<float>(a, r.n, r.m, mean_a, inv_a, cf_a, rs_a, st));
+        PlainRequest pr;
+        pr.a = a;
+        pr.na = r.n;
+        pr.nq = nq;
+        pr.m = r.m;
+        pr.n_groups = geo.n_groups;
+        pr.rs_a = rs_a;
+        pr.mean_a = mean_a;
+        pr.b = (const float *)r.dict->d_samples;
+        pr.nb = r.dict->nb;
+        pr.rs_b = (const float4 *)s->rs;
+        pr.mean_b = s->mean;
+        pr.spans = gr->spans;
+        pr.group_start = gr->group_start;
+        pr.part = part;
+        const int ridx = (int)preqs.size();
+        preqs.push_back(pr);
+        for (int64_t rb = 0; rb < geo.n_row_blocks; ++rb)
+            for (int g = 0; g < geo.n_groups; ++g) items.push_back(BatchItem{ridx, g, rb});
+        max_m = std::max(max_m, (int)r.m);
+        post.push_back(Post{&r, s, geo.n_groups, p, (float *)a, dist, idx});
+    }
+    if (!preqs.empty()) {
+        const size_t sz_req = align_up(preqs.size() * sizeof(PlainRequest), 256);
+        const size_t sz_items = align_up(items.size() * sizeof(BatchItem), 256);
+        if (cudaMallocAsync(&bt.dmem, sz_req + sz_items + 256, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MP_E_NOMEM, "batch tables");
+        }
+        unsigned char *bp = (unsigned char *)bt.dmem;
+        CUDA_TRY(cudaMemcpyAsync(bp, preqs.data(), preqs.size() * sizeof(PlainRequest), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(bp + sz_req, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                                 st));
+        int32_t *counter = (int32_t *)(bp + sz_req + sz_items);
+        CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+        const int grid = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)ctx->sm_count * 2);
+        CUDA_TRY(launch_plain_batched((const PlainRequest *)bp, (const BatchItem *)(bp + sz_req),
+                                      (int32_t)items.size(), counter, 4, max_m, grid, st));
+        for (Post &ps : post) {
+            Request &r = *ps.r;
+            const int64_t nq = r.n - r.m + 1;
+            JoinWs w = join_ws_layout(nq, r.dtype, ps.n_groups, 0);
+            CUDA_TRY(launch_finalize<float>(nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part),
+                                            ps.a, (const double *)(ps.base + w.off_mean),
+                                            (const double *)(ps.base + w.off_inv),
+                                            (const uint8_t *)(ps.base + w.off_cflag),
+                                            (const float *)r.dict->d_samples, ps.s->mean, ps.s->invstd,
+                                            ps.s->g_const, ps.s->g_first, ps.dist, ps.idx, st));
+            CUDA_TRY(cudaMemcpyAsync(r.out_dist, ps.dist, nq * 8, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(r.out_idx, ps.idx, nq * 8, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(bt.done, st));
+    return MP_OK;
+}
+
+static void scheduler_loop(mp_ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->smu);
+    while (true) {
+        // 1. retire finished batches
+        for (size_t k = 0; k < ctx->inflight.size();) {
+            Batch &bt = ctx->inflight[k];
+            cudaError_t q = cudaEventQuery(bt.done);
+            if (q == cudaErrorNotReady) {
+                ++k;
+                continue;
+            }
+            const int32_t state = (q == cudaSuccess) ? MP_DONE : MP_FAILED;
+            if (q != cudaSuccess) cudaGetLastError();
+            for (auto &r : bt.reqs) finish_request(ctx, *r, state, bt.stream);
+            cudaEventDestroy(bt.done);
+            if (bt.dmem) cudaFreeAsync(bt.dmem, bt.stream);
+            ctx->inflight.erase(ctx->inflight.begin() + k);
+        }
+        if (ctx->stop && ctx->pending.empty() && ctx->inflight.empty()) break;
+        // 2. admit: FIFO, while a slot and the memory budget allow
+        Batch bt;
+        bt.stream = ctx->sstreams[ctx->next_stream];
+        while (!ctx->pending.empty() && (int)bt.reqs.size() < ctx->cfg.max_batch &&
+               ctx->n_inflight_reqs < ctx->cfg.max_inflight) {
+            std::shared_ptr<Request> r = ctx->pending.front();
+            if (ctx->mem_used + r->bytes > ctx->mem_budget && ctx->n_inflight_reqs > 0) break;
+            ctx->pending.pop_front();
+            if (cudaMallocAsync(&r->dmem, r->bytes, bt.stream) != cudaSuccess) {
+                cudaGetLastError();
+                r->t_done = now_s();
+                r->state = MP_FAILED;
+                r->dict->refs.fetch_sub(1);
+                continue;
+            }
+            ctx->mem_used += r->bytes;
+            ctx->n_inflight_reqs += 1;
+            bt.reqs.push_back(r);
+        }
+        if (!bt.reqs.empty()) {
+            ctx->next_stream ^= 1;
+            cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
+            lk.unlock();
+            int rc;
+            {
+                std::lock_guard<std::mutex> g(ctx->mu);
+                rc = launch_batch(ctx, bt);
+            }
+            lk.lock();
+            if (rc != MP_OK) {
+                cudaStreamSynchronize(bt.stream);
+                for (auto &r : bt.reqs) finish_request(ctx, *r, MP_FAILED, bt.stream);
+                cudaEventDestroy(bt.done);
+                if (bt.dmem) cudaFreeAsync(bt.dmem, bt.stream);
+            } else {
+                ctx->inflight.push_back(std::move(bt));
+            }
+            continue;
+        }
+        // 3. nothing to admit: wait for a submission or poll the device
+        if (ctx->inflight.empty())
+            ctx->scv.wait(lk, [&] { return ctx->stop || !ctx->pending.empty(); });
+        else
+            ctx->scv.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *mp_last_error(void) { return g_err.c_str(); }
+
+int mp_config_default(mp_config *cfg)
+{
+    if (!cfg) return fail(MP_E_ARG, "null cfg");
+    memset(cfg, 0, sizeof *cfg);
+    cfg->device = 0;
+    cfg->kernel = MP_KERNEL_AUTO;
+    cfg->max_inflight = 8;
+    cfg->max_batch = 64;
+    cfg->mem_budget = 0;
+    cfg->tune_cache = nullptr;
+    return MP_OK;
+}
+
+int mp_init(mp_ctx **out, const mp_config *cfg_in)
+{
+    g_err.clear();
+    if (!out) return fail(MP_E_ARG, "null ctx pointer");
+    mp_config cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        mp_config_default(&cfg);
+    if (cfg.kernel < MP_KERNEL_AUTO || cfg.kernel > MP_KERNEL_TC_TF32) return fail(MP_E_ARG, "unknown kernel");
+    if (cfg.max_inflight <= 0) cfg.max_inflight = 8;
+    if (cfg.max_batch <= 0) cfg.max_batch = 64;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (cfg.device < 0 || cfg.device >= ndev) return fail(MP_E_ARG, "device %d of %d", cfg.device, ndev);
+    CUDA_TRY(cudaSetDevice(cfg.device));
+    std::unique_ptr<mp_ctx> c(new mp_ctx());
+    c->device = cfg.device;
+    c->cfg = cfg;
+    c->kernel = cfg.kernel;
+    CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg.device));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[0], cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[1], cudaStreamNonBlocking));
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    c->mem_budget = cfg.mem_budget ? cfg.mem_budget : fr / 2;
+    if (cfg.tune_cache) tc_load_tune_cache(cfg.tune_cache);
+    mp_ctx *p = c.release();
+    p->worker = std::thread(scheduler_loop, p);
+    *out = p;
+    return MP_OK;
+}
+
+int mp_shutdown(mp_ctx *ctx)
+{
+    g_err.clear();
+    if (!ctx) return fail(MP_E_ARG, "null ctx");
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->stop = true;
+    }
+    ctx->scv.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (mp_dict *d : ctx->dicts) {
+        for (auto &kv : d->stats) free_stats(kv.second.get());
+        cudaFree(d->d_samples);
+        delete d;
+    }
+    if (ctx->ws) cudaFree(ctx->ws);
+    for (auto &mk : ctx->marks) {
+        cudaEventDestroy(mk.t0);
+        cudaEventDestroy(mk.t1);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    cudaStreamDestroy(ctx->stream);
+    cudaStreamDestroy(ctx->sstreams[0]);
+    cudaStreamDestroy(ctx->sstreams[1]);
+    delete ctx;
+    return MP_OK;
+}
+
+int mp_set_kernel(mp_ctx *ctx, int32_t kernel)
+{
+    g_err.clear();
+    if (!ctx) return fail(MP_E_ARG, "null ctx");
+    if (kernel < MP_KERNEL_AUTO || kernel > MP_KERNEL_TC_TF32) return fail(MP_E_ARG, "unknown kernel %d", kernel);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->kernel = kernel;
+    return MP_OK;
+}
+
+int mp_dict_load(mp_ctx *ctx, const void *samples, int32_t dtype, const int64_t *offs, int32_t n_segments,
+                 const int32_t *ms, int32_t n_ms, mp_dict **out)
+{
+    g_err.clear();
+    if (!ctx || !offs || !out || n_segments < 0) return fail(MP_E_ARG, "null argument");
+    if (dtype != MP_F32 && dtype != MP_F64) return fail(MP_E_ARG, "unknown dtype %d", dtype);
+    if (offs[0] != 0) return fail(MP_E_ARG, "seg_offsets[0] must be 0");
+    for (int32_t s = 0; s < n_segments; ++s)
+        if (offs[s + 1] < offs[s]) return fail(MP_E_ARG, "seg_offsets not sorted at %d", s);
+    const int64_t nb = offs[n_segments];
+    if (nb >= ((int64_t)1 << 31)) return fail(MP_E_ARG, "dictionary larger than 2^31 samples");
+    if (nb > 0 && !samples) return fail(MP_E_ARG, "null samples");
+    if (!host_all_finite(samples, dtype, nb)) return fail(MP_E_ARG, "dictionary has NaN or Inf samples");
+    if (n_ms < 0 || (n_ms > 0 && !ms)) return fail(MP_E_ARG, "bad ms");
+    for (int32_t k = 0; k < n_ms; ++k)
+        if (ms[k] < 2 || ms[k] > 8192) return fail(MP_E_ARG, "m=%d outside [2, 8192]", ms[k]);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::unique_ptr<mp_dict> d(new mp_dict());
+    d->ctx = ctx;
+    d->dtype = dtype;
+    d->nb = nb;
+    d->offs.assign(offs, offs + n_segments + 1);
+    const size_t bytes = std::max<int64_t>(nb, 1) * dtype_size(dtype) + 64;
+    if (cudaMalloc(&d->d_samples, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MP_E_NOMEM, "dictionary of %zu bytes", bytes);
+    }
+    CUDA_TRY(cudaMemsetAsync(d->d_samples, 0, bytes, ctx->stream));
+    if (nb > 0)
+        CUDA_TRY(cudaMemcpyAsync(d->d_samples, samples, nb * dtype_size(dtype), cudaMemcpyHostToDevice, ctx->stream));
+    for (int32_t k = 0; k < n_ms; ++k) {
+        DictStats *s;
+        int rc = get_stats(ctx, d.get(), ms[k], &s);
+        if (rc) {
+            for (auto &kv : d->stats) free_stats(kv.second.get());
+            cudaFree(d->d_samples);
+            return rc;
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *out = d.get();
+    ctx->dicts.insert(d.release());
+    return MP_OK;
+}
+
+int mp_dict_free(mp_ctx *ctx, mp_dict *d)
+{
+    g_err.clear();
+    if (!ctx || !d) return fail(MP_E_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->dicts.count(d)) return fail(MP_E_ARG, "unknown dictionary");
+    if (d->refs.load() > 0) return fail(MP_E_BUSY, "dictionary referenced by %d requests in flight", d->refs.load());
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : d->stats) free_stats(kv.second.get());
+    cudaFree(d->d_samples);
+    ctx->dicts.erase(d);
+    delete d;
+    return MP_OK;
+}
+
+int mp_dict_windows(const mp_dict *d, int32_t m, int64_t *n_windows)
+{
+    g_err.clear();
+    if (!d || !n_windows || m < 1) return fail(MP_E_ARG, "bad argument");
+    int64_t w = 0;
+    for (size_t k = 0; k + 1 < d->offs.size(); ++k) w += std::max<int64_t>(0, d->offs[k + 1] - d->offs[k] - m + 1);
+    *n_windows = w;
+    return MP_OK;
+}
+
+int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int32_t dtype, int64_t n, int32_t m,
+                      double *d_dist, int64_t *d_idx, void *stream)
+{
+    g_err.clear();
+    int rc = check_join_args(ctx, dict, d_query, dtype, n, m);
+    if (rc) return rc;
+    if (!d_dist || !d_idx) return fail(MP_E_ARG, "null output");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    mp_dict *d = const_cast<mp_dict *>(dict);
+    DictStats *s;
+    rc = get_stats(ctx, d, m, &s);
+    if (rc) return rc;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const int64_t nq = n - m + 1;
+    if (s->n_windows == 0) {
+        // No dictionary window: +inf and index -1 (Algorithm 2's initial value).
+        std::vector<double> inf(nq, INFINITY);
+        std::vector<int64_t> neg(nq, -1);
+        CUDA_TRY(cudaMemcpyAsync(d_dist, inf.data(), nq * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(d_idx, neg.data(), nq * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return MP_OK;
+    }
+    rc = ensure_ws(ctx, join_ws_bytes(ctx, s, dtype, n, m));
+    if (rc) return rc;
+    if (st != ctx->stream) {
+        // the workspace may still be in use by earlier work on the context stream
+        cudaEvent_t ev;
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(ev, ctx->stream));
+        CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    rc = join_device(ctx, d, s, d_query, dtype, n, m, d_dist, d_idx, st, (unsigned char *)ctx->ws,
+                     resolve_kernel(ctx, dtype, m, s));
+    if (rc) return rc;
+    if (st != ctx->stream) {
+        cudaEvent_t ev;
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(ev, st));
+        CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    return MP_OK;
+}
+
+int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+               double *out_dist, int64_t *out_idx)
+{
+    g_err.clear();
+    int rc = check_join_args(ctx, dict, query, dtype, n, m);
+    if (rc) return rc;
+    if (!out_dist || !out_idx) return fail(MP_E_ARG, "null output");
+    if (!host_all_finite(query, dtype, n)) return fail(MP_E_ARG, "query has NaN or Inf samples");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    mp_dict *d = const_cast<mp_dict *>(dict);
+    DictStats *s;
+    rc = get_stats(ctx, d, m, &s);
+    if (rc) return rc;
+    const int64_t nq = n - m + 1;
+    if (s->n_windows == 0) {
+        for (int64_t i = 0; i < nq; ++i) {
+            out_dist[i] = INFINITY;
+            out_idx[i] = -1;
+        }
+        return MP_OK;
+    }
+    const size_t qbytes = align_up((size_t)n * dtype_size(dtype), 256);
+    const size_t obytes = align_up((size_t)nq * 8, 256);
+    const size_t jb = join_ws_bytes(ctx, s, dtype, n, m);
+    rc = ensure_ws(ctx, qbytes + 2 * obytes + jb);
+    if (rc) return rc;
+    unsigned char *base = (unsigned char *)ctx->ws;
+    void *dq = base;
+    double *dd = (double *)(base + qbytes);
+    int64_t *di = (int64_t *)(base + qbytes + obytes);
+    cudaStream_t st = ctx->stream;
+    CUDA_TRY(cudaMemcpyAsync(dq, query, (size_t)n * dtype_size(dtype), cudaMemcpyHostToDevice, st));
+    rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes,
+                     resolve_kernel(ctx, dtype, m, s));
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return MP_OK;
+}
+
+int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int32_t m, double *d_mean,
+                    double *d_invstd, uint8_t *d_const, void *stream)
+{
+    g_err.clear();
+    if (!ctx || !d_x || !d_mean || !d_invstd || !d_const) return fail(MP_E_ARG, "null argument");
+    if (dtype != MP_F32 && dtype != MP_F64) return fail(MP_E_ARG, "unknown dtype");
+    if (m < 2 || m > 8192 || n < m) return fail(MP_E_ARG, "bad n/m");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    if (dtype == MP_F64)
+        CUDA_TRY(launch_window_stats<double>((const double *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, st));
+    else
+        CUDA_TRY(launch_window_stats<float>((const float *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, st));
+    return MP_OK;
+}
+
+int mp_submit(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+              double *out_dist, int64_t *out_idx, uint64_t *ticket)
+{
+    g_err.clear();
+    int rc = check_join_args(ctx, dict, query, dtype, n, m);
+    if (rc) return rc;
+    if (!out_dist || !out_idx || !ticket) return fail(MP_E_ARG, "null output");
+    if (!host_all_finite(query, dtype, n)) return fail(MP_E_ARG, "query has NaN or Inf samples");
+    mp_dict *d = const_cast<mp_dict *>(dict);
+    auto r = std::make_shared<Request>();
+    r->dict = d;
+    r->dtype = dtype;
+    r->n = n;
+    r->m = m;
+    r->query.assign((const unsigned char *)query, (const unsigned char *)query + (size_t)n * dtype_size(dtype));
+    r->out_dist = out_dist;
+    r->out_idx = out_idx;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        CUDA_TRY(cudaSetDevice(ctx->device));
+        DictStats *s;
+        rc = get_stats(ctx, d, m, &s);
+        if (rc) return rc;
+        r->bytes = request_bytes(ctx, *r, s);
+    }
+    if (r->bytes > ctx->mem_budget) return fail(MP_E_NOMEM, "request needs %zu bytes, budget %zu", r->bytes,
+                                                 ctx->mem_budget);
+    d->refs.fetch_add(1);
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        r->ticket = ctx->next_ticket++;
+        r->t_submit = now_s();
+        ctx->tickets[r->ticket] = r;
+        ctx->pending.push_back(r);
+        *ticket = r->ticket;
+    }
+    ctx->scv.notify_all();
+    return MP_OK;
+}
+
+int mp_poll(mp_ctx *ctx, uint64_t ticket, int32_t *state, double *latency_s)
+{
+    g_err.clear();
+    if (!ctx || !state) return fail(MP_E_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(MP_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Request &r = *it->second;
+    *state = r.state;
+    if (r.state != MP_PENDING) {
+        if (latency_s) *latency_s = r.t_done - r.t_submit;
+        ctx->tickets.erase(it);
+    }
+    return MP_OK;
+}
+
+int mp_profile(mp_ctx *ctx, int32_t enable)
+{
+    g_err.clear();
+    if (!ctx) return fail(MP_E_ARG, "null ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->profiling = enable != 0;
+    return MP_OK;
+}
+
+int mp_profile_read(mp_ctx *ctx, double *ms, int64_t *launches, int32_t reset)
+{
+    g_err.clear();
+    if (!ctx) return fail(MP_E_ARG, "null ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    for (auto &mk : ctx->marks) {
+        CUDA_TRY(cudaEventSynchronize(mk.t1));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, mk.t0, mk.t1));
+        ctx->prof_ms[mk.phase] += t;
+        ctx->prof_n[mk.phase] += 1;
+        ctx->ev_pool.push_back(mk.t0);
+        ctx->ev_pool.push_back(mk.t1);
+    }
+    ctx->marks.clear();
+    for (int k = 0; k < MP_PHASE_COUNT; ++k) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->prof_n[k];
+        if (reset) {
+            ctx->prof_ms[k] = 0;
+            ctx->prof_n[k] = 0;
+        }
+    }
+    return MP_OK;
+}
+
+int mp_drain(mp_ctx *ctx, double timeout_s)
+{
+    g_err.clear();
+    if (!ctx) return fail(MP_E_ARG, "null ctx");
+    const double t_end = now_s() + timeout_s;
+    while (true) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->smu);
+            if (ctx->pending.empty() && ctx->inflight.empty()) return MP_OK;
+        }
+        if (now_s() > t_end) return fail(MP_E_TIMEOUT, "requests still in flight after %.3f s", timeout_s);
+        ctx->scv.notify_all();
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+"""GPU join through the C ABI against the CPU oracle (needs a GB300)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(mp):
+    c = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    yield c
+    mp.mp_shutdown(c)
+
+
+def join(mp, ctx, q, b, offs, m, ms=None):
+    d = mp.mp_dict_load(ctx, b, offs, [m] if ms is None else ms)
+    try:
+        return mp.mp_ab_join(ctx, d, q, m)
+    finally:
+        mp.mp_dict_free(ctx, d)
+
+
+def test_window_stats_match_oracle(mp, ctx):
+    import torch
+
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(3000).cumsum() + 5000.0, np.full(300, 7.25),
+                        rng.standard_normal(700)]).astype(np.float32)
+    for m in (3, 64, 257, 1024):
+        xt = torch.from_numpy(x).cuda()
+        nw = len(x) - m + 1
+        mean = torch.empty(nw, dtype=torch.float64, device="cuda")
+        inv = torch.empty_like(mean)
+        cst = torch.empty(nw, dtype=torch.uint8, device="cuda")
+        mp.mp_window_stats(ctx, xt.data_ptr(), mp.MP_F32, len(x), m, mean.data_ptr(), inv.data_ptr(), cst.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        om, osd, oc = oracle.window_stats(x, m)
+        assert np.array_equal(cst.cpu().numpy().astype(bool), oc)
+        np.testing.assert_allclose(mean.cpu().numpy(), om, rtol=1e-12, atol=1e-9)
+        inv_o = np.where(oc, 0.0, 1.0 / np.where(oc, 1.0, osd))
+        np.testing.assert_allclose(inv.cpu().numpy(), inv_o, rtol=1e-9)
+
+
+def test_fp64_random_walk_all_rows(mp, ctx):
+    w = synthetic.workload("rw_fp64_4k")
+    dist, idx = join(mp, ctx, w.query, w.dict_samples, w.offsets, w.m)
+    r = parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, atol=1e-8, gap=1e-6)
+    assert r["n_rows"] == 4033
+
+
+def test_fp32_ecg_all_rows_small(mp, ctx):
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 128)
+    dist, idx = join(mp, ctx, w.query, w.dict_samples, w.offsets, w.m)
+    parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, atol=1e-4)
+
+
+def test_fp32_ecg_full_size_sampled_rows(mp, ctx):
+    w = synthetic.workload("ecg_1m_m256")
+    dist, idx = join(mp, ctx, w.query, w.dict_samples, w.offsets, w.m)
+    assert len(dist) == 1048321
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.choice(len(dist), 768, replace=False), np.arange(0, 64),
+                                     np.arange(len(dist) - 64, len(dist)), [int(np.argmax(dist))]]))
+    parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, rows=rows, atol=1e-4)
+    # properties that hold at any size
+    assert np.all((dist >= 0) & (dist <= 2 * math.sqrt(w.m) + 1e-9))
+    assert np.all((idx >= 0) & (idx < len(w.dict_samples)))
+
+
+def test_transport_m512_sampled_rows(mp, ctx):
+    w = synthetic.workload("transport_4m_m512", scale=0.25)
+    dist, idx = join(mp, ctx, w.query, w.dict_samples, w.offsets, w.m)
+    rows = np.random.default_rng(1).choice(len(dist), 192, replace=False)
+    parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, rows=rows, atol=1e-4)
+
+
+EDGE_CASES = {
+    # name: (query length, segment lengths, m, generator)
+    "ragged_segments": (3001, [700, 129, 64, 1500, 63, 2], 64, "rw"),
+    "m2": (400, [50, 3, 1, 70], 2, "rw"),
+    "m37_odd": (1777, [300, 36, 37, 38, 900], 37, "ecg"),
+    "one_row": (100, [250, 300], 100, "rw"),
+    "one_window_segments": (2500, [96] * 40, 96, "rw"),
+    "many_tiny_segments": (5000, [20 + (k % 7) for k in range(300)], 16, "ecg"),
+    "long_single_segment": (3000, [9000], 200, "ecg"),
+    "rows_span_cta_tail": (2048 + 511 + 300, [2000, 1000], 300, "rw"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE_CASES))
+def test_edge_cases(mp, ctx, name):
+    n, lens, m, gen = EDGE_CASES[name]
+    rng_seed = sum(map(ord, name))
+    src = synthetic.random_walk if gen == "rw" else synthetic.ecg_like
+    q = src(n, rng_seed).astype(np.float32)
+    b = src(int(sum(lens)), rng_seed + 1).astype(np.float32)
+    offs = np.concatenate(([0], np.cumsum(lens))).astype(np.int64)
+    dist, idx = join(mp, ctx, q, b, offs, m)
+    parity.check(dist, idx, q, b, offs, m, atol=1e-4)
+
+
+def test_no_dictionary_window(mp, ctx):
+    q = synthetic.random_walk(500, 3).astype(np.float32)
+    b = synthetic.random_walk(90, 4).astype(np.float32)
+    dist, idx = join(mp, ctx, q, b, np.array([0, 30, 60, 90]), 31)
+    assert np.all(np.isinf(dist)) and np.all(idx == -1)
+
+
+def test_constant_windows(mp, ctx):
+    rng = np.random.default_rng(9)
+    q = np.concatenate([rng.standard_normal(300), np.full(100, 2.5), rng.standard_normal(300)]).astype(np.float32)
+    b = np.concatenate([rng.standard_normal(400), np.full(80, -1.0), rng.standard_normal(400)]).astype(np.float32)
+    offs = np.array([0, 350, 500, 880])
+    for m in (16, 50):
+        dist, idx = join(mp, ctx, q, b, offs, m)
+        parity.check(dist, idx, q, b, offs, m, atol=1e-4)
+    # no constant dictionary window: constant query rows are sqrt(m) from every window, lowest index wins
+    b2 = rng.standard_normal(600).astype(np.float32)
+    dist, idx = join(mp, ctx, q, b2, np.array([0, 600]), 16)
+    crow = np.arange(300, 300 + 100 - 16 + 1)
+    assert np.allclose(dist[crow], 4.0) and np.all(idx[crow] == 0)
+
+
+def test_planted_copy_and_segment_junction(mp, ctx):
+    rng = np.random.default_rng(11)
+    m = 64
+    b = rng.standard_normal(3000).cumsum().astype(np.float32)
+    offs = np.array([0, 1000, 2000, 3000])
+    q = rng.standard_normal(4000).cumsum().astype(np.float32)
+    g = 1000 + 321
+    q[1500 : 1500 + m] = b[g : g + m]
+    j = 2000 - m // 2
+    q[3000 : 3000 + m] = b[j : j + m]
+    dist, idx = join(mp, ctx, q, b, offs, m)
+    assert idx[1500] == g and dist[1500] < 1e-3
+    assert idx[3000] != j and dist[3000] > 0.05
+    d1, i1 = join(mp, ctx, q, b, np.array([0, 1000, 3000]), m)
+    assert i1[3000] == j and d1[3000] < 1e-3
+
+
+def test_device_api_matches_host_api_and_is_deterministic(mp, ctx):
+    import torch
+
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 32)
+    d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+    try:
+        hd, hi = mp.mp_ab_join(ctx, d, w.query, w.m)
+        hd2, hi2 = mp.mp_ab_join(ctx, d, w.query, w.m)
+        assert np.array_equal(hd, hd2) and np.array_equal(hi, hi2)
+        qt = torch.from_numpy(w.query).cuda()
+        nq = len(w.query) - w.m + 1
+        dd = torch.empty(nq, dtype=torch.float64, device="cuda")
+        di = torch.empty(nq, dtype=torch.int64, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            mp.mp_ab_join_device(ctx, d, qt.data_ptr(), mp.MP_F32, len(w.query), w.m, dd.data_ptr(), di.data_ptr(),
+                                 s.cuda_stream)
+        s.synchronize()
+        assert np.array_equal(dd.cpu().numpy(), hd) and np.array_equal(di.cpu().numpy(), hi)
+    finally:
+        mp.mp_dict_free(ctx, d)
+
+
+def test_argument_errors(mp, ctx):
+    b = synthetic.random_walk(1000, 1).astype(np.float32)
+    d = mp.mp_dict_load(ctx, b, [0, 1000], [32])
+    try:
+        q = synthetic.random_walk(200, 2).astype(np.float32)
+        for bad_m in (1, 201):
+            with pytest.raises(mp.MPError) as e:
+                mp.mp_ab_join(ctx, d, q, bad_m)
+            assert e.value.code == mp.MP_E_ARG
+        qn = q.copy()
+        qn[17] = np.nan
+        with pytest.raises(mp.MPError) as e:
+            mp.mp_ab_join(ctx, d, qn, 32)
+        assert e.value.code == mp.MP_E_ARG
+        with pytest.raises(mp.MPError) as e:
+            mp.mp_ab_join(ctx, d, q.astype(np.float64), 32)
+        assert e.value.code == mp.MP_E_ARG
+        with pytest.raises(mp.MPError) as e:
+            mp.mp_dict_load(ctx, b, [0, 600, 500, 1000])
+        assert e.value.code == mp.MP_E_ARG
+    finally:
+        mp.mp_dict_free(ctx, d)
+
+
+def test_profile_phases(mp, ctx):
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 64)
+    d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+    try:
+        mp.mp_profile(ctx, True)
+        mp.mp_profile_read(ctx, reset=True)
+        for _ in range(3):
+            mp.mp_ab_join(ctx, d, w.query, w.m)
+        ms, n = mp.mp_profile_read(ctx, reset=True)
+        assert list(n) == [3, 3, 3] and np.all(ms > 0)
+    finally:
+        mp.mp_profile(ctx, False)
+        mp.mp_dict_free(ctx, d)
