@@ -4,14 +4,17 @@
 //   1. reduces the column groups' partial maxima of q = C * invstd_b (the
 //      element-wise minimum of Algorithm 2, Sec. 3.2, over the distance
 //      d^2 = 2m - 2 invstd_a q), keeping the lowest window index on ties;
-//   2. applies the constant-window convention (a constant window normalises
+//   2. re-scores the kChunk dictionary windows of the winning chunk with
+//      direct dot products (the join kernels keep only a running maximum and
+//      the chunk that raised it) and takes their argmax, lowest g on ties;
+//   3. applies the constant-window convention (a constant window normalises
 //      to the zero vector: d = sqrt(m) against a non-constant window, 0
 //      against a constant one);
-//   3. recomputes the chosen pair's distance from its definition,
+//   4. recomputes the chosen pair's distance from its definition,
 //      sqrt(sum_k (z_a[k] - z_b[k])^2), so the reported value carries no
 //      error from the recurrence or the tensor-core products, only from the
 //      choice of the pair.
-// One warp per query window: the lanes split the m terms of the sum.
+// One warp per query window.
 #include <math.h>
 
 #include "mp_internal.cuh"
@@ -19,7 +22,7 @@
 namespace mpd {
 namespace {
 
-// Exact-as-practical distance of query window i and dictionary window g.
+// Distance of query window i and dictionary window g from the definition.
 __device__ __forceinline__ double pair_distance(const float *a, int64_t i, double mu_a, double is_a, const float *b,
                                                 int64_t g, double mu_b, double is_b, int m, int lane)
 {
@@ -35,10 +38,9 @@ __device__ __forceinline__ double pair_distance(const float *a, int64_t i, doubl
         const float d = za - zb;
         acc = fmaf(d, d, acc);
     }
-    double t = (double)acc;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    return sqrt(t);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return (double)sqrtf(acc);
 }
 
 __device__ __forceinline__ double pair_distance(const double *a, int64_t i, double mu_a, double is_a,
@@ -55,27 +57,27 @@ __device__ __forceinline__ double pair_distance(const double *a, int64_t i, doub
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize(int64_t nq, int32_t m, int32_t n_groups,
-                                                  const Partial<T> *__restrict__ part, const T *__restrict__ a,
-                                                  const double *__restrict__ mean_a,
-                                                  const double *__restrict__ invstd_a,
-                                                  const uint8_t *__restrict__ cflag_a, const T *__restrict__ b,
-                                                  const double *__restrict__ mean_b,
-                                                  const double *__restrict__ invstd_b, int64_t g_const,
-                                                  int64_t g_first, double *__restrict__ out_dist,
-                                                  int64_t *__restrict__ out_idx)
+__device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
+{
+    // (q1, g1) beats (q2, g2): valid, larger score, or equal score and lower index
+    return g1 >= 0 && (g2 < 0 || q1 > q2 || (q1 == q2 && g1 < g2));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double sqrt_m = sqrt((double)m);
-    for (int64_t i = warp_global; i < nq; i += nwarps) {
-        // 1. reduce the column groups: largest q, then lowest g
+    const double sqrt_m = sqrt((double)p.m);
+    const int m = p.m;
+    for (int64_t i = warp_global; i < p.nq; i += nwarps) {
+        // 1. reduce the column groups: largest q, then lowest chunk start
         T q = T(-INFINITY);
         int32_t g = -1;
-        for (int k = lane; k < n_groups; k += 32) {
-            const Partial<T> v = part[(int64_t)k * nq + i];
-            if (v.g >= 0 && (g < 0 || v.q > q || (v.q == q && v.g < g))) {
+        for (int k = lane; k < p.n_groups; k += 32) {
+            const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+            if (better(v.q, v.g, q, g)) {
                 q = v.q;
                 g = v.g;
             }
@@ -84,37 +86,76 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t nq, int32_t m, int32_t
         for (int o = 16; o > 0; o >>= 1) {
             const T q2 = __shfl_xor_sync(0xffffffffu, q, o);
             const int32_t g2 = __shfl_xor_sync(0xffffffffu, g, o);
-            if (g2 >= 0 && (g < 0 || q2 > q || (q2 == q && g2 < g))) {
+            if (better(q2, g2, q, g)) {
                 q = q2;
                 g = g2;
             }
         }
-        // 2. constant-window convention and 3. exact distance of the pick
         double d = INFINITY;
         int64_t gi = -1;
-        if (g_first >= 0) {
-            if (cflag_a[i]) {
-                if (g_const >= 0) {
+        if (p.g_first >= 0) {
+            if (p.cflag_a[i]) {
+                // 3. a constant query window is 0 from a constant window, sqrt(m) from the rest
+                if (p.g_const >= 0) {
                     d = 0.0;
-                    gi = g_const;
+                    gi = p.g_const;
                 } else {
                     d = sqrt_m;
-                    gi = g_first;
+                    gi = p.g_first;
                 }
             } else {
                 if (g >= 0) {
-                    d = pair_distance(a, i, mean_a[i], invstd_a[i], b, g, mean_b[g], invstd_b[g], m, lane);
-                    gi = g;
+                    // 2. re-score the chunk's windows: two lanes per candidate, each
+                    // summing half of the m products of shifted samples
+                    const int cand = lane >> 1, half = lane & 1;
+                    const int64_t gc = (int64_t)g + cand;
+                    bool ok = gc < p.npos_b;
+                    vec4_t<T> r;
+                    if (ok) {
+                        r = p.rs_b[gc];
+                        ok = r.w == T(0);
+                    }
+                    T sc = T(-INFINITY);
+                    if (cand < kChunk) {
+                        const double mua = p.mean_a[i];
+                        const double mub = ok ? p.mean_b[gc] : 0.0;
+                        const T sa = (T)mua, sb = (T)mub;
+                        T acc = T(0);
+                        const int k0 = half * (m >> 1), k1 = half ? m : (m >> 1);
+                        if (ok)
+                            for (int k = k0; k < k1; ++k) acc = fma(p.a[i + k] - sa, p.b[gc + k] - sb, acc);
+                        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                        const T cov = acc - (T)((double)m * (mua - (double)sa) * (mub - (double)sb));
+                        if (ok) sc = cov * r.z;
+                    } else {
+                        __shfl_xor_sync(0xffffffffu, T(0), 1);
+                    }
+                    int32_t gw = (ok && cand < kChunk) ? (int32_t)gc : -1;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                        const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
+                        if (better(s2, g2, sc, gw)) {
+                            sc = s2;
+                            gw = g2;
+                        }
+                    }
+                    if (gw >= 0) {
+                        // 4. the chosen pair's distance from its definition
+                        d = pair_distance(p.a, i, p.mean_a[i], p.invstd_a[i], p.b, gw, p.mean_b[gw], p.invstd_b[gw],
+                                          m, lane);
+                        gi = gw;
+                    }
                 }
-                if (g_const >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && g_const < gi))) {
+                if (p.g_const >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && p.g_const < gi))) {
                     d = sqrt_m;
-                    gi = g_const;
+                    gi = p.g_const;
                 }
             }
         }
         if (lane == 0) {
-            out_dist[i] = d;
-            out_idx[i] = gi;
+            p.out_dist[i] = d;
+            p.out_idx[i] = gi;
         }
     }
 }
@@ -122,26 +163,16 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t nq, int32_t m, int32_t
 }  // namespace
 
 template <typename T>
-cudaError_t launch_finalize(int64_t nq, int32_t m, int32_t n_groups, const Partial<T> *part, const T *a,
-                            const double *mean_a, const double *invstd_a, const uint8_t *cflag_a, const T *b,
-                            const double *mean_b, const double *invstd_b, int64_t g_const, int64_t g_first,
-                            double *out_dist, int64_t *out_idx, cudaStream_t st)
+cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st)
 {
-    if (nq <= 0) return cudaSuccess;
-    int64_t grid = (nq + 7) / 8;  // 8 warps (rows) per CTA
-    if (grid > 152 * 32) grid = 152 * 32;
-    k_finalize<T><<<(unsigned)grid, 256, 0, st>>>(nq, m, n_groups, part, a, mean_a, invstd_a, cflag_a, b, mean_b,
-                                                  invstd_b, g_const, g_first, out_dist, out_idx);
+    if (p.nq <= 0) return cudaSuccess;
+    int64_t grid = (p.nq + 7) / 8;  // 8 warps (rows) per CTA
+    if (grid > 152 * 64) grid = 152 * 64;
+    k_finalize<T><<<(unsigned)grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_finalize<float>(int64_t, int32_t, int32_t, const Partial<float> *, const float *,
-                                            const double *, const double *, const uint8_t *, const float *,
-                                            const double *, const double *, int64_t, int64_t, double *, int64_t *,
-                                            cudaStream_t);
-template cudaError_t launch_finalize<double>(int64_t, int32_t, int32_t, const Partial<double> *, const double *,
-                                             const double *, const double *, const uint8_t *, const double *,
-                                             const double *, const double *, int64_t, int64_t, double *, int64_t *,
-                                             cudaStream_t);
+template cudaError_t launch_finalize<float>(const FinalizeParams<float> &, cudaStream_t);
+template cudaError_t launch_finalize<double>(const FinalizeParams<double> &, cudaStream_t);
 
 }  // namespace mpd

@@ -27,6 +27,7 @@ struct Span {
 // Launch geometry of the plain diagonal kernel.
 constexpr int kPlainRowsPerLane = 16;  // query windows owned by one lane
 constexpr int kPlainColBlock = 256;    // dictionary windows staged per block
+constexpr int kChunk = 16;             // windows per chunk of the lazy argmax
 
 // Per-window statistics of a series for one window length m (kernel K1).
 //   mean[i], invstd[i]   FP64 mean and 1/population-std (0 for a constant window)
@@ -37,7 +38,13 @@ constexpr int kPlainColBlock = 256;    // dictionary windows staged per block
 //                          y = dg[i] = (x[i+m-1] - mean[i]) + (x[i-1] - mean[i-1])  (0 for i = 0)
 //                          z = invstd[i] rounded to T
 //                          w = 0, or -inf for a constant window (excludes it from
-//                              the maximum of the correlation score)
+//                              the maximum of the correlation score); for a
+//                              dictionary, launch_mark_invalid also sets -inf
+//                              (and z = 0) on every position whose window
+//                              crosses a segment end
+template <typename T>
+cudaError_t launch_mark_invalid(vec4_t<T> *rs, int64_t npos, const int64_t *seg_offsets, int32_t n_segments,
+                                int32_t m, cudaStream_t st);
 template <typename T>
 cudaError_t launch_window_stats(const T *x, int64_t n, int32_t m, double *mean, double *invstd, uint8_t *cflag,
                                 vec4_t<T> *rs, cudaStream_t st);
@@ -51,8 +58,10 @@ cudaError_t launch_dict_specials(const Span *spans, int32_t n_spans, const uint8
                                  cudaStream_t st);
 
 // Partial result of one column group for one query window: the largest
-// correlation score q = cov * invstd_b over the group's non-constant windows
-// and the lowest global window index attaining it (-1 if none).
+// correlation score q = cov * invstd_b over the group's valid non-constant
+// windows, and the first window g of the kChunk-window chunk (inside one
+// segment) where that maximum was first reached (-1 if none). The
+// finalisation re-scores windows g .. g + kChunk - 1 to find the exact one.
 template <typename T> struct Partial {
     T q;
     int32_t g;
@@ -104,14 +113,26 @@ cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *
                                  int32_t *counter, int warps, int max_m, int grid, cudaStream_t st);
 template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
 
-// Finalisation (kernel K4): reduce the column groups, apply the constant-window
-// convention, recompute the chosen pair's distance exactly and write the output.
-//   g_const  lowest constant valid dictionary window, or -1
-//   g_first  lowest valid dictionary window, or -1 (no window at all)
-template <typename T>
-cudaError_t launch_finalize(int64_t nq, int32_t m, int32_t n_groups, const Partial<T> *part, const T *a,
-                            const double *mean_a, const double *invstd_a, const uint8_t *cflag_a, const T *b,
-                            const double *mean_b, const double *invstd_b, int64_t g_const, int64_t g_first,
-                            double *out_dist, int64_t *out_idx, cudaStream_t st);
+// Finalisation (kernel K4): reduce the column groups, re-score the winning
+// chunk, apply the constant-window convention, recompute the chosen pair's
+// distance exactly and write the output.
+template <typename T> struct FinalizeParams {
+    int64_t nq;
+    int32_t m;
+    int32_t n_groups;
+    const Partial<T> *part;   // [n_groups][nq]
+    const T *a;               // query samples
+    const double *mean_a, *invstd_a;
+    const uint8_t *cflag_a;
+    const T *b;               // dictionary samples
+    int64_t npos_b;           // window positions of the concatenated dictionary (nb - m + 1)
+    const vec4_t<T> *rs_b;    // dictionary recurrence terms (z = invstd, w = 0 or -inf)
+    const double *mean_b, *invstd_b;
+    int64_t g_const;          // lowest constant valid dictionary window, or -1
+    int64_t g_first;          // lowest valid dictionary window, or -1 (no window at all)
+    double *out_dist;
+    int64_t *out_idx;
+};
+template <typename T> cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st);
 
 }  // namespace mpd

@@ -86,6 +86,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     const int NB_pad = pad<8>(NB) + 1;
     // stop: top seeds, one per (warp, column of the block)
     T *stop = sb + NB_pad;
+    // scs: recurrence terms of the block's columns (padded to whole chunks)
+    vec4_t<T> *scs = reinterpret_cast<vec4_t<T> *>(
+        (reinterpret_cast<uintptr_t>(stop + nwarps * CB) + 31) & ~static_cast<uintptr_t>(31));
 
     const T shift_a = (T)p.mean_a[R0 < p.nq ? R0 : p.nq - 1];
     for (int e = threadIdx.x; e < NA; e += blockDim.x) {
@@ -96,7 +99,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     const int64_t r_w = R0 + (int64_t)warp * 32 * kRows;  // first row of this warp
     const int64_t r0 = r_w + (int64_t)lane * kRows;       // first row of this lane
     T dfa[kRows], dga[kRows], C[kRows], best[kRows];
-    int32_t bidx[kRows];
+    int32_t bchunk[kRows];  // first window of the chunk holding the row's best score
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
         const int64_t r = r0 + j;
@@ -110,7 +113,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
         }
         C[j] = T(0);
         best[j] = T(-INFINITY);
-        bidx[j] = -1;
+        bchunk[j] = -1;
     }
     const T da_w = (T)(p.mean_a[r_w < p.nq ? r_w : p.nq - 1] - (double)shift_a);
     const int sa_w = warp * 32 * kRows;      // sa index of this warp's first row
@@ -127,6 +130,19 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             for (int e = threadIdx.x; e < NB; e += blockDim.x) {
                 const int64_t j = gblk + e;
                 sb[pad<8>(e)] = (j < p.nb) ? (p.b[j] - shift_b) : T(0);
+            }
+            const int ncb_up = (ncb + kChunk - 1) / kChunk * kChunk;
+            for (int c = threadIdx.x; c < ncb_up; c += blockDim.x) {
+                vec4_t<T> v;
+                if (c < ncb) {
+                    v = p.rs_b[gblk + c];
+                } else {  // padding columns: no recurrence change, never selected
+                    v.x = T(0);
+                    v.y = T(0);
+                    v.z = T(0);
+                    v.w = T(-INFINITY);
+                }
+                scs[c] = v;
             }
             __syncthreads();
 
@@ -155,6 +171,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     if (c < ncb) {
                         const T db = (T)(p.mean_b[gblk + c] - (double)shift_b);
                         stop[warp * CB + c] = acc[t] - T(m) * da_w * db;
+                    } else {
+                        stop[warp * CB + c] = T(0);
                     }
                 }
             }
@@ -186,27 +204,38 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             }
             __syncwarp();
 
-            // ---- main loop: one dictionary window (column) per step ----
-            vec4_t<T> cs = p.rs_b[gblk];
-            for (int c = 0; c < ncb; ++c) {
-                const int64_t g = gblk + c;
-                const vec4_t<T> cs_next = p.rs_b[(c + 1 < ncb) ? g + 1 : g];
-                if (cb > 0 || c > 0) {
-                    const T up = __shfl_up_sync(0xffffffffu, C[kRows - 1], 1);
+            // ---- main loop: one dictionary window (column) per step, in
+            // chunks of kChunk columns. Only the running maximum of each
+            // row's score is kept per step; the chunk that raised it is
+            // recorded, and the finalisation re-scores that chunk's
+            // windows to find the exact one.
+            const T *stop_w = stop + warp * CB;
+            for (int c0 = 0; c0 < ncb; c0 += kChunk) {
+                T cm[kRows];
 #pragma unroll
-                    for (int j = kRows - 1; j >= 1; --j) C[j] = fma(dfa[j], cs.y, fma(cs.x, dga[j], C[j - 1]));
-                    const T c0v = fma(dfa[0], cs.y, fma(cs.x, dga[0], up));
-                    C[0] = (lane == 0) ? stop[warp * CB + c] : c0v;
+                for (int j = 0; j < kRows; ++j) cm[j] = T(-INFINITY);
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) {
+                    const int c = c0 + u;
+                    const vec4_t<T> cs = scs[c];
+                    if (cb > 0 || c > 0) {
+                        const T up = __shfl_up_sync(0xffffffffu, C[kRows - 1], 1);
+#pragma unroll
+                        for (int j = kRows - 1; j >= 1; --j) C[j] = fma(dfa[j], cs.y, fma(cs.x, dga[j], C[j - 1]));
+                        const T c0v = fma(dfa[0], cs.y, fma(cs.x, dga[0], up));
+                        C[0] = (lane == 0) ? stop_w[c] : c0v;
+                    }
+#pragma unroll
+                    for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fma(C[j], cs.z, cs.w));
                 }
+                const int32_t gch = (int32_t)(gblk + c0);
 #pragma unroll
                 for (int j = 0; j < kRows; ++j) {
-                    const T q = fma(C[j], cs.z, cs.w);
-                    if (q > best[j]) {
-                        best[j] = q;
-                        bidx[j] = (int32_t)g;
+                    if (cm[j] > best[j]) {
+                        best[j] = cm[j];
+                        bchunk[j] = gch;
                     }
                 }
-                cs = cs_next;
             }
         }
     }
@@ -217,7 +246,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
         if (r < p.nq) {
             Partial<T> v;
             v.q = best[j];
-            v.g = bidx[j];
+            v.g = bchunk[j];
             p.part[(int64_t)grp * p.nq + r] = v;
         }
     }
@@ -261,7 +290,9 @@ size_t plain_smem_bytes(int warps, int m)
     const int m_up8 = (m + 7) & ~7, m_up16 = (m + 15) & ~15;
     const int NA = rows_cta + m_up16 + 32;
     const int NB = kPlainColBlock + m_up8 + 16;
-    return sizeof(T) * ((size_t)(NA + NA / 16 + 1) + (size_t)(NB + NB / 8 + 1) + (size_t)warps * kPlainColBlock);
+    const size_t scalars = (size_t)(NA + NA / 16 + 1) + (size_t)(NB + NB / 8 + 1) + (size_t)warps * kPlainColBlock;
+    // + 32: the column-stat array is aligned up to 32 bytes inside the block
+    return sizeof(T) * scalars + 32 + sizeof(vec4_t<T>) * kPlainColBlock;
 }
 
 template <typename T>

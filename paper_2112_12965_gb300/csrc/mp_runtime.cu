@@ -287,6 +287,21 @@ static int get_stats(mp_ctx *ctx, mp_dict *d, int32_t m, DictStats **out)
             e = launch_window_stats<float>((const float *)d->d_samples, d->nb, m, s->mean, s->invstd, s->cflag,
                                            (float4 *)s->rs, ctx->stream);
         CUDA_TRY(e);
+        {
+            int64_t *doffs = nullptr;
+            const size_t ob = d->offs.size() * sizeof(int64_t);
+            CUDA_TRY(cudaMalloc(&doffs, ob));
+            CUDA_TRY(cudaMemcpyAsync(doffs, d->offs.data(), ob, cudaMemcpyHostToDevice, ctx->stream));
+            if (d->dtype == MP_F64)
+                e = launch_mark_invalid<double>((dvec4 *)s->rs, npos, doffs, (int32_t)d->offs.size() - 1, m,
+                                                ctx->stream);
+            else
+                e = launch_mark_invalid<float>((float4 *)s->rs, npos, doffs, (int32_t)d->offs.size() - 1, m,
+                                               ctx->stream);
+            CUDA_TRY(e);
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            cudaFree(doffs);
+        }
         if (!s->seg_spans.empty()) {
             Span *dsp = nullptr;
             int64_t *dsv = nullptr;
@@ -368,6 +383,32 @@ static void free_stats(DictStats *s)
         cudaFree(kv.second.group_start);
     }
     tc_free_pack(s->tc_pack);
+}
+
+template <typename T>
+static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const Partial<T> *part, const T *a,
+                                    const double *mean_a, const double *inv_a, const uint8_t *cf_a, const mp_dict *d,
+                                    const DictStats *s, double *dist, int64_t *idx)
+{
+    FinalizeParams<T> f;
+    f.nq = nq;
+    f.m = m;
+    f.n_groups = n_groups;
+    f.part = part;
+    f.a = a;
+    f.mean_a = mean_a;
+    f.invstd_a = inv_a;
+    f.cflag_a = cf_a;
+    f.b = (const T *)d->d_samples;
+    f.npos_b = d->nb - m + 1;
+    f.rs_b = (const vec4_t<T> *)s->rs;
+    f.mean_b = s->mean;
+    f.invstd_b = s->invstd;
+    f.g_const = s->g_const;
+    f.g_first = s->g_first;
+    f.out_dist = dist;
+    f.out_idx = idx;
+    return f;
 }
 
 // Launch geometry of the plain kernel for nq rows and W columns.
@@ -453,9 +494,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
-            CUDA_TRY(launch_finalize<double>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a,
-                                             (const double *)d->d_samples, s->mean, s->invstd, s->g_const,
-                                             s->g_first, d_dist, d_idx, st));
+            CUDA_TRY(launch_finalize<double>(
+                fin_params<double>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a, d, s, d_dist, d_idx), st));
         }
     } else {
         const float *a = (const float *)dq;
@@ -478,9 +518,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
-            CUDA_TRY(launch_finalize<float>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a,
-                                            (const float *)d->d_samples, s->mean, s->invstd, s->g_const,
-                                            s->g_first, d_dist, d_idx, st));
+            CUDA_TRY(launch_finalize<float>(
+                fin_params<float>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a, d, s, d_dist, d_idx), st));
         }
     }
     return MP_OK;
@@ -629,12 +668,11 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
             Request &r = *ps.r;
             const int64_t nq = r.n - r.m + 1;
             JoinWs w = join_ws_layout(nq, r.dtype, ps.n_groups, 0);
-            CUDA_TRY(launch_finalize<float>(nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part),
-                                            ps.a, (const double *)(ps.base + w.off_mean),
-                                            (const double *)(ps.base + w.off_inv),
-                                            (const uint8_t *)(ps.base + w.off_cflag),
-                                            (const float *)r.dict->d_samples, ps.s->mean, ps.s->invstd,
-                                            ps.s->g_const, ps.s->g_first, ps.dist, ps.idx, st));
+            CUDA_TRY(launch_finalize<float>(
+                fin_params<float>(nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part), ps.a,
+                                  (const double *)(ps.base + w.off_mean), (const double *)(ps.base + w.off_inv),
+                                  (const uint8_t *)(ps.base + w.off_cflag), r.dict, ps.s, ps.dist, ps.idx),
+                st));
             CUDA_TRY(cudaMemcpyAsync(r.out_dist, ps.dist, nq * 8, cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaMemcpyAsync(r.out_idx, ps.idx, nq * 8, cudaMemcpyDeviceToHost, st));
         }

@@ -210,6 +210,28 @@ __global__ void k_check_finite(const T *__restrict__ x, int64_t n, int32_t *bad)
     if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
 }
 
+// Positions of the concatenated dictionary whose window crosses a segment end
+// (or lies in a segment shorter than m) are not dictionary windows (Def. 8):
+// give them score weight 0 and penalty -inf so that no kernel can select them.
+template <typename T>
+__global__ void k_mark_invalid(vec4_t<T> *__restrict__ rs, int64_t npos, const int64_t *__restrict__ offs,
+                               int32_t nseg, int32_t m)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < npos; g += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nseg;  // find s with offs[s] <= g < offs[s+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (offs[mid] <= g) lo = mid; else hi = mid;
+        }
+        if (g + m > offs[lo + 1]) {
+            vec4_t<T> v = rs[g];
+            v.z = T(0);
+            v.w = T(-INFINITY);
+            rs[g] = v;
+        }
+    }
+}
+
 __global__ void k_dict_specials(const Span *__restrict__ spans, int32_t n_spans, const uint8_t *__restrict__ cflag,
                                 unsigned long long *out)
 {
@@ -259,6 +281,19 @@ cudaError_t launch_dict_specials(const Span *spans, int32_t n_spans, const uint8
                                                                       reinterpret_cast<unsigned long long *>(out));
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_mark_invalid(vec4_t<T> *rs, int64_t npos, const int64_t *seg_offsets, int32_t n_segments,
+                                int32_t m, cudaStream_t st)
+{
+    if (npos <= 0 || n_segments <= 0) return cudaSuccess;
+    int64_t grid = (npos + 255) / 256;
+    if (grid > 8192) grid = 8192;
+    k_mark_invalid<T><<<(unsigned)grid, 256, 0, st>>>(rs, npos, seg_offsets, n_segments, m);
+    return cudaGetLastError();
+}
+template cudaError_t launch_mark_invalid<float>(float4 *, int64_t, const int64_t *, int32_t, int32_t, cudaStream_t);
+template cudaError_t launch_mark_invalid<double>(dvec4 *, int64_t, const int64_t *, int32_t, int32_t, cudaStream_t);
 
 template cudaError_t launch_window_stats<float>(const float *, int64_t, int32_t, double *, double *, uint8_t *,
                                                 float4 *, cudaStream_t);
