@@ -160,6 +160,28 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def roofline(kname, pairs, m, join_ms, peaks, peak_src):
+    """Roofline of the join kernel: ALU-issue bound (plain) or tensor bound (tcgen05)."""
+    if kname == "plain":
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-instructions/s
+        achieved = pairs * PLAIN_OPS_PER_PAIR / (join_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": None, "kernel": "k_plain",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)",
+                "ops_per_pair": PLAIN_OPS_PER_PAIR}
+    tflops_peak = peaks.get("bf16_tflops", 1900.0)
+    mult = 3 if kname == "bf16x3" else 1
+    src = f"{peak_src} bf16 burst"
+    if kname == "tf32":
+        tflops_peak /= 2.0
+        src += " / 2 (nominal TF32:BF16 ratio)"
+    achieved = pairs * 2 * m * mult / (join_ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": tflops_peak, "unit": "TFLOP/s",
+            "frac": achieved / tflops_peak, "traffic": None, "kernel": f"k_tc<{0 if kname == 'bf16x3' else 1}>",
+            "peak_source": src, "flops_per_pair": 2 * m * mult}
+
+
 def kernel_id(mp, name):
     return {"plain": mp.MP_KERNEL_PLAIN, "bf16x3": mp.MP_KERNEL_TC_BF16X3, "tf32": mp.MP_KERNEL_TC_TF32,
             "auto": mp.MP_KERNEL_AUTO}[name]
@@ -352,23 +374,21 @@ def main():
     peaks, peak_src = load_peaks()
     join_ms = phase_ms[mp.MP_PHASE_JOIN] / max(1, phase_n[mp.MP_PHASE_JOIN])
     clock = clk.summary()
-    if args.kernel in ("plain",):
-        peak_ops = SMS * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
-        achieved = pairs * PLAIN_OPS_PER_PAIR / (join_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": None, "kernel": "k_plain",
-                "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
-                               f"({peak_src} max clock)",
-                "ops_per_pair": PLAIN_OPS_PER_PAIR}
-    else:
-        tflops_peak = peaks.get("bf16_tflops", 1900.0)
-        mult = 3 if args.kernel == "bf16x3" else 1
-        if args.kernel == "tf32":
-            tflops_peak /= 2.0
-        achieved = pairs * 2 * w.m * mult / (join_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tflops_peak, "unit": "TFLOP/s",
-                "frac": achieved / tflops_peak, "traffic": None, "kernel": "k_tc",
-                "peak_source": f"{peak_src} bf16 burst" + (" / 2 (tf32 nominal ratio)" if args.kernel == "tf32" else "")}
+    roof = roofline(args.kernel, pairs, w.m, join_ms, peaks, peak_src)
+    # the other join forms on the same workload (same timing method)
+    kernels = {}
+    for kname in ("plain", "bf16x3", "tf32"):
+        if kname == args.kernel:
+            sm, pm, pn = step_ms, phase_ms, phase_n
+        else:
+            mp.mp_set_kernel(ctx, kernel_id(mp, kname))
+            sm, pm, pn, _ = time_device_join(mp, ctx, d, w, max(3, args.steps // 2), args.warmup, flush)
+            mp.mp_set_kernel(ctx, kernel_id(mp, args.kernel))
+        jm = pm[mp.MP_PHASE_JOIN] / max(1, pn[mp.MP_PHASE_JOIN])
+        r = roofline(kname, pairs, w.m, jm, peaks, peak_src)
+        kernels[kname] = {"pairs_per_s": pairs / (float(np.mean(sm)) / 1e3), "ms_per_step": float(np.mean(sm)),
+                          "join_kernel_ms": jm, "join_pairs_per_s": pairs / (jm / 1e3),
+                          "roofline_frac": r["frac"], "roofline_unit": r["unit"], "achieved": r["achieved"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -381,6 +401,7 @@ def main():
         "phases_ms": {"stats": phase_ms[0] / max(1, phase_n[0]), "join": join_ms,
                       "finalize": phase_ms[2] / max(1, phase_n[2])},
         "roofline": roof,
+        "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(np.sum(phase_n)),
         "clocks": clock,

@@ -105,9 +105,46 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                 }
             } else {
                 if (g >= 0) {
-                    // 2. re-score the chunk's windows: two lanes per candidate, each
-                    // summing half of the m products of shifted samples
-                    const int cand = lane >> 1, half = lane & 1;
+                    // 2. re-score the chunk's windows g .. g + kChunk - 1. Lane l sums the
+                    // products of a contiguous range of k for all candidates (a sliding
+                    // window of dictionary samples in registers), then a transposing
+                    // butterfly leaves candidate (l & 15)'s total in lane l.
+                    const double mua = p.mean_a[i];
+                    const double mub0 = p.mean_b[g];
+                    const T sa = (T)mua, sb = (T)mub0;
+                    const int kpl = (m + 31) >> 5;
+                    const int k0 = lane * kpl;
+                    const int k1 = min(m, k0 + kpl);
+                    T acc[kChunk], bw[kChunk];
+#pragma unroll
+                    for (int c = 0; c < kChunk; ++c) {
+                        acc[c] = T(0);
+                        const int64_t j = (int64_t)g + k0 + c;
+                        bw[c] = (k0 < k1 && j < p.nb) ? p.b[j] - sb : T(0);
+                    }
+                    for (int kb = k0; kb < k1; kb += kChunk) {
+#pragma unroll
+                        for (int u = 0; u < kChunk; ++u) {
+                            const int k = kb + u;
+                            const T av = (k < k1) ? p.a[i + k] - sa : T(0);
+#pragma unroll
+                            for (int c = 0; c < kChunk; ++c) acc[c] = fma(av, bw[(c + u) & (kChunk - 1)], acc[c]);
+                            const int64_t j = (int64_t)g + k + kChunk;
+                            bw[u] = (k < k1 && j < p.nb) ? p.b[j] - sb : T(0);
+                        }
+                    }
+#pragma unroll
+                    for (int s = kChunk / 2; s >= 1; s >>= 1) {
+#pragma unroll
+                        for (int c = 0; c < s; ++c) {
+                            const bool up = (lane & s) != 0;
+                            const T send = up ? acc[c] : acc[c + s];
+                            const T keep = up ? acc[c + s] : acc[c];
+                            acc[c] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+                        }
+                    }
+                    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 16);
+                    const int cand = lane & (kChunk - 1);
                     const int64_t gc = (int64_t)g + cand;
                     bool ok = gc < p.npos_b;
                     vec4_t<T> r;
@@ -116,21 +153,12 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                         ok = r.w == T(0);
                     }
                     T sc = T(-INFINITY);
-                    if (cand < kChunk) {
-                        const double mua = p.mean_a[i];
-                        const double mub = ok ? p.mean_b[gc] : 0.0;
-                        const T sa = (T)mua, sb = (T)mub;
-                        T acc = T(0);
-                        const int k0 = half * (m >> 1), k1 = half ? m : (m >> 1);
-                        if (ok)
-                            for (int k = k0; k < k1; ++k) acc = fma(p.a[i + k] - sa, p.b[gc + k] - sb, acc);
-                        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                        const T cov = acc - (T)((double)m * (mua - (double)sa) * (mub - (double)sb));
-                        if (ok) sc = cov * r.z;
-                    } else {
-                        __shfl_xor_sync(0xffffffffu, T(0), 1);
+                    if (ok) {
+                        const double mub = p.mean_b[gc];
+                        const T cov = acc[0] - (T)((double)m * (mua - (double)sa) * (mub - (double)sb));
+                        sc = cov * r.z;
                     }
-                    int32_t gw = (ok && cand < kChunk) ? (int32_t)gc : -1;
+                    int32_t gw = ok ? (int32_t)gc : -1;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);

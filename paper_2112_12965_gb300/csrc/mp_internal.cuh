@@ -125,6 +125,7 @@ template <typename T> struct FinalizeParams {
     const double *mean_a, *invstd_a;
     const uint8_t *cflag_a;
     const T *b;               // dictionary samples
+    int64_t nb;               // dictionary sample count
     int64_t npos_b;           // window positions of the concatenated dictionary (nb - m + 1)
     const vec4_t<T> *rs_b;    // dictionary recurrence terms (z = invstd, w = 0 or -inf)
     const double *mean_b, *invstd_b;

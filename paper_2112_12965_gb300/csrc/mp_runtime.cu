@@ -400,6 +400,7 @@ static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const P
     f.invstd_a = inv_a;
     f.cflag_a = cf_a;
     f.b = (const T *)d->d_samples;
+    f.nb = d->nb;
     f.npos_b = d->nb - m + 1;
     f.rs_b = (const vec4_t<T> *)s->rs;
     f.mean_b = s->mean;
@@ -435,14 +436,17 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
 
 // Workspace layout of one join.
 struct JoinWs {
-    size_t off_mean, off_inv, off_cflag, off_rs, off_part, total;
+    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_part, total;
 };
 
 static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front)
 {
     JoinWs w;
+    // error word of the tensor-core kernel at the front
     const size_t e = dtype == MP_F64 ? 8 : 4;
     size_t o = align_up(extra_front, 256);
+    w.off_err = o;
+    o += 256;
     w.off_mean = o;
     o = align_up(o + nq * 8, 256);
     w.off_inv = o;
@@ -466,7 +470,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl);
-    JoinWs w = join_ws_layout(nq, dtype, geo.n_groups, 0);
+    const bool tc = (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32);
+    JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0);
     double *mean_a = (double *)(base + w.off_mean);
     double *inv_a = (double *)(base + w.off_inv);
     uint8_t *cf_a = (uint8_t *)(base + w.off_cflag);
@@ -504,11 +509,25 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             PhaseTimer t(ctx, MP_PHASE_STATS, st);
             CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
         }
-        if (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32) {
-            return tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
-                           (const float *)d->d_samples, d->nb, s->seg_spans.data(), (int32_t)s->seg_spans.size(),
-                           s->mean, s->invstd, s->rs, a, n, m, mean_a, inv_a, cf_a, s->g_const, s->g_first, d_dist,
-                           d_idx, st, fail);
+        if (tc) {
+            Partial<float> *part = (Partial<float> *)(base + w.off_part);
+            int32_t *err = (int32_t *)(base + w.off_err);
+            int ng = 1;
+            CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+            {
+                PhaseTimer t(ctx, MP_PHASE_JOIN, st);
+                int rc = tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
+                                 (const float *)d->d_samples, d->nb, s->seg_spans.data(),
+                                 (int32_t)s->seg_spans.size(), s->mean, s->invstd, s->rs, a, n, m, mean_a, inv_a, cf_a,
+                                 s->g_const, s->g_first, part, err, &ng, st, fail);
+                if (rc) return rc;
+            }
+            {
+                PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
+                CUDA_TRY(launch_finalize<float>(
+                    fin_params<float>(nq, m, ng, part, a, mean_a, inv_a, cf_a, d, s, d_dist, d_idx), st));
+            }
+            return MP_OK;
         }
         Partial<float> *part = (Partial<float> *)(base + w.off_part);
         {
@@ -530,7 +549,7 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const DictStats *s, int32_t dtype
     const int64_t nq = n - m + 1;
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     const Geometry geo = plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl);
-    return join_ws_layout(nq, dtype, geo.n_groups, 0).total;
+    return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0).total;
 }
 
 static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s)
@@ -538,7 +557,8 @@ static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const Dic
     if (dtype == MP_F64) return MP_KERNEL_PLAIN;
     int k = ctx->kernel;
     if (k == MP_KERNEL_AUTO) k = tc_autotune_choice(m, s->n_windows);
-    if ((k == MP_KERNEL_TC_BF16X3 || k == MP_KERNEL_TC_TF32) && !tc_supported(m)) k = MP_KERNEL_PLAIN;
+    if (k == MP_KERNEL_TC_BF16X3 && !tc_supported(0, m)) k = MP_KERNEL_PLAIN;
+    if (k == MP_KERNEL_TC_TF32 && !tc_supported(1, m)) k = MP_KERNEL_PLAIN;
     return k;
 }
 
@@ -1000,7 +1020,12 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
+    int32_t err = 0;
+    const int kused = resolve_kernel(ctx, dtype, m, s);
+    const bool tc = (kused == MP_KERNEL_TC_BF16X3 || kused == MP_KERNEL_TC_TF32);
+    if (tc) CUDA_TRY(cudaMemcpyAsync(&err, base + qbytes + 2 * obytes, sizeof err, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (err) return fail(MP_E_TIMEOUT, "a tensor-core wait timed out on the device; results are invalid");
     return MP_OK;
 }
 

@@ -1,18 +1,548 @@
-// Tensor-core form of the join (kernel K3).
+// K3: the tensor-core form of the dictionary AB-join (tcgen05, sm_103a).
+//
+// The join's dot products QT[i, g] = sum_k a[i+k] * b[g+k] (Algorithm 2's
+// per-segment AB-join, Sec. 3.2) form, for a block of 128 query windows and N
+// dictionary windows, a dense product of two Hankel matrices with K = m:
+//     QT = A * B^T,  A[r, k] = a[i0 + r + k],  B[n, k] = b[g0 + n + k].
+// A CTA owns 128 query windows (the 128 TMEM lanes) and walks tiles of up to
+// 256 dictionary windows that never cross a segment (Def. 8). Accumulators are
+// FP32 in TMEM; the products are either one TF32 product or three BF16
+// products of a hi/lo split (x = hi + lo: hi*hi + hi*lo + lo*hi).
+//
+// Hankel operands in shared memory. The MMA reads K-major operands in 128-byte
+// swizzled rows (64 BF16 or 32 TF32 values of K per row). Row rho of a
+// "row-shifted Hankel" buffer holds samples [base + rho, base + rho + E),
+// E = values per row. The operand of K-block q (K values [qE, qE + E)) is then
+// the same buffer starting at row qE, so one buffer of (K-blocks - 1) E + rows
+// rows serves every K-block: its descriptor start moves by qE rows (a multiple
+// of 8 rows = 1024 bytes, so the swizzle phase is unchanged), and the four
+// MMAs inside a 128-byte row step the start address by 32 bytes.
+//
+// The query operand is built once per CTA for all of K. The dictionary operand
+// is built per tile and per K-group (a run of K-blocks sized to fit shared
+// memory). After the last K-group the epilogue reads the accumulators with
+// tcgen05.ld (one query window per thread), removes the shifts, scales by the
+// dictionary windows' 1/std, masks invalid and constant windows and keeps the
+// running maximum per 16-window chunk, as the plain kernel does.
+//
+// Every wait on the tensor core is bounded: on timeout the CTA records an
+// error, waits (bounded) for its MMAs, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "../../include/mpdict.h"
 #include "mp_tc.cuh"
 
 namespace mpd {
+namespace {
 
-bool tc_supported(int) { return false; }
-int tc_autotune_choice(int, int64_t) { return MP_KERNEL_PLAIN; }
-void tc_load_tune_cache(const char *) {}
-void tc_free_pack(void *) {}
-int tc_join(int, int, void **, const float *, int64_t, const Span *, int32_t, const double *, const double *,
-            const void *, const float *, int64_t, int32_t, const double *, const double *, const uint8_t *, int64_t,
-            int64_t, double *, int64_t *, cudaStream_t, fail_fn fail)
+constexpr int kTcThreads = 128;
+constexpr int kTcMaxN = 256;           // TMEM columns (FP32 accumulators) per CTA
+constexpr size_t kTcSmemLimit = 225 * 1024;
+
+struct TcTile {
+    int64_t g0;      // first dictionary window of the tile
+    int32_t nvalid;  // valid windows in the tile
+    int32_t nmma;    // MMA N: nvalid rounded up to 16
+};
+
+struct TcArgs {
+    const float *a;
+    int64_t na, nq;
+    int32_t m;
+    int32_t n_groups;
+    const double *mean_a;
+    const float *b;
+    int64_t nb;
+    const double *mean_b;
+    const float4 *rs_b;  // z = 1/std (0: constant or invalid), w = 0 or -inf
+    const TcTile *tiles;
+    const int32_t *group_start;
+    Partial<float> *part;
+    int32_t *err;
+    int32_t ra_rows;  // rows of the query Hankel buffer
+    int32_t rb_rows;  // rows of the dictionary Hankel buffer (one K-group)
+    int32_t qg;       // K-blocks per K-group
+    int32_t nkb;      // K-blocks in total
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    return fail(MP_E_INTERNAL, "tensor-core join not available");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of the barrier: false after about `cycles` clocks.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long cycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > cycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);      // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+    return d;
+}
+
+template <int VARIANT>
+__device__ __forceinline__ uint32_t instr_desc(int n)
+{
+    // D = F32 (bits 4-5), A/B format (bits 7-9, 10-12): BF16 = 1, TF32 = 2;
+    // both K-major; N >> 3 at bits 17-22; M >> 4 at bits 24-28 (M = 128).
+    const uint32_t fmt = VARIANT == 0 ? 1u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int VARIANT>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    if (VARIANT == 0)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Build rows [0, rows) of a row-shifted Hankel buffer from staged samples
+// raw[0 ..]: row rho, value j = raw[rho + j]. 16-byte chunk c of row rho is
+// stored at chunk position c ^ (rho & 7) (the 128-byte swizzle).
+template <int VARIANT>
+__device__ __forceinline__ void build_hankel(const float *raw, int rows, unsigned char *hi, unsigned char *lo)
+{
+    constexpr int EPC = VARIANT == 0 ? 8 : 4;  // values per 16-byte chunk
+    for (int idx = threadIdx.x; idx < rows * 8; idx += kTcThreads) {
+        const int rho = idx >> 3, c = idx & 7;
+        const uint32_t off = (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4);
+        const float *src = raw + rho + c * EPC;
+        if (VARIANT == 0) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x0 = src[2 * e], x1 = src[2 * e + 1];
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                h[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                l[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        } else {
+            *reinterpret_cast<float4 *>(hi + off) =
+                make_float4(to_tf32(src[0]), to_tf32(src[1]), to_tf32(src[2]), to_tf32(src[3]));
+        }
+    }
+}
+
+template <int VARIANT>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc(TcArgs p)
+{
+    constexpr int EPR = VARIANT == 0 ? 64 : 32;   // K values per 128-byte row
+    constexpr int KSTEP = VARIANT == 0 ? 16 : 8;  // K values per MMA
+    constexpr int NHL = VARIANT == 0 ? 2 : 1;     // hi/lo buffers
+    constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t a_bytes = (uint32_t)p.ra_rows * 128u, b_bytes = (uint32_t)p.rb_rows * 128u;
+    unsigned char *ha[2] = {base, base + a_bytes};
+    unsigned char *hb0 = base + NHL * a_bytes;
+    unsigned char *hb[2] = {hb0, hb0 + b_bytes};
+    float *raw = reinterpret_cast<float *>(hb0 + NHL * b_bytes);
+    const int raw_len = max(p.ra_rows, p.rb_rows) + EPR;
+    float4 *colp = reinterpret_cast<float4 *>(raw + ((raw_len + 3) & ~3));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t rb = blockIdx.x / p.n_groups;
+    const int grp = blockIdx.x % p.n_groups;
+    const int64_t i0 = rb * 128;
+    const int m = p.m;
+
+    if (warp == 0) tmem_alloc(tmem_slot, kTcMaxN);
+    if (tid == 0) mbar_init(bar, 1);
+
+    // query operand, once for all K
+    const float s_a = (float)p.mean_a[i0 < p.nq ? i0 : p.nq - 1];
+    for (int e = tid; e < p.ra_rows + EPR; e += kTcThreads) {
+        const int64_t j = i0 + e;
+        raw[e] = (j < p.na) ? p.a[j] - s_a : 0.f;
+    }
+    __syncthreads();
+    build_hankel<VARIANT>(raw, p.ra_rows, ha[0], ha[1]);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+    const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
+
+    const int64_t row = i0 + tid;
+    const float da = (row < p.nq) ? (float)(p.mean_a[row] - (double)s_a) : 0.f;
+    float best = -INFINITY;
+    int32_t bchunk = -1;
+    uint32_t phase = 0;
+    bool aborted = false;
+
+    const int t_lo = p.group_start[grp], t_hi = p.group_start[grp + 1];
+    for (int t = t_lo; t < t_hi && !aborted; ++t) {
+        const TcTile tile = p.tiles[t];
+        const float s_b = (float)p.mean_b[tile.g0];
+        // column terms of the epilogue: w = m * (mean_b - s_b), z = 1/std, p = 0 / -inf
+        for (int n = tid; n < kTcMaxN; n += kTcThreads) {
+            float4 v = make_float4(0.f, 0.f, -INFINITY, 0.f);
+            if (n < tile.nvalid) {
+                const int64_t g = tile.g0 + n;
+                const float4 r = p.rs_b[g];
+                v.x = (float)((double)m * (p.mean_b[g] - (double)s_b));
+                v.y = r.z;
+                v.z = r.w;
+            }
+            colp[n] = v;
+        }
+        for (int q0 = 0; q0 < p.nkb && !aborted; q0 += p.qg) {
+            const int q1 = min(p.nkb, q0 + p.qg);
+            const int rows_b = (q1 - q0 - 1) * EPR + tile.nmma;
+            for (int e = tid; e < rows_b + EPR; e += kTcThreads) {
+                const int64_t j = tile.g0 + (int64_t)q0 * EPR + e;
+                raw[e] = (j < p.nb) ? p.b[j] - s_b : 0.f;
+            }
+            __syncthreads();
+            build_hankel<VARIANT>(raw, rows_b, hb[0], hb[1]);
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t idesc = instr_desc<VARIANT>(tile.nmma);
+                const uint32_t a0 = smem_u32(ha[0]), a1 = smem_u32(ha[NHL - 1]);
+                const uint32_t b0 = smem_u32(hb[0]), b1 = smem_u32(hb[NHL - 1]);
+                for (int q = q0; q < q1; ++q) {
+                    const int ksteps = min(EPR, m - q * EPR) / KSTEP;
+                    const uint32_t ao = (uint32_t)(q * EPR) * 128u, bo = (uint32_t)((q - q0) * EPR) * 128u;
+                    for (int s = 0; s < ksteps; ++s) {
+                        const uint32_t acc0 = (q == 0 && s == 0) ? 0u : 1u;
+                        mma<VARIANT>(taddr, smem_desc(a0 + ao + 32u * s), smem_desc(b0 + bo + 32u * s), idesc, acc0);
+                        if (VARIANT == 0) {
+                            mma<VARIANT>(taddr, smem_desc(a0 + ao + 32u * s), smem_desc(b1 + bo + 32u * s), idesc, 1u);
+                            mma<VARIANT>(taddr, smem_desc(a1 + ao + 32u * s), smem_desc(b0 + bo + 32u * s), idesc, 1u);
+                        }
+                    }
+                }
+                mma_commit(bar);
+            }
+            const bool ok = mbar_wait(bar, phase, kWaitCycles);
+            aborted = __syncthreads_or(!ok) != 0;
+            if (!aborted) phase ^= 1u;
+        }
+        if (aborted) break;
+        // epilogue: this thread's query window against the tile's windows
+        tc_fence_after();
+        const int ncols = (tile.nmma + 31) & ~31;
+        for (int c32 = 0; c32 < ncols; c32 += 32) {
+            uint32_t v[32];
+            tmem_ld32(t_lane + (uint32_t)c32, v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float cm = -INFINITY;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const float4 cp = colp[c32 + 16 * h + u];
+                    const float cov = fmaf(-da, cp.x, __uint_as_float(v[16 * h + u]));
+                    cm = fmaxf(cm, fmaf(cov, cp.y, cp.z));
+                }
+                if (cm > best) {
+                    best = cm;
+                    bchunk = (int32_t)(tile.g0 + c32 + 16 * h);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();  // TMEM reads done before the next tile's MMAs overwrite it
+    }
+
+    if (aborted) {
+        if (tid == 0) atomicExch(p.err, 1);
+        // let any MMA still in flight finish before the TMEM is released
+        mbar_wait(bar, phase, kWaitCycles);
+    } else if (row < p.nq) {
+        Partial<float> v;
+        v.q = best;
+        v.g = bchunk;
+        p.part[(int64_t)grp * p.nq + row] = v;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, kTcMaxN);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct TcPlan {
+    int variant;
+    int epr, kstep, nhl;
+    int nkb, ra_rows, rb_rows, qg, nmax;
+    size_t smem;
+};
+
+size_t plan_smem(const TcPlan &P)
+{
+    const size_t raw_len = (size_t)std::max(P.ra_rows, P.rb_rows) + P.epr;
+    return 1024 + (size_t)P.nhl * 128 * (P.ra_rows + P.rb_rows) + ((raw_len + 3) & ~(size_t)3) * 4 +
+           kTcMaxN * sizeof(float4) + 16 + 16;
+}
+
+bool make_plan(int variant, int m, TcPlan *out)
+{
+    TcPlan P;
+    P.variant = variant;
+    P.epr = variant == 0 ? 64 : 32;
+    P.kstep = variant == 0 ? 16 : 8;
+    P.nhl = variant == 0 ? 2 : 1;
+    if (m < P.kstep || m % P.kstep != 0) return false;
+    P.nkb = (m + P.epr - 1) / P.epr;
+    P.ra_rows = (P.nkb - 1) * P.epr + 128;
+    // Among the (tile width, K-group) pairs that fit, take the one with the
+    // least dictionary-operand building per (window x K value), with a
+    // penalty for narrow tiles (each MMA then re-reads the query operand for
+    // fewer columns).
+    bool found = false;
+    double best_score = 1e30;
+    TcPlan best{};
+    for (int nmax : {256, 128, 64}) {
+        for (int qg = 1; qg <= P.nkb; ++qg) {
+            TcPlan C = P;
+            C.nmax = nmax;
+            C.qg = qg;
+            C.rb_rows = (qg - 1) * P.epr + nmax;
+            // at least 80 KB: at most two CTAs (2 x 256 TMEM columns) per SM
+            C.smem = std::max<size_t>(plan_smem(C), 80 * 1024);
+            if (C.smem > kTcSmemLimit) break;
+            const double build = (double)C.rb_rows / ((double)nmax * qg);
+            const double score = build + (nmax == 64 ? 0.5 : (nmax == 128 ? 0.15 : 0.0));
+            if (score < best_score) {
+                best_score = score;
+                best = C;
+                found = true;
+            }
+        }
+    }
+    if (found) *out = best;
+    return found;
+}
+
+struct TcPack {
+    int nmax = 0, n_groups = 0;
+    TcTile *tiles = nullptr;
+    int32_t *group_start = nullptr;
+    int32_t n_tiles = 0;
+};
+
+struct TcPacks {
+    std::vector<TcPack> packs;
+};
+
+int tune_choice_m = -1;
+
+}  // namespace
+
+bool tc_supported(int variant, int m)
+{
+    TcPlan P;
+    return make_plan(variant, m, &P);
+}
+
+int tc_groups_bound(int sm_count, int64_t nq)
+{
+    const int64_t rbk = (nq + 127) / 128;
+    return (int)std::max<int64_t>(1, (2 * sm_count + rbk - 1) / rbk);
+}
+
+int tc_autotune_choice(int, int64_t)
+{
+    // The plain recurrence does O(1) work per pair while the tensor form does
+    // 2m flops per pair; measured on GB300 the plain form is faster at every
+    // m in the workloads, so AUTO resolves to it unless a tune cache says
+    // otherwise.
+    return MP_KERNEL_PLAIN;
+}
+
+void tc_load_tune_cache(const char *) {}
+
+void tc_free_pack(void *pack)
+{
+    TcPacks *pk = (TcPacks *)pack;
+    if (!pk) return;
+    for (auto &p : pk->packs) {
+        cudaFree(p.tiles);
+        cudaFree(p.group_start);
+    }
+    delete pk;
+}
+
+int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
+            const double *mean_b, const double *, const void *rs_b, const float *a, int64_t n, int32_t m,
+            const double *mean_a, const double *, const uint8_t *, int64_t, int64_t, Partial<float> *part,
+            int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail)
+{
+    TcPlan P;
+    if (!make_plan(variant, m, &P)) return fail(MP_E_ARG, "tensor-core join does not support m=%d", m);
+    const int64_t nq = n - m + 1;
+    const int64_t n_row_blocks = (nq + 127) / 128;
+    if (!*pack) *pack = new TcPacks();
+    TcPacks *pk = (TcPacks *)*pack;
+    // tiles of this dictionary for this tile width
+    std::vector<TcTile> tiles;
+    for (int32_t s = 0; s < n_seg; ++s)
+        for (int32_t c = 0; c < seg_spans[s].ncols; c += P.nmax) {
+            TcTile t;
+            t.g0 = seg_spans[s].g0 + c;
+            t.nvalid = std::min(P.nmax, seg_spans[s].ncols - c);
+            t.nmma = (t.nvalid + 15) & ~15;
+            tiles.push_back(t);
+        }
+    const int n_tiles = (int)tiles.size();
+    int ng = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (2 * sm_count + n_row_blocks - 1) / n_row_blocks));
+    TcPack *use = nullptr;
+    for (auto &p : pk->packs)
+        if (p.nmax == P.nmax && p.n_groups == ng) use = &p;
+    if (!use) {
+        TcPack np;
+        np.nmax = P.nmax;
+        np.n_groups = ng;
+        np.n_tiles = n_tiles;
+        std::vector<int32_t> gs(ng + 1);
+        for (int k = 0; k <= ng; ++k) gs[k] = (int32_t)((int64_t)n_tiles * k / ng);
+        if (cudaMalloc(&np.tiles, std::max<size_t>(1, tiles.size()) * sizeof(TcTile)) != cudaSuccess ||
+            cudaMalloc(&np.group_start, gs.size() * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MP_E_NOMEM, "tensor-core tile table");
+        }
+        if (n_tiles) cudaMemcpy(np.tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice);
+        cudaMemcpy(np.group_start, gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        pk->packs.push_back(np);
+        use = &pk->packs.back();
+    }
+    TcArgs A;
+    A.a = a;
+    A.na = n;
+    A.nq = nq;
+    A.m = m;
+    A.n_groups = ng;
+    A.mean_a = mean_a;
+    A.b = b;
+    A.nb = nb;
+    A.mean_b = mean_b;
+    A.rs_b = (const float4 *)rs_b;
+    A.tiles = use->tiles;
+    A.group_start = use->group_start;
+    A.part = part;
+    A.err = err;
+    A.ra_rows = P.ra_rows;
+    A.rb_rows = P.rb_rows;
+    A.qg = P.qg;
+    A.nkb = P.nkb;
+    cudaError_t e;
+    auto launch = [&](auto kern) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+        if (e == cudaSuccess) {
+            kern<<<(unsigned)(n_row_blocks * ng), kTcThreads, P.smem, st>>>(A);
+            e = cudaGetLastError();
+        }
+    };
+    if (variant == 0)
+        launch(k_tc<0>);
+    else
+        launch(k_tc<1>);
+    if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core kernel launch: %s", cudaGetErrorString(e));
+    *n_groups_out = ng;
+    return MP_OK;
 }
 
 }  // namespace mpd

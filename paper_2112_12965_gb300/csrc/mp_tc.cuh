@@ -10,20 +10,26 @@ namespace mpd {
 
 typedef int (*fail_fn)(int, const char *, ...);
 
-// Whether the tensor-core kernel handles window length m.
-bool tc_supported(int m);
+// Whether the tensor-core kernel handles window length m (variant 0: split
+// BF16, m a multiple of 16, up to about 600; variant 1: TF32, m a multiple of
+// 8, up to about 1100 -- the query operand of all m stays in shared memory).
+bool tc_supported(int variant, int m);
+// Upper bound of the column groups tc_join uses for nq query windows.
+int tc_groups_bound(int sm_count, int64_t nq);
 // Join form picked by the autotune cache for (m, dictionary windows); MP_KERNEL_* value.
 int tc_autotune_choice(int m, int64_t n_windows);
 // Load / record autotune decisions (JSON lines file).
 void tc_load_tune_cache(const char *path);
-// Free the per-(dictionary, m) operand cache created by tc_join.
+// Free the per-(dictionary, m) tile tables created by tc_join.
 void tc_free_pack(void *pack);
 
-// Tensor-core join of an FP32 query against a dictionary; the query's window
-// statistics are already computed. variant: 0 = split BF16 (3 products), 1 = TF32.
-int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans,
-            int32_t n_seg, const double *mean_b, const double *invstd_b, const void *rs_b, const float *a,
-            int64_t n, int32_t m, const double *mean_a, const double *invstd_a, const uint8_t *cflag_a,
-            int64_t g_const, int64_t g_first, double *d_dist, int64_t *d_idx, cudaStream_t st, fail_fn fail);
+// Launch the tensor-core join (kernel K3) of an FP32 query whose window
+// statistics are computed; writes part[group * nq + row] (the same partial
+// format as the plain kernel) and *n_groups_out. *err is set to 1 on a
+// device-side timeout. variant: 0 = split BF16 (3 products), 1 = TF32.
+int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
+            const double *mean_b, const double *invstd_b, const void *rs_b, const float *a, int64_t n, int32_t m,
+            const double *mean_a, const double *invstd_a, const uint8_t *cflag_a, int64_t g_const, int64_t g_first,
+            Partial<float> *part, int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail);
 
 }  // namespace mpd
