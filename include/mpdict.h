@@ -150,6 +150,34 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
                       double *d_out_dist, int64_t *d_out_idx, void *stream);
 
 /*
+ * The join of mp_ab_join_device without any device allocation (the paper has
+ * no counterpart; this is a service of the library). It is meant for callers
+ * that must not allocate device memory while they serve a request: services
+ * that reserve all GPU memory up front and forbid allocation on the request
+ * path, because cudaMalloc/cudaFree can synchronise the device and add
+ * latency jitter, and applications that own the device allocator (a caching
+ * allocator or pool whose accounting a foreign cudaMalloc would break).
+ *
+ * Its scratch is one fixed array of about 26 MB inside this library, held by
+ * every GPU that loads the library until the process exits. Limits: float32
+ * samples only, at most 2^19 query windows (n - m + 1), and a dictionary cut
+ * into at most 2^16 runs of windows; larger calls return MP_E_ARG with a
+ * message and do nothing. The dictionary's statistics for m must already be
+ * resident (list m in mp_dict_load), since computing them would allocate.
+ * The caller passes the device query and outputs as for mp_ab_join_device.
+ *
+ * The first call on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Every call shares the array and it keeps the
+ * last call's contents; everything a call reads from it is written by that
+ * call first. Calls whose work overlaps on the GPU (other streams, other
+ * contexts, other threads) race on the array and give undefined results:
+ * serialise them.
+ */
+int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int32_t dtype, int64_t n, int32_t m,
+                       double *d_out_dist, int64_t *d_out_idx, void *stream);
+
+/*
  * Window statistics (the first pass of the join) of a device series:
  * mean, 1/std (0 for a constant window) and the constant flag of each of the
  * n - m + 1 windows, in FP64, enqueued on `stream`.

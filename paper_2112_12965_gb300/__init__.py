@@ -94,6 +94,7 @@ def _load():
         "mp_dict_windows": ([P, i32, ctypes.POINTER(i64)], ctypes.c_int),
         "mp_ab_join": ([P, P, P, i32, i64, i32, P, P], ctypes.c_int),
         "mp_ab_join_device": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
+        "mp_ab_join_noalloc": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
         "mp_window_stats": ([P, P, i32, i64, i32, P, P, P, P], ctypes.c_int),
         "mp_submit": ([P, P, P, i32, i64, i32, P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "mp_poll": ([P, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -193,6 +194,12 @@ def mp_ab_join_device(ctx, d, d_query: int, dtype: int, n: int, m: int, d_dist: 
                       stream: int = 0) -> None:
     """Join on device pointers, enqueued on `stream` (0: the context's stream)."""
     _check(lib.mp_ab_join_device(ctx, d, d_query, dtype, n, m, d_dist, d_idx, stream or None))
+
+
+def mp_ab_join_noalloc(ctx, d, d_query: int, dtype: int, n: int, m: int, d_dist: int, d_idx: int,
+                       stream: int = 0) -> None:
+    """Join on device pointers using the library's fixed scratch array (no device allocation)."""
+    _check(lib.mp_ab_join_noalloc(ctx, d, d_query, dtype, n, m, d_dist, d_idx, stream or None))
 
 
 def mp_window_stats(ctx, d_x: int, dtype: int, n: int, m: int, d_mean: int, d_invstd: int, d_const: int,

@@ -1154,3 +1154,132 @@ int mp_drain(mp_ctx *ctx, double timeout_s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Join without device allocation
+//
+// Some callers cannot allocate device memory while they serve a request:
+// services that reserve all of the GPU's memory up front and forbid
+// allocation on the request path (cudaMalloc and cudaFree can synchronise the
+// device and add latency jitter), and host applications that own the device
+// allocator (a caching allocator or memory pool whose accounting a foreign
+// cudaMalloc would break). mp_ab_join_noalloc serves them: its scratch lives
+// in the fixed array below, which every GPU that loads this library holds
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocMaxWindows = (int64_t)1 << 19;   // query windows per call
+constexpr int64_t kNoAllocMaxPartials = (int64_t)1 << 20;  // column groups x query windows
+constexpr int64_t kNoAllocMaxSpans = (int64_t)1 << 16;     // runs of dictionary windows
+constexpr size_t kNoAllocMeanOff = 0;
+constexpr size_t kNoAllocInvOff = kNoAllocMeanOff + kNoAllocMaxWindows * sizeof(double);
+constexpr size_t kNoAllocFlagOff = kNoAllocInvOff + kNoAllocMaxWindows * sizeof(double);
+constexpr size_t kNoAllocRsOff = kNoAllocFlagOff + kNoAllocMaxWindows;
+constexpr size_t kNoAllocPartOff = kNoAllocRsOff + kNoAllocMaxWindows * sizeof(float4);
+constexpr size_t kNoAllocSpanOff = kNoAllocPartOff + kNoAllocMaxPartials * sizeof(Partial<float>);
+constexpr size_t kNoAllocGroupOff = kNoAllocSpanOff + kNoAllocMaxSpans * sizeof(Span);
+constexpr size_t kNoAllocBytes = kNoAllocGroupOff + (kNoAllocMaxSpans + 1) * sizeof(int32_t);
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+// About 26 MB: statistics of 2^19 query windows, 2^20 partial results and
+// 2^16 spans. Host code must not use this name as an address: it is a
+// host-side stand-in; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static unsigned char *g_noalloc_dev[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on `device` (which must be current).
+// Resolved once per device, at that device's first call.
+static int noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(MP_E_ARG, "device %d out of range", device);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_dev[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MP_E_CUDA, "cudaGetSymbolAddress of the no-allocation scratch: %s", cudaGetErrorString(e));
+        g_noalloc_dev[device] = (unsigned char *)p;
+    }
+    *out = g_noalloc_dev[device];
+    return MP_OK;
+}
+
+extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int32_t dtype, int64_t n,
+                                  int32_t m, double *d_out_dist, int64_t *d_out_idx, void *stream)
+{
+    g_err.clear();
+    int rc = check_join_args(ctx, dict, d_query, dtype, n, m);
+    if (rc) return rc;
+    if (!d_out_dist || !d_out_idx) return fail(MP_E_ARG, "null output");
+    if (dtype != MP_F32) return fail(MP_E_ARG, "the no-allocation join takes float32 samples only");
+    const int64_t nq = n - m + 1;
+    if (nq > kNoAllocMaxWindows)
+        return fail(MP_E_ARG, "query of %lld windows exceeds the no-allocation limit of %lld windows (n - m + 1)",
+                    (long long)nq, (long long)kNoAllocMaxWindows);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    mp_dict *d = const_cast<mp_dict *>(dict);
+    auto it = d->stats.find(m);
+    if (it == d->stats.end())
+        return fail(MP_E_ARG, "dictionary statistics for m=%d are not resident; list m when loading the dictionary "
+                              "(computing them would allocate)", m);
+    DictStats *s = it->second.get();
+    unsigned char *base = nullptr;
+    rc = noalloc_scratch(ctx->device, &base);
+    if (rc) return rc;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const float *a = (const float *)d_query;
+    double *mean_a = (double *)(base + kNoAllocMeanOff);
+    double *inv_a = (double *)(base + kNoAllocInvOff);
+    uint8_t *cf_a = (uint8_t *)(base + kNoAllocFlagOff);
+    float4 *rs_a = (float4 *)(base + kNoAllocRsOff);
+    Partial<float> *part = (Partial<float> *)(base + kNoAllocPartOff);
+    CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
+    int n_groups = 0;
+    if (s->n_windows > 0) {
+        Geometry geo = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane);
+        geo.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(geo.n_groups, kNoAllocMaxPartials / nq));
+        // the same cut into column groups as get_grouping, staged through the scratch
+        std::vector<Span> spans;
+        std::vector<int32_t> gstart(1, 0);
+        const int64_t target = (s->n_windows + geo.n_groups - 1) / geo.n_groups;
+        int64_t fill = 0;
+        for (const Span &seg : s->seg_spans) {
+            for (int64_t off = 0; off < seg.ncols;) {
+                const int64_t take = std::min<int64_t>(seg.ncols - off, target - fill);
+                spans.push_back(Span{seg.g0 + off, (int32_t)take, 0});
+                off += take;
+                fill += take;
+                if (fill == target) {
+                    gstart.push_back((int32_t)spans.size());
+                    fill = 0;
+                }
+            }
+        }
+        if (fill > 0) gstart.push_back((int32_t)spans.size());
+        while ((int)gstart.size() < geo.n_groups + 1) gstart.push_back((int32_t)spans.size());
+        if ((int64_t)spans.size() > kNoAllocMaxSpans)
+            return fail(MP_E_ARG, "dictionary needs %zu spans, above the no-allocation limit of %lld", spans.size(),
+                        (long long)kNoAllocMaxSpans);
+        Span *d_spans = (Span *)(base + kNoAllocSpanOff);
+        int32_t *d_gstart = (int32_t *)(base + kNoAllocGroupOff);
+        // pageable sources: the copies are staged before these calls return
+        CUDA_TRY(cudaMemcpyAsync(d_spans, spans.data(), spans.size() * sizeof(Span), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PlainLaunch L;
+        L.nq = nq;
+        L.m = m;
+        L.n_row_blocks = geo.n_row_blocks;
+        L.n_groups = geo.n_groups;
+        L.warps = geo.warps;
+        CUDA_TRY(launch_plain<float>(L, a, n, rs_a, mean_a, (const float *)d->d_samples, d->nb, (const float4 *)s->rs,
+                                     s->mean, d_spans, d_gstart, part, st));
+        n_groups = geo.n_groups;
+    }
+    // with no dictionary window (n_groups = 0, g_first = -1) this writes +inf / -1
+    CUDA_TRY(launch_finalize<float>(
+        fin_params<float>(nq, m, n_groups, part, a, mean_a, inv_a, cf_a, d, s, d_out_dist, d_out_idx), st));
+    return MP_OK;
+}
