@@ -158,7 +158,7 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
  * latency jitter, and applications that own the device allocator (a caching
  * allocator or pool whose accounting a foreign cudaMalloc would break).
  *
- * Its scratch is one fixed array of about 26 MB inside this library, held by
+ * Its scratch is one fixed array of about 30 MB inside this library, held by
  * every GPU that loads the library until the process exits. Limits: float32
  * samples only, at most 2^19 query windows (n - m + 1), and a dictionary cut
  * into at most 2^16 runs of windows; larger calls return MP_E_ARG with a

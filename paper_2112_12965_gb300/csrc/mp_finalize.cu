@@ -22,38 +22,24 @@
 namespace mpd {
 namespace {
 
-// Distance of query window i and dictionary window g from the definition.
-__device__ __forceinline__ double pair_distance(const float *a, int64_t i, double mu_a, double is_a, const float *b,
-                                                int64_t g, double mu_b, double is_b, int m, int lane)
+// Distance of query window i and dictionary window g from the definition,
+// sqrt(sum_k (z_a[k] - z_b[k])^2). Samples are centred with the split means
+// (hi, then lo), so the centring is accurate to T's relative precision even
+// for series with large offsets; lanes split the m terms.
+template <typename T>
+__device__ __forceinline__ double pair_distance(const T *a, int64_t i, Split<T> ma, T is_a, const T *b, int64_t g,
+                                                Split<T> mb, T is_b, int m, int lane)
 {
-    // Split each FP64 mean into two floats so the centring is accurate to
-    // FP32 relative to the centred values, even for series with big offsets.
-    const float ma_hi = (float)mu_a, ma_lo = (float)(mu_a - (double)ma_hi);
-    const float mb_hi = (float)mu_b, mb_lo = (float)(mu_b - (double)mb_hi);
-    const float sa = (float)is_a, sb = (float)is_b;
-    float acc = 0.f;
+    T acc = T(0);
     for (int k = lane; k < m; k += 32) {
-        const float za = ((a[i + k] - ma_hi) - ma_lo) * sa;
-        const float zb = ((b[g + k] - mb_hi) - mb_lo) * sb;
-        const float d = za - zb;
-        acc = fmaf(d, d, acc);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return (double)sqrtf(acc);
-}
-
-__device__ __forceinline__ double pair_distance(const double *a, int64_t i, double mu_a, double is_a,
-                                                const double *b, int64_t g, double mu_b, double is_b, int m, int lane)
-{
-    double acc = 0.0;
-    for (int k = lane; k < m; k += 32) {
-        const double d = (a[i + k] - mu_a) * is_a - (b[g + k] - mu_b) * is_b;
+        const T za = ((a[i + k] - ma.hi) - ma.lo) * is_a;
+        const T zb = ((b[g + k] - mb.hi) - mb.lo) * is_b;
+        const T d = za - zb;
         acc = fma(d, d, acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return sqrt(acc);
+    return (double)sqrt(acc);
 }
 
 template <typename T>
@@ -109,9 +95,8 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                     // products of a contiguous range of k for all candidates (a sliding
                     // window of dictionary samples in registers), then a transposing
                     // butterfly leaves candidate (l & 15)'s total in lane l.
-                    const double mua = p.mean_a[i];
-                    const double mub0 = p.mean_b[g];
-                    const T sa = (T)mua, sb = (T)mub0;
+                    const Split<T> ma = p.ms_a[i];
+                    const T sa = ma.hi, sb = p.ms_b[g].hi;
                     const int kpl = (m + 31) >> 5;
                     const int k0 = lane * kpl;
                     const int k1 = min(m, k0 + kpl);
@@ -154,8 +139,9 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                     }
                     T sc = T(-INFINITY);
                     if (ok) {
-                        const double mub = p.mean_b[gc];
-                        const T cov = acc[0] - (T)((double)m * (mua - (double)sa) * (mub - (double)sb));
+                        // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
+                        const Split<T> mb = p.ms_b[gc];
+                        const T cov = acc[0] - T(m) * ma.lo * ((mb.hi - sb) + mb.lo);
                         sc = cov * r.z;
                     }
                     int32_t gw = ok ? (int32_t)gc : -1;
@@ -170,8 +156,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                     }
                     if (gw >= 0) {
                         // 4. the chosen pair's distance from its definition
-                        d = pair_distance(p.a, i, p.mean_a[i], p.invstd_a[i], p.b, gw, p.mean_b[gw], p.invstd_b[gw],
-                                          m, lane);
+                        d = pair_distance<T>(p.a, i, ma, p.rs_a[i].z, p.b, gw, p.ms_b[gw], p.rs_b[gw].z, m, lane);
                         gi = gw;
                     }
                 }

@@ -16,6 +16,14 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = dvec4; };
 template <typename T> using vec4_t = typename Vec4<T>::type;
 
+// A window mean split into two values of the join's arithmetic type,
+// hi = mean rounded to T and lo = (mean - hi) rounded to T, so that kernels
+// can centre samples to T's relative precision without FP64 arithmetic
+// (FP64 throughput on GB300 is a small fraction of FP32's).
+template <typename T> struct __align__(2 * sizeof(T)) Split {
+    T hi, lo;
+};
+
 // A run of consecutive valid dictionary windows inside one segment:
 // global windows g0 .. g0 + ncols - 1.
 struct Span {
@@ -45,9 +53,10 @@ constexpr int kChunk = 16;             // windows per chunk of the lazy argmax
 template <typename T>
 cudaError_t launch_mark_invalid(vec4_t<T> *rs, int64_t npos, const int64_t *seg_offsets, int32_t n_segments,
                                 int32_t m, cudaStream_t st);
+// ms[i] (may be null): mean[i] split into hi + lo of type T.
 template <typename T>
 cudaError_t launch_window_stats(const T *x, int64_t n, int32_t m, double *mean, double *invstd, uint8_t *cflag,
-                                vec4_t<T> *rs, cudaStream_t st);
+                                vec4_t<T> *rs, Split<T> *ms, cudaStream_t st);
 
 // Checks every sample is finite; sets *bad to 1 otherwise (bad must be zeroed).
 template <typename T>
@@ -78,8 +87,8 @@ struct PlainLaunch {
 // Plain diagonal-recurrence join (kernel K2). Writes part[group * nq + row].
 // spans[group_start[k] .. group_start[k+1]) are the spans of column group k.
 template <typename T>
-cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const double *mean_a,
-                         const T *b, int64_t nb, const vec4_t<T> *rs_b, const double *mean_b, const Span *spans,
+cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
+                         const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, cudaStream_t st);
 template <typename T> size_t plain_smem_bytes(int warps, int m);
 
@@ -92,11 +101,11 @@ struct PlainRequest {
     int32_t m;
     int32_t n_groups;
     const float4 *rs_a;
-    const double *mean_a;
+    const Split<float> *ms_a;
     const float *b;
     int64_t nb;
     const float4 *rs_b;
-    const double *mean_b;
+    const Split<float> *ms_b;
     const Span *spans;
     const int32_t *group_start;
     Partial<float> *part;
@@ -122,13 +131,14 @@ template <typename T> struct FinalizeParams {
     int32_t n_groups;
     const Partial<T> *part;   // [n_groups][nq]
     const T *a;               // query samples
-    const double *mean_a, *invstd_a;
+    const vec4_t<T> *rs_a;    // query recurrence terms (z = 1/std)
+    const Split<T> *ms_a;     // query window means, split
     const uint8_t *cflag_a;
     const T *b;               // dictionary samples
     int64_t nb;               // dictionary sample count
     int64_t npos_b;           // window positions of the concatenated dictionary (nb - m + 1)
-    const vec4_t<T> *rs_b;    // dictionary recurrence terms (z = invstd, w = 0 or -inf)
-    const double *mean_b, *invstd_b;
+    const vec4_t<T> *rs_b;    // dictionary recurrence terms (z = 1/std, w = 0 or -inf)
+    const Split<T> *ms_b;     // dictionary window means, split
     int64_t g_const;          // lowest constant valid dictionary window, or -1
     int64_t g_first;          // lowest valid dictionary window, or -1 (no window at all)
     double *out_dist;

@@ -47,11 +47,11 @@ template <typename T> struct PlainParams {
     int32_t m;
     int32_t n_groups;
     const vec4_t<T> *rs_a;
-    const double *mean_a;
+    const Split<T> *ms_a;
     const T *b;
     int64_t nb;
     const vec4_t<T> *rs_b;
-    const double *mean_b;
+    const Split<T> *ms_b;
     const Span *spans;
     const int32_t *group_start;
     Partial<T> *part;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     vec4_t<T> *scs = reinterpret_cast<vec4_t<T> *>(
         (reinterpret_cast<uintptr_t>(stop + nwarps * CB) + 31) & ~static_cast<uintptr_t>(31));
 
-    const T shift_a = (T)p.mean_a[R0 < p.nq ? R0 : p.nq - 1];
+    const T shift_a = p.ms_a[R0 < p.nq ? R0 : p.nq - 1].hi;
     for (int e = threadIdx.x; e < NA; e += blockDim.x) {
         const int64_t j = R0 + e;
         sa[pad<16>(e)] = (j < p.na) ? (p.a[j] - shift_a) : T(0);
@@ -115,7 +115,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
         best[j] = T(-INFINITY);
         bchunk[j] = -1;
     }
-    const T da_w = (T)(p.mean_a[r_w < p.nq ? r_w : p.nq - 1] - (double)shift_a);
+    const Split<T> mw = p.ms_a[r_w < p.nq ? r_w : p.nq - 1];
+    const T da_w = (mw.hi - shift_a) + mw.lo;
     const int sa_w = warp * 32 * kRows;      // sa index of this warp's first row
     const int sa_l = sa_w + lane * kRows;    // sa index of this lane's first row
 
@@ -125,7 +126,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
         for (int cb = 0; cb < sp.ncols; cb += CB) {
             const int ncb = min(CB, sp.ncols - cb);
             const int64_t gblk = sp.g0 + cb;
-            const T shift_b = (T)p.mean_b[gblk];
+            const T shift_b = p.ms_b[gblk].hi;
             __syncthreads();  // previous block's sb / stop no longer in use
             for (int e = threadIdx.x; e < NB; e += blockDim.x) {
                 const int64_t j = gblk + e;
@@ -169,7 +170,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                 for (int t = 0; t < 8; ++t) {
                     const int c = c0 + t;
                     if (c < ncb) {
-                        const T db = (T)(p.mean_b[gblk + c] - (double)shift_b);
+                        const Split<T> mb = p.ms_b[gblk + c];
+                        const T db = (mb.hi - shift_b) + mb.lo;
                         stop[warp * CB + c] = acc[t] - T(m) * da_w * db;
                     } else {
                         stop[warp * CB + c] = T(0);
@@ -194,11 +196,12 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                         aw[u] = sa[pad<16>(sa_l + 16 + k)];
                     }
                 }
-                const T db0 = (T)(p.mean_b[gblk] - (double)shift_b);
+                const T db0 = p.ms_b[gblk].lo;  // shift_b is this window's mean rounded
 #pragma unroll
                 for (int j = 0; j < kRows; ++j) {
                     const int64_t r = r0 + j;
-                    const T da = (T)(p.mean_a[r < p.nq ? r : p.nq - 1] - (double)shift_a);
+                    const Split<T> ma = p.ms_a[r < p.nq ? r : p.nq - 1];
+                    const T da = (ma.hi - shift_a) + ma.lo;
                     C[j] -= T(m) * da * db0;
                 }
             }
@@ -296,8 +299,8 @@ size_t plain_smem_bytes(int warps, int m)
 }
 
 template <typename T>
-cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const double *mean_a,
-                         const T *b, int64_t nb, const vec4_t<T> *rs_b, const double *mean_b, const Span *spans,
+cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
+                         const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, cudaStream_t st)
 {
     PlainParams<T> p;
@@ -307,11 +310,11 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     p.m = L.m;
     p.n_groups = L.n_groups;
     p.rs_a = rs_a;
-    p.mean_a = mean_a;
+    p.ms_a = ms_a;
     p.b = b;
     p.nb = nb;
     p.rs_b = rs_b;
-    p.mean_b = mean_b;
+    p.ms_b = ms_b;
     p.spans = spans;
     p.group_start = group_start;
     p.part = part;
@@ -340,11 +343,13 @@ cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *
 
 template size_t plain_smem_bytes<float>(int, int);
 template size_t plain_smem_bytes<double>(int, int);
-template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *, const double *,
-                                         const float *, int64_t, const float4 *, const double *, const Span *,
-                                         const int32_t *, Partial<float> *, cudaStream_t);
+template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,
+                                         const Split<float> *, const float *, int64_t, const float4 *,
+                                         const Split<float> *, const Span *, const int32_t *, Partial<float> *,
+                                         cudaStream_t);
 template cudaError_t launch_plain<double>(const PlainLaunch &, const double *, int64_t, const dvec4 *,
-                                          const double *, const double *, int64_t, const dvec4 *, const double *,
-                                          const Span *, const int32_t *, Partial<double> *, cudaStream_t);
+                                          const Split<double> *, const double *, int64_t, const dvec4 *,
+                                          const Split<double> *, const Span *, const int32_t *, Partial<double> *,
+                                          cudaStream_t);
 
 }  // namespace mpd

@@ -80,6 +80,7 @@ struct DictStats {
     double *invstd = nullptr;
     uint8_t *cflag = nullptr;
     void *rs = nullptr;         // float4 / dvec4 recurrence terms
+    void *ms = nullptr;         // Split<float> / Split<double> window means
     std::vector<Span> seg_spans;  // one span per segment with at least one window
     int64_t n_windows = 0;        // W
     int64_t g_const = -1, g_first = -1;
@@ -268,24 +269,28 @@ static int get_stats(mp_ctx *ctx, mp_dict *d, int32_t m, DictStats **out)
     }
     const int64_t npos = d->nb - m + 1;
     if (npos > 0) {
-        const size_t rs_sz = (size_t)npos * (d->dtype == MP_F64 ? sizeof(dvec4) : sizeof(float4));
+        const bool f64 = d->dtype == MP_F64;
+        const size_t rs_sz = (size_t)npos * (f64 ? sizeof(dvec4) : sizeof(float4));
+        const size_t ms_sz = (size_t)npos * (f64 ? sizeof(Split<double>) : sizeof(Split<float>));
         if (cudaMalloc(&s->mean, npos * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&s->invstd, npos * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&s->cflag, npos) != cudaSuccess || cudaMalloc(&s->rs, rs_sz) != cudaSuccess) {
+            cudaMalloc(&s->cflag, npos) != cudaSuccess || cudaMalloc(&s->rs, rs_sz) != cudaSuccess ||
+            cudaMalloc(&s->ms, ms_sz) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(s->mean);
             cudaFree(s->invstd);
             cudaFree(s->cflag);
             cudaFree(s->rs);
+            cudaFree(s->ms);
             return fail(MP_E_NOMEM, "dictionary statistics for m=%d", m);
         }
         cudaError_t e;
-        if (d->dtype == MP_F64)
+        if (f64)
             e = launch_window_stats<double>((const double *)d->d_samples, d->nb, m, s->mean, s->invstd, s->cflag,
-                                            (dvec4 *)s->rs, ctx->stream);
+                                            (dvec4 *)s->rs, (Split<double> *)s->ms, ctx->stream);
         else
             e = launch_window_stats<float>((const float *)d->d_samples, d->nb, m, s->mean, s->invstd, s->cflag,
-                                           (float4 *)s->rs, ctx->stream);
+                                           (float4 *)s->rs, (Split<float> *)s->ms, ctx->stream);
         CUDA_TRY(e);
         {
             int64_t *doffs = nullptr;
@@ -378,6 +383,7 @@ static void free_stats(DictStats *s)
     cudaFree(s->invstd);
     cudaFree(s->cflag);
     cudaFree(s->rs);
+    cudaFree(s->ms);
     for (auto &kv : s->groupings) {
         cudaFree(kv.second.spans);
         cudaFree(kv.second.group_start);
@@ -387,8 +393,8 @@ static void free_stats(DictStats *s)
 
 template <typename T>
 static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const Partial<T> *part, const T *a,
-                                    const double *mean_a, const double *inv_a, const uint8_t *cf_a, const mp_dict *d,
-                                    const DictStats *s, double *dist, int64_t *idx)
+                                    const vec4_t<T> *rs_a, const Split<T> *ms_a, const uint8_t *cf_a,
+                                    const mp_dict *d, const DictStats *s, double *dist, int64_t *idx)
 {
     FinalizeParams<T> f;
     f.nq = nq;
@@ -396,15 +402,14 @@ static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const P
     f.n_groups = n_groups;
     f.part = part;
     f.a = a;
-    f.mean_a = mean_a;
-    f.invstd_a = inv_a;
+    f.rs_a = rs_a;
+    f.ms_a = ms_a;
     f.cflag_a = cf_a;
     f.b = (const T *)d->d_samples;
     f.nb = d->nb;
     f.npos_b = d->nb - m + 1;
     f.rs_b = (const vec4_t<T> *)s->rs;
-    f.mean_b = s->mean;
-    f.invstd_b = s->invstd;
+    f.ms_b = (const Split<T> *)s->ms;
     f.g_const = s->g_const;
     f.g_first = s->g_first;
     f.out_dist = dist;
@@ -436,7 +441,7 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
 
 // Workspace layout of one join.
 struct JoinWs {
-    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_part, total;
+    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, total;
 };
 
 static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front)
@@ -455,6 +460,8 @@ static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t ext
     o = align_up(o + nq, 256);
     w.off_rs = o;
     o = align_up(o + nq * 4 * e, 256);
+    w.off_ms = o;
+    o = align_up(o + nq * 2 * e, 256);
     w.off_part = o;
     o = align_up(o + (size_t)n_groups * nq * (e == 8 ? sizeof(Partial<double>) : sizeof(Partial<float>)), 256);
     w.total = o;
@@ -487,27 +494,30 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
     if (dtype == MP_F64) {
         const double *a = (const double *)dq;
         dvec4 *rs_a = (dvec4 *)(base + w.off_rs);
+        Split<double> *ms_a = (Split<double> *)(base + w.off_ms);
         Partial<double> *part = (Partial<double> *)(base + w.off_part);
         {
             PhaseTimer t(ctx, MP_PHASE_STATS, st);
-            CUDA_TRY(launch_window_stats<double>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
+            CUDA_TRY(launch_window_stats<double>(a, n, m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
-            CUDA_TRY(launch_plain<double>(L, a, n, rs_a, mean_a, (const double *)d->d_samples, d->nb,
-                                          (const dvec4 *)s->rs, s->mean, gr->spans, gr->group_start, part, st));
+            CUDA_TRY(launch_plain<double>(L, a, n, rs_a, ms_a, (const double *)d->d_samples, d->nb,
+                                          (const dvec4 *)s->rs, (const Split<double> *)s->ms, gr->spans,
+                                          gr->group_start, part, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
             CUDA_TRY(launch_finalize<double>(
-                fin_params<double>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a, d, s, d_dist, d_idx), st));
+                fin_params<double>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx), st));
         }
     } else {
         const float *a = (const float *)dq;
         float4 *rs_a = (float4 *)(base + w.off_rs);
+        Split<float> *ms_a = (Split<float> *)(base + w.off_ms);
         {
             PhaseTimer t(ctx, MP_PHASE_STATS, st);
-            CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
+            CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
         }
         if (tc) {
             Partial<float> *part = (Partial<float> *)(base + w.off_part);
@@ -518,27 +528,28 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
                 PhaseTimer t(ctx, MP_PHASE_JOIN, st);
                 int rc = tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
                                  (const float *)d->d_samples, d->nb, s->seg_spans.data(),
-                                 (int32_t)s->seg_spans.size(), s->mean, s->invstd, s->rs, a, n, m, mean_a, inv_a, cf_a,
-                                 s->g_const, s->g_first, part, err, &ng, st, fail);
+                                 (int32_t)s->seg_spans.size(), s->ms, s->rs, a, n, m, ms_a, part, err, &ng, st,
+                                 fail);
                 if (rc) return rc;
             }
             {
                 PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
                 CUDA_TRY(launch_finalize<float>(
-                    fin_params<float>(nq, m, ng, part, a, mean_a, inv_a, cf_a, d, s, d_dist, d_idx), st));
+                    fin_params<float>(nq, m, ng, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx), st));
             }
             return MP_OK;
         }
         Partial<float> *part = (Partial<float> *)(base + w.off_part);
         {
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
-            CUDA_TRY(launch_plain<float>(L, a, n, rs_a, mean_a, (const float *)d->d_samples, d->nb,
-                                         (const float4 *)s->rs, s->mean, gr->spans, gr->group_start, part, st));
+            CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb,
+                                         (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
+                                         gr->group_start, part, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
             CUDA_TRY(launch_finalize<float>(
-                fin_params<float>(nq, m, geo.n_groups, part, a, mean_a, inv_a, cf_a, d, s, d_dist, d_idx), st));
+                fin_params<float>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx), st));
         }
     }
     return MP_OK;
@@ -644,8 +655,9 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         double *inv_a = (double *)(p + w.off_inv);
         uint8_t *cf_a = (uint8_t *)(p + w.off_cflag);
         float4 *rs_a = (float4 *)(p + w.off_rs);
+        Split<float> *ms_a = (Split<float> *)(p + w.off_ms);
         Partial<float> *part = (Partial<float> *)(p + w.off_part);
-        CUDA_TRY(launch_window_stats<float>(a, r.n, r.m, mean_a, inv_a, cf_a, rs_a, st));
+        CUDA_TRY(launch_window_stats<float>(a, r.n, r.m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
         PlainRequest pr;
         pr.a = a;
         pr.na = r.n;
@@ -653,11 +665,11 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         pr.m = r.m;
         pr.n_groups = geo.n_groups;
         pr.rs_a = rs_a;
-        pr.mean_a = mean_a;
+        pr.ms_a = ms_a;
         pr.b = (const float *)r.dict->d_samples;
         pr.nb = r.dict->nb;
         pr.rs_b = (const float4 *)s->rs;
-        pr.mean_b = s->mean;
+        pr.ms_b = (const Split<float> *)s->ms;
         pr.spans = gr->spans;
         pr.group_start = gr->group_start;
         pr.part = part;
@@ -690,7 +702,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
             JoinWs w = join_ws_layout(nq, r.dtype, ps.n_groups, 0);
             CUDA_TRY(launch_finalize<float>(
                 fin_params<float>(nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part), ps.a,
-                                  (const double *)(ps.base + w.off_mean), (const double *)(ps.base + w.off_inv),
+                                  (const float4 *)(ps.base + w.off_rs), (const Split<float> *)(ps.base + w.off_ms),
                                   (const uint8_t *)(ps.base + w.off_cflag), r.dict, ps.s, ps.dist, ps.idx),
                 st));
             CUDA_TRY(cudaMemcpyAsync(r.out_dist, ps.dist, nq * 8, cudaMemcpyDeviceToHost, st));
@@ -1039,9 +1051,11 @@ int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int3
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     if (dtype == MP_F64)
-        CUDA_TRY(launch_window_stats<double>((const double *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, st));
+        CUDA_TRY(launch_window_stats<double>((const double *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, nullptr,
+                                             st));
     else
-        CUDA_TRY(launch_window_stats<float>((const float *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, st));
+        CUDA_TRY(launch_window_stats<float>((const float *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, nullptr,
+                                            st));
     return MP_OK;
 }
 
@@ -1175,14 +1189,15 @@ constexpr size_t kNoAllocMeanOff = 0;
 constexpr size_t kNoAllocInvOff = kNoAllocMeanOff + kNoAllocMaxWindows * sizeof(double);
 constexpr size_t kNoAllocFlagOff = kNoAllocInvOff + kNoAllocMaxWindows * sizeof(double);
 constexpr size_t kNoAllocRsOff = kNoAllocFlagOff + kNoAllocMaxWindows;
-constexpr size_t kNoAllocPartOff = kNoAllocRsOff + kNoAllocMaxWindows * sizeof(float4);
+constexpr size_t kNoAllocMsOff = kNoAllocRsOff + kNoAllocMaxWindows * sizeof(float4);
+constexpr size_t kNoAllocPartOff = kNoAllocMsOff + kNoAllocMaxWindows * sizeof(Split<float>);
 constexpr size_t kNoAllocSpanOff = kNoAllocPartOff + kNoAllocMaxPartials * sizeof(Partial<float>);
 constexpr size_t kNoAllocGroupOff = kNoAllocSpanOff + kNoAllocMaxSpans * sizeof(Span);
 constexpr size_t kNoAllocBytes = kNoAllocGroupOff + (kNoAllocMaxSpans + 1) * sizeof(int32_t);
 constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
-// About 26 MB: statistics of 2^19 query windows, 2^20 partial results and
+// About 30 MB: statistics of 2^19 query windows, 2^20 partial results and
 // 2^16 spans. Host code must not use this name as an address: it is a
 // host-side stand-in; the device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1235,8 +1250,9 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
     double *inv_a = (double *)(base + kNoAllocInvOff);
     uint8_t *cf_a = (uint8_t *)(base + kNoAllocFlagOff);
     float4 *rs_a = (float4 *)(base + kNoAllocRsOff);
+    Split<float> *ms_a = (Split<float> *)(base + kNoAllocMsOff);
     Partial<float> *part = (Partial<float> *)(base + kNoAllocPartOff);
-    CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, st));
+    CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
     int n_groups = 0;
     if (s->n_windows > 0) {
         Geometry geo = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane);
@@ -1274,12 +1290,12 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
         L.n_row_blocks = geo.n_row_blocks;
         L.n_groups = geo.n_groups;
         L.warps = geo.warps;
-        CUDA_TRY(launch_plain<float>(L, a, n, rs_a, mean_a, (const float *)d->d_samples, d->nb, (const float4 *)s->rs,
-                                     s->mean, d_spans, d_gstart, part, st));
+        CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb, (const float4 *)s->rs,
+                                     (const Split<float> *)s->ms, d_spans, d_gstart, part, st));
         n_groups = geo.n_groups;
     }
     // with no dictionary window (n_groups = 0, g_first = -1) this writes +inf / -1
     CUDA_TRY(launch_finalize<float>(
-        fin_params<float>(nq, m, n_groups, part, a, mean_a, inv_a, cf_a, d, s, d_out_dist, d_out_idx), st));
+        fin_params<float>(nq, m, n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_out_dist, d_out_idx), st));
     return MP_OK;
 }

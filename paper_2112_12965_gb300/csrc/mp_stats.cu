@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
                                                                  double *__restrict__ mean,
                                                                  double *__restrict__ invstd,
                                                                  uint8_t *__restrict__ cflag,
-                                                                 vec4_t<T> *__restrict__ rs)
+                                                                 vec4_t<T> *__restrict__ rs,
+                                                                 Split<T> *__restrict__ ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t nw = n - m + 1;
@@ -181,6 +182,12 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
         mean[i] = mu;
         invstd[i] = inv_s;
         cflag[i] = is_const ? 1 : 0;
+        if (ms) {
+            Split<T> sp;
+            sp.hi = (T)mu;
+            sp.lo = (T)(mu - (double)sp.hi);
+            ms[i] = sp;
+        }
         if (rs) {
             vec4_t<T> r;
             if (i == 0) {
@@ -247,7 +254,7 @@ __global__ void k_dict_specials(const Span *__restrict__ spans, int32_t n_spans,
 
 template <typename T>
 cudaError_t launch_window_stats(const T *x, int64_t n, int32_t m, double *mean, double *invstd, uint8_t *cflag,
-                                vec4_t<T> *rs, cudaStream_t st)
+                                vec4_t<T> *rs, Split<T> *ms, cudaStream_t st)
 {
     const int64_t nw = n - m + 1;
     if (nw <= 0) return cudaSuccess;
@@ -258,7 +265,7 @@ cudaError_t launch_window_stats(const T *x, int64_t n, int32_t m, double *mean, 
         cudaError_t e = cudaFuncSetAttribute(k_window_stats<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_window_stats<T><<<(unsigned)grid, kStatsThreads, smem, st>>>(x, n, m, mean, invstd, cflag, rs);
+    k_window_stats<T><<<(unsigned)grid, kStatsThreads, smem, st>>>(x, n, m, mean, invstd, cflag, rs, ms);
     return cudaGetLastError();
 }
 
@@ -296,9 +303,9 @@ template cudaError_t launch_mark_invalid<float>(float4 *, int64_t, const int64_t
 template cudaError_t launch_mark_invalid<double>(dvec4 *, int64_t, const int64_t *, int32_t, int32_t, cudaStream_t);
 
 template cudaError_t launch_window_stats<float>(const float *, int64_t, int32_t, double *, double *, uint8_t *,
-                                                float4 *, cudaStream_t);
+                                                float4 *, Split<float> *, cudaStream_t);
 template cudaError_t launch_window_stats<double>(const double *, int64_t, int32_t, double *, double *, uint8_t *,
-                                                 dvec4 *, cudaStream_t);
+                                                 dvec4 *, Split<double> *, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float *, int64_t, int32_t *, cudaStream_t);
 template cudaError_t launch_check_finite<double>(const double *, int64_t, int32_t *, cudaStream_t);
 

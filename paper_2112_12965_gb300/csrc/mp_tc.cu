@@ -55,11 +55,11 @@ struct TcArgs {
     int64_t na, nq;
     int32_t m;
     int32_t n_groups;
-    const double *mean_a;
+    const Split<float> *ms_a;  // query window means, split
     const float *b;
     int64_t nb;
-    const double *mean_b;
-    const float4 *rs_b;  // z = 1/std (0: constant or invalid), w = 0 or -inf
+    const Split<float> *ms_b;  // dictionary window means, split
+    const float4 *rs_b;        // z = 1/std (0: constant or invalid), w = 0 or -inf
     const TcTile *tiles;
     const int32_t *group_start;
     Partial<float> *part;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(TcArgs p)
     if (tid == 0) mbar_init(bar, 1);
 
     // query operand, once for all K
-    const float s_a = (float)p.mean_a[i0 < p.nq ? i0 : p.nq - 1];
+    const float s_a = p.ms_a[i0 < p.nq ? i0 : p.nq - 1].hi;
     for (int e = tid; e < p.ra_rows + EPR; e += kTcThreads) {
         const int64_t j = i0 + e;
         raw[e] = (j < p.na) ? p.a[j] - s_a : 0.f;
@@ -263,7 +263,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(TcArgs p)
     const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
 
     const int64_t row = i0 + tid;
-    const float da = (row < p.nq) ? (float)(p.mean_a[row] - (double)s_a) : 0.f;
+    float da = 0.f;
+    if (row < p.nq) {
+        const Split<float> ma = p.ms_a[row];
+        da = (ma.hi - s_a) + ma.lo;
+    }
     float best = -INFINITY;
     int32_t bchunk = -1;
     uint32_t phase = 0;
@@ -272,14 +276,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(TcArgs p)
     const int t_lo = p.group_start[grp], t_hi = p.group_start[grp + 1];
     for (int t = t_lo; t < t_hi && !aborted; ++t) {
         const TcTile tile = p.tiles[t];
-        const float s_b = (float)p.mean_b[tile.g0];
+        const float s_b = p.ms_b[tile.g0].hi;
         // column terms of the epilogue: w = m * (mean_b - s_b), z = 1/std, p = 0 / -inf
         for (int n = tid; n < kTcMaxN; n += kTcThreads) {
             float4 v = make_float4(0.f, 0.f, -INFINITY, 0.f);
             if (n < tile.nvalid) {
                 const int64_t g = tile.g0 + n;
                 const float4 r = p.rs_b[g];
-                v.x = (float)((double)m * (p.mean_b[g] - (double)s_b));
+                const Split<float> mb = p.ms_b[g];
+                v.x = (float)m * ((mb.hi - s_b) + mb.lo);
                 v.y = r.z;
                 v.z = r.w;
             }
@@ -467,8 +472,8 @@ void tc_free_pack(void *pack)
 }
 
 int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
-            const double *mean_b, const double *, const void *rs_b, const float *a, int64_t n, int32_t m,
-            const double *mean_a, const double *, const uint8_t *, int64_t, int64_t, Partial<float> *part,
+            const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
+            Partial<float> *part,
             int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail)
 {
     TcPlan P;
@@ -515,10 +520,10 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     A.nq = nq;
     A.m = m;
     A.n_groups = ng;
-    A.mean_a = mean_a;
+    A.ms_a = (const Split<float> *)ms_a;
     A.b = b;
     A.nb = nb;
-    A.mean_b = mean_b;
+    A.ms_b = (const Split<float> *)ms_b;
     A.rs_b = (const float4 *)rs_b;
     A.tiles = use->tiles;
     A.group_start = use->group_start;

@@ -24,12 +24,11 @@ void tc_load_tune_cache(const char *path);
 void tc_free_pack(void *pack);
 
 // Launch the tensor-core join (kernel K3) of an FP32 query whose window
-// statistics are computed; writes part[group * nq + row] (the same partial
+// statistics are computed (ms_*: Split<float> means, rs_*: float4 terms); writes part[group * nq + row] (the same partial
 // format as the plain kernel) and *n_groups_out. *err is set to 1 on a
 // device-side timeout. variant: 0 = split BF16 (3 products), 1 = TF32.
 int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
-            const double *mean_b, const double *invstd_b, const void *rs_b, const float *a, int64_t n, int32_t m,
-            const double *mean_a, const double *invstd_a, const uint8_t *cflag_a, int64_t g_const, int64_t g_first,
+            const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
             Partial<float> *part, int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail);
 
 }  // namespace mpd
