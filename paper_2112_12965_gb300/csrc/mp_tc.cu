@@ -40,7 +40,6 @@
 namespace mpd {
 namespace {
 
-constexpr int kTcThreads = 128;
 constexpr int kTcMaxN = 256;           // TMEM columns (FP32 accumulators) per CTA
 constexpr size_t kTcSmemLimit = 225 * 1024;
 
@@ -64,10 +63,12 @@ struct TcArgs {
     const int32_t *group_start;
     Partial<float> *part;
     int32_t *err;
-    int32_t ra_rows;  // rows of the query Hankel buffer
-    int32_t rb_rows;  // rows of the dictionary Hankel buffer (one K-group)
-    int32_t qg;       // K-blocks per K-group
-    int32_t nkb;      // K-blocks in total
+    int32_t ra_rows;   // rows of the query Hankel buffer
+    int32_t nmax;      // widest tile
+    int32_t nkb;       // K-blocks
+    int32_t qg;        // K-blocks per stage (one stage = one tile's K-group)
+    int32_t rb_rows;   // rows of a stage buffer: (qg - 1) * values-per-row + nmax
+    int32_t n_stages;  // stage buffers in flight (1 or 2)
 };
 
 // ---------------------------------------------------------------------------
@@ -186,184 +187,368 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
+// Write one 16-byte chunk (EPC values) of a Hankel row: BF16 hi and lo
+// halves, or TF32 values.
+template <int VARIANT>
+__device__ __forceinline__ void put_chunk(const float *x, unsigned char *hi, unsigned char *lo, uint32_t off)
+{
+    if (VARIANT == 0) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            // packed conversions: two values per instruction
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+            const __nv_bfloat162 ll =
+                __floats2bfloat162_rn(x[2 * e] - __low2float(hh), x[2 * e + 1] - __high2float(hh));
+            h[e] = *reinterpret_cast<const uint32_t *>(&hh);
+            l[e] = *reinterpret_cast<const uint32_t *>(&ll);
+        }
+        *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+        *reinterpret_cast<float4 *>(hi + off) = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+    }
+}
+
 // Build rows [0, rows) of a row-shifted Hankel buffer from staged samples
 // raw[0 ..]: row rho, value j = raw[rho + j]. 16-byte chunk c of row rho is
-// stored at chunk position c ^ (rho & 7) (the 128-byte swizzle).
+// stored at chunk position c ^ (rho & 7) (the 128-byte swizzle). Thread t of
+// nthr (a multiple of 8) owns chunk column c = t % 8 of a contiguous run of
+// rows and slides a register window down them: one shared-memory load per
+// chunk instead of one per value.
 template <int VARIANT>
-__device__ __forceinline__ void build_hankel(const float *raw, int rows, unsigned char *hi, unsigned char *lo)
+__device__ __forceinline__ void build_hankel(const float *raw, int rows, unsigned char *hi, unsigned char *lo, int t,
+                                             int nthr)
 {
     constexpr int EPC = VARIANT == 0 ? 8 : 4;  // values per 16-byte chunk
-    for (int idx = threadIdx.x; idx < rows * 8; idx += kTcThreads) {
-        const int rho = idx >> 3, c = idx & 7;
-        const uint32_t off = (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4);
-        const float *src = raw + rho + c * EPC;
-        if (VARIANT == 0) {
-            uint32_t h[4], l[4];
+    const int c = t & 7, groups = nthr >> 3, rg = t >> 3;
+    const int rpg = (rows + groups - 1) / groups;
+    const int r0 = rg * rpg, r1 = min(rows, r0 + rpg);
+    if (r0 >= r1) return;
+    float w[EPC];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float x0 = src[2 * e], x1 = src[2 * e + 1];
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-                h[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                l[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    for (int e = 0; e < EPC; ++e) w[e] = raw[r0 + c * EPC + e];
+    for (int rb = r0; rb < r1; rb += EPC) {
+#pragma unroll
+        for (int u = 0; u < EPC; ++u) {
+            const int rho = rb + u;
+            if (rho < r1) {
+                float x[EPC];
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) x[e] = w[(u + e) % EPC];
+                put_chunk<VARIANT>(x, hi, lo, (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4));
+                // slot u held raw[rho + c*EPC]; replace it with the value row rho + EPC needs last
+                w[u] = raw[rho + c * EPC + EPC];
             }
-            *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-        } else {
-            *reinterpret_cast<float4 *>(hi + off) =
-                make_float4(to_tf32(src[0]), to_tf32(src[1]), to_tf32(src[2]), to_tf32(src[3]));
         }
     }
 }
 
-template <int VARIANT>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc(TcArgs p)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
-    constexpr int EPR = VARIANT == 0 ? 64 : 32;   // K values per 128-byte row
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Named barrier that also ANDs a predicate over its threads, so that every
+// thread of a role takes the same branch after a wait that may have failed.
+__device__ __forceinline__ bool named_sync_and(int id, int nthreads, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Warp roles of the pipelined kernel.
+constexpr int kMmaWarp = 0;                  // TMEM owner; lane 0 issues the MMAs
+constexpr int kBuildWarp0 = 1;               // warps 1..8 build operand stages (two groups of 4)
+constexpr int kEpiWarp0 = 9;                 // warps 9..12 read the accumulators
+constexpr int kTcThreadsP = 13 * 32;
+constexpr int kRoleThreads = 128;            // threads of one builder group / of the epilogue
+constexpr int kBuildThreads = 256;           // all builders
+constexpr int kBarBuild = 1, kBarGroup0 = 2, kBarEpi = 4;  // named barriers (group g uses kBarGroup0 + g)
+constexpr uint32_t kTmemCols = 2 * kTcMaxN;  // two accumulators of 256 FP32 columns
+
+// The join of 128 query windows (one CTA) against the tiles of one column
+// group. A stage holds the dictionary operand of one tile for one K-block
+// (64 BF16 / 32 TF32 values of K); builders fill stage s while the MMAs read
+// the other; each tile's accumulator alternates between two TMEM buffers so
+// that the epilogue of tile t overlaps the MMAs of tile t + 1.
+template <int VARIANT>
+__global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
+{
+    constexpr int EPR = VARIANT == 0 ? 64 : 32;   // K values per 128-byte row (one K-block)
     constexpr int KSTEP = VARIANT == 0 ? 16 : 8;  // K values per MMA
     constexpr int NHL = VARIANT == 0 ? 2 : 1;     // hi/lo buffers
-    constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const uint32_t a_bytes = (uint32_t)p.ra_rows * 128u, b_bytes = (uint32_t)p.rb_rows * 128u;
+    const int NS = p.n_stages;
+    const uint32_t a_bytes = (uint32_t)p.ra_rows * 128u, st_bytes = (uint32_t)p.rb_rows * 128u;
     unsigned char *ha[2] = {base, base + a_bytes};
-    unsigned char *hb0 = base + NHL * a_bytes;
-    unsigned char *hb[2] = {hb0, hb0 + b_bytes};
-    float *raw = reinterpret_cast<float *>(hb0 + NHL * b_bytes);
-    const int raw_len = max(p.ra_rows, p.rb_rows) + EPR;
-    float4 *colp = reinterpret_cast<float4 *>(raw + ((raw_len + 3) & ~3));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    unsigned char *hb = base + NHL * a_bytes;  // stage s, half h at hb + (s * NHL + h) * st_bytes
+    float *raw = reinterpret_cast<float *>(hb + NS * NHL * st_bytes);  // query staging, then two tile stagings
+    const int raw_tile = p.nmax + p.m + EPR;  // samples a tile's stages read
+    const int raw_a = p.ra_rows + EPR;
+    float *raw_b[2] = {raw + raw_a, raw + raw_a + raw_tile};
+    float4 *colp = reinterpret_cast<float4 *>(raw + ((raw_a + 2 * raw_tile + 3) & ~3));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
+    uint64_t *full_a = bars + 0;
+    uint64_t *full_b = bars + 1;     // [2]
+    uint64_t *empty_b = bars + 3;    // [2]
+    uint64_t *acc_full = bars + 5;   // [2]
+    uint64_t *acc_empty = bars + 7;  // [2]
+    uint64_t *drain = bars + 9;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t rb = blockIdx.x / p.n_groups;
     const int grp = blockIdx.x % p.n_groups;
     const int64_t i0 = rb * 128;
     const int m = p.m;
+    const int t_lo = p.group_start[grp], t_hi = p.group_start[grp + 1];
 
-    if (warp == 0) tmem_alloc(tmem_slot, kTcMaxN);
-    if (tid == 0) mbar_init(bar, 1);
-
-    // query operand, once for all K
-    const float s_a = p.ms_a[i0 < p.nq ? i0 : p.nq - 1].hi;
-    for (int e = tid; e < p.ra_rows + EPR; e += kTcThreads) {
-        const int64_t j = i0 + e;
-        raw[e] = (j < p.na) ? p.a[j] - s_a : 0.f;
+    if (warp == kMmaWarp) tmem_alloc(tmem_slot, kTmemCols);
+    if (tid == 0) {
+        *abort_flag = 0;
+        mbar_init(full_a, kBuildThreads);
+        for (int s = 0; s < 2; ++s) {
+            // two stages: each is built by one builder group; one stage: by both
+            mbar_init(&full_b[s], NS == 2 ? kRoleThreads : kBuildThreads);
+            mbar_init(&empty_b[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kRoleThreads);
+        }
+        mbar_init(drain, 1);
     }
-    __syncthreads();
-    build_hankel<VARIANT>(raw, p.ra_rows, ha[0], ha[1]);
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = *tmem_slot;
-    const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
 
-    const int64_t row = i0 + tid;
-    float da = 0.f;
-    if (row < p.nq) {
-        const Split<float> ma = p.ms_a[row];
-        da = (ma.hi - s_a) + ma.lo;
-    }
-    float best = -INFINITY;
-    int32_t bchunk = -1;
-    uint32_t phase = 0;
-    bool aborted = false;
-
-    const int t_lo = p.group_start[grp], t_hi = p.group_start[grp + 1];
-    for (int t = t_lo; t < t_hi && !aborted; ++t) {
-        const TcTile tile = p.tiles[t];
-        const float s_b = p.ms_b[tile.g0].hi;
-        // column terms of the epilogue: w = m * (mean_b - s_b), z = 1/std, p = 0 / -inf
-        for (int n = tid; n < kTcMaxN; n += kTcThreads) {
-            float4 v = make_float4(0.f, 0.f, -INFINITY, 0.f);
-            if (n < tile.nvalid) {
-                const int64_t g = tile.g0 + n;
-                const float4 r = p.rs_b[g];
-                const Split<float> mb = p.ms_b[g];
-                v.x = (float)m * ((mb.hi - s_b) + mb.lo);
-                v.y = r.z;
-                v.z = r.w;
-            }
-            colp[n] = v;
-        }
-        for (int q0 = 0; q0 < p.nkb && !aborted; q0 += p.qg) {
-            const int q1 = min(p.nkb, q0 + p.qg);
-            const int rows_b = (q1 - q0 - 1) * EPR + tile.nmma;
-            for (int e = tid; e < rows_b + EPR; e += kTcThreads) {
-                const int64_t j = tile.g0 + (int64_t)q0 * EPR + e;
-                raw[e] = (j < p.nb) ? p.b[j] - s_b : 0.f;
-            }
-            __syncthreads();
-            build_hankel<VARIANT>(raw, rows_b, hb[0], hb[1]);
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
+    if (warp == kMmaWarp) {
+        // ---------------- MMA issue (one lane) ----------------
+        if (lane == 0) {
+            bool ok = role_wait(full_a, 0, abort_flag);
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(ha[0]), a1 = smem_u32(ha[NHL - 1]);
+            int j = 0;  // stage counter
+            for (int t = t_lo; ok && t < t_hi; ++t) {
+                const TcTile tile = p.tiles[t];
+                const int ab = (t - t_lo) & 1;
+                const int k_t = (t - t_lo) >> 1;
+                if (k_t >= 1 && !(ok = role_wait(&acc_empty[ab], (k_t - 1) & 1, abort_flag))) break;
                 tc_fence_after();
+                const uint32_t d_tmem = taddr + (uint32_t)(ab * kTcMaxN);
                 const uint32_t idesc = instr_desc<VARIANT>(tile.nmma);
-                const uint32_t a0 = smem_u32(ha[0]), a1 = smem_u32(ha[NHL - 1]);
-                const uint32_t b0 = smem_u32(hb[0]), b1 = smem_u32(hb[NHL - 1]);
-                for (int q = q0; q < q1; ++q) {
-                    const int ksteps = min(EPR, m - q * EPR) / KSTEP;
-                    const uint32_t ao = (uint32_t)(q * EPR) * 128u, bo = (uint32_t)((q - q0) * EPR) * 128u;
-                    for (int s = 0; s < ksteps; ++s) {
-                        const uint32_t acc0 = (q == 0 && s == 0) ? 0u : 1u;
-                        mma<VARIANT>(taddr, smem_desc(a0 + ao + 32u * s), smem_desc(b0 + bo + 32u * s), idesc, acc0);
-                        if (VARIANT == 0) {
-                            mma<VARIANT>(taddr, smem_desc(a0 + ao + 32u * s), smem_desc(b1 + bo + 32u * s), idesc, 1u);
-                            mma<VARIANT>(taddr, smem_desc(a1 + ao + 32u * s), smem_desc(b0 + bo + 32u * s), idesc, 1u);
+                for (int q0 = 0; q0 < p.nkb; q0 += p.qg, ++j) {
+                    const int q1 = min(p.nkb, q0 + p.qg);
+                    const int s = j % NS;
+                    if (!(ok = role_wait(&full_b[s], (j / NS) & 1, abort_flag))) break;
+                    tc_fence_after();
+                    const uint32_t b0 = smem_u32(hb + (s * NHL) * st_bytes);
+                    const uint32_t b1 = smem_u32(hb + (s * NHL + NHL - 1) * st_bytes);
+                    for (int q = q0; q < q1; ++q) {
+                        const uint32_t ao = (uint32_t)(q * EPR) * 128u, bo = (uint32_t)((q - q0) * EPR) * 128u;
+                        const int ksteps = min(EPR, m - q * EPR) / KSTEP;
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t acc0 = (q == 0 && k == 0) ? 0u : 1u;
+                            mma<VARIANT>(d_tmem, smem_desc(a0 + ao + 32u * k), smem_desc(b0 + bo + 32u * k), idesc,
+                                         acc0);
+                            if (VARIANT == 0) {
+                                mma<VARIANT>(d_tmem, smem_desc(a0 + ao + 32u * k), smem_desc(b1 + bo + 32u * k),
+                                             idesc, 1u);
+                                mma<VARIANT>(d_tmem, smem_desc(a1 + ao + 32u * k), smem_desc(b0 + bo + 32u * k),
+                                             idesc, 1u);
+                            }
                         }
                     }
+                    mma_commit(&empty_b[s]);  // stage s is free once these MMAs are done
                 }
-                mma_commit(bar);
+                if (!ok) break;
+                mma_commit(&acc_full[ab]);  // tile t's accumulator is complete
             }
-            const bool ok = mbar_wait(bar, phase, kWaitCycles);
-            aborted = __syncthreads_or(!ok) != 0;
-            if (!aborted) phase ^= 1u;
+            // every MMA issued so far must finish before the TMEM is released
+            mma_commit(drain);
+            role_wait(drain, 0, abort_flag) || mbar_wait(drain, 0, 4000000000LL);
         }
-        if (aborted) break;
-        // epilogue: this thread's query window against the tile's windows
-        tc_fence_after();
-        const int ncols = (tile.nmma + 31) & ~31;
-        for (int c32 = 0; c32 < ncols; c32 += 32) {
-            uint32_t v[32];
-            tmem_ld32(t_lane + (uint32_t)c32, v);
+        __syncwarp();
+    } else if (warp < kEpiWarp0) {
+        // ---------------- operand builders ----------------
+        // Two groups of four warps. With two stage buffers, group g builds
+        // stage buffer g (every other stage), so each group has two stages'
+        // worth of MMA time per build; with one buffer both groups build it.
+        const int bt = tid - kBuildWarp0 * 32;  // 0 .. 255
+        const int bgrp = bt >> 7, gt = bt & (kRoleThreads - 1);
+        const float s_a = p.ms_a[i0 < p.nq ? i0 : p.nq - 1].hi;
+        for (int e = bt; e < raw_a; e += kBuildThreads) {
+            const int64_t jj = i0 + e;
+            raw[e] = (jj < p.na) ? p.a[jj] - s_a : 0.f;
+        }
+        named_sync(kBarBuild, kBuildThreads);
+        build_hankel<VARIANT>(raw, p.ra_rows, ha[0], ha[1], bt, kBuildThreads);
+        fence_async_smem();
+        mbar_arrive(full_a);
+        // Each tile's samples b[g0 .. g0 + nmma + m + values-per-row) are staged
+        // once in shared memory (two tile buffers); the next tile's samples are
+        // loaded into registers at the top of the current tile, so their
+        // global-memory latency overlaps the current tile's MMAs.
+        constexpr int kPre = 6;  // covers nmax + m + values-per-row <= kPre * 256
+        float pre[kPre];
+        auto load_tile = [&](int t) {
+            const TcTile tl = p.tiles[t];
+            const float sb = p.ms_b[tl.g0].hi;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float cm = -INFINITY;
+            for (int k = 0; k < kPre; ++k) {
+                const int e = bt + k * kBuildThreads;
+                const int64_t jj = tl.g0 + e;
+                pre[k] = (e < raw_tile && jj < p.nb) ? p.b[jj] - sb : 0.f;
+            }
+        };
+        auto store_tile = [&](float *dst) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const float4 cp = colp[c32 + 16 * h + u];
-                    const float cov = fmaf(-da, cp.x, __uint_as_float(v[16 * h + u]));
-                    cm = fmaxf(cm, fmaf(cov, cp.y, cp.z));
+            for (int k = 0; k < kPre; ++k) {
+                const int e = bt + k * kBuildThreads;
+                if (e < raw_tile) dst[e] = pre[k];
+            }
+        };
+        if (t_lo < t_hi) {
+            load_tile(t_lo);
+            store_tile(raw_b[0]);
+        }
+        named_sync(kBarBuild, kBuildThreads);
+        const int nthr = NS == 2 ? kRoleThreads : kBuildThreads;
+        const int tt = NS == 2 ? gt : bt;
+        const int bar_id = NS == 2 ? kBarGroup0 + bgrp : kBarBuild;
+        int j = 0;
+        bool ok = true;
+        for (int t = t_lo; ok && t < t_hi; ++t) {
+            const TcTile tile = p.tiles[t];
+            const float *rt = raw_b[(t - t_lo) & 1];
+            if (t + 1 < t_hi) load_tile(t + 1);
+            j = (t - t_lo) * ((p.nkb + p.qg - 1) / p.qg);  // stages before this tile
+            bool gok = true;
+            for (int q0 = 0; q0 < p.nkb; q0 += p.qg, ++j) {
+                const int s = j % NS;
+                if (NS == 2 && s != bgrp) continue;  // the other group's stage
+                const int q1 = min(p.nkb, q0 + p.qg);
+                if (j >= NS) {
+                    const bool w = role_wait(&empty_b[s], ((j / NS) - 1) & 1, abort_flag);
+                    if (!(gok = named_sync_and(bar_id, nthr, w))) break;
                 }
-                if (cm > best) {
-                    best = cm;
-                    bchunk = (int32_t)(tile.g0 + c32 + 16 * h);
+                const int rows = (q1 - q0 - 1) * EPR + tile.nmma;
+                build_hankel<VARIANT>(rt + q0 * EPR, rows, hb + (s * NHL) * st_bytes,
+                                      hb + (s * NHL + NHL - 1) * st_bytes, tt, nthr);
+                fence_async_smem();
+                mbar_arrive(&full_b[s]);
+            }
+            // every builder takes the same branch (j is recomputed per tile below)
+            if (!(ok = named_sync_and(kBarBuild, kBuildThreads, gok))) break;
+            if (t + 1 < t_hi) store_tile(raw_b[(t + 1 - t_lo) & 1]);
+            named_sync(kBarBuild, kBuildThreads);
+        }
+    } else {
+        // ---------------- epilogue: one query window per thread ----------------
+        const int quad = warp & 3;                 // TMEM lanes this warp may read
+        const int row_in = quad * 32 + lane;       // query window within the CTA
+        const int et = tid - kEpiWarp0 * 32;
+        const int64_t row = i0 + row_in;
+        const float s_a = p.ms_a[i0 < p.nq ? i0 : p.nq - 1].hi;
+        float da = 0.f;
+        if (row < p.nq) {
+            const Split<float> ma = p.ms_a[row];
+            da = (ma.hi - s_a) + ma.lo;
+        }
+        float best = -INFINITY;
+        int32_t bchunk = -1;
+        bool ok = true;
+        for (int t = t_lo; ok && t < t_hi; ++t) {
+            const TcTile tile = p.tiles[t];
+            const int ab = (t - t_lo) & 1;
+            const int k_t = (t - t_lo) >> 1;
+            // column terms: w = m (mean_b - s_b), z = 1/std, penalty 0 / -inf
+            const float s_b = p.ms_b[tile.g0].hi;
+            for (int n = et; n < kTcMaxN; n += kRoleThreads) {
+                float4 v = make_float4(0.f, 0.f, -INFINITY, 0.f);
+                if (n < tile.nvalid) {
+                    const int64_t g = tile.g0 + n;
+                    const float4 r = p.rs_b[g];
+                    const Split<float> mb = p.ms_b[g];
+                    v.x = (float)m * ((mb.hi - s_b) + mb.lo);
+                    v.y = r.z;
+                    v.z = r.w;
+                }
+                colp[n] = v;
+            }
+            named_sync(kBarEpi, kRoleThreads);
+            ok = role_wait(&acc_full[ab], k_t & 1, abort_flag);
+            if (!(ok = named_sync_and(kBarEpi, kRoleThreads, ok))) break;
+            tc_fence_after();
+            const uint32_t t_lane = taddr + (uint32_t)(ab * kTcMaxN) + ((uint32_t)(quad * 32) << 16);
+            const int ncols = (tile.nmma + 31) & ~31;
+            for (int c32 = 0; c32 < ncols; c32 += 32) {
+                uint32_t v[32];
+                tmem_ld32(t_lane + (uint32_t)c32, v);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float cm = -INFINITY;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const float4 cp = colp[c32 + 16 * h + u];
+                        const float cov = fmaf(-da, cp.x, __uint_as_float(v[16 * h + u]));
+                        cm = fmaxf(cm, fmaf(cov, cp.y, cp.z));
+                    }
+                    if (cm > best) {
+                        best = cm;
+                        bchunk = (int32_t)(tile.g0 + c32 + 16 * h);
+                    }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[ab]);
+            named_sync(kBarEpi, kRoleThreads);  // colp is rewritten for the next tile
         }
-        tc_fence_before();
-        __syncthreads();  // TMEM reads done before the next tile's MMAs overwrite it
+        if (ok && !*abort_flag && row < p.nq) {
+            Partial<float> pv;
+            pv.q = best;
+            pv.g = bchunk;
+            p.part[(int64_t)grp * p.nq + row] = pv;
+        }
     }
 
-    if (aborted) {
-        if (tid == 0) atomicExch(p.err, 1);
-        // let any MMA still in flight finish before the TMEM is released
-        mbar_wait(bar, phase, kWaitCycles);
-    } else if (row < p.nq) {
-        Partial<float> v;
-        v.q = best;
-        v.g = bchunk;
-        p.part[(int64_t)grp * p.nq + row] = v;
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(taddr, kTcMaxN);
+    if (tid == 0 && *abort_flag) atomicExch(p.err, 1);
+    if (warp == kMmaWarp) tmem_dealloc(taddr, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,54 +556,72 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(TcArgs p)
 // ---------------------------------------------------------------------------
 struct TcPlan {
     int variant;
-    int epr, kstep, nhl;
-    int nkb, ra_rows, rb_rows, qg, nmax;
+    int m;
+    int epr, kstep, nhl, nprod;
+    int nkb, ra_rows, nmax, qg, rb_rows, n_stages;
     size_t smem;
 };
 
 size_t plan_smem(const TcPlan &P)
 {
-    const size_t raw_len = (size_t)std::max(P.ra_rows, P.rb_rows) + P.epr;
-    return 1024 + (size_t)P.nhl * 128 * (P.ra_rows + P.rb_rows) + ((raw_len + 3) & ~(size_t)3) * 4 +
-           kTcMaxN * sizeof(float4) + 16 + 16;
+    const size_t raw = (size_t)(P.ra_rows + P.epr) + 2 * (size_t)(P.nmax + P.m + P.epr);
+    return 1024 + (size_t)P.nhl * 128 * ((size_t)P.ra_rows + (size_t)P.n_stages * P.rb_rows) +
+           ((raw + 3) & ~(size_t)3) * 4 + kTcMaxN * sizeof(float4) + 11 * 8 + 16;
+}
+
+// Estimated SM clocks per tile: the MMAs (or the shared-memory traffic they
+// and the builders cause, if larger) plus, with one stage, the builders'
+// time that cannot overlap the MMAs.
+double plan_clocks(const TcPlan &P, int m)
+{
+    const double ksteps = (double)m / P.kstep;
+    const double mma = ksteps * P.nprod * 128.0 * P.nmax / 256.0;
+    const double reads = ksteps * P.nprod * (128.0 + P.nmax) * 32.0;
+    const int groups = (P.nkb + P.qg - 1) / P.qg;
+    const double writes = (double)groups * P.rb_rows * 128.0 * P.nhl;
+    const double build = (double)groups * P.rb_rows * 8.0 / kBuildThreads * (P.variant == 0 ? 16.0 : 10.0);
+    const double smem = (reads + writes) / 128.0;
+    return std::max(mma, smem) + (P.n_stages == 1 ? build : 0.0);
 }
 
 bool make_plan(int variant, int m, TcPlan *out)
 {
     TcPlan P;
     P.variant = variant;
+    P.m = m;
     P.epr = variant == 0 ? 64 : 32;
     P.kstep = variant == 0 ? 16 : 8;
     P.nhl = variant == 0 ? 2 : 1;
+    P.nprod = variant == 0 ? 3 : 1;
     if (m < P.kstep || m % P.kstep != 0) return false;
     P.nkb = (m + P.epr - 1) / P.epr;
     P.ra_rows = (P.nkb - 1) * P.epr + 128;
-    // Among the (tile width, K-group) pairs that fit, take the one with the
-    // least dictionary-operand building per (window x K value), with a
-    // penalty for narrow tiles (each MMA then re-reads the query operand for
-    // fewer columns).
+    // one CTA per SM: the two accumulators use all 512 TMEM columns
     bool found = false;
-    double best_score = 1e30;
-    TcPlan best{};
-    for (int nmax : {256, 128, 64}) {
-        for (int qg = 1; qg <= P.nkb; ++qg) {
-            TcPlan C = P;
-            C.nmax = nmax;
-            C.qg = qg;
-            C.rb_rows = (qg - 1) * P.epr + nmax;
-            // at least 80 KB: at most two CTAs (2 x 256 TMEM columns) per SM
-            C.smem = std::max<size_t>(plan_smem(C), 80 * 1024);
-            if (C.smem > kTcSmemLimit) break;
-            const double build = (double)C.rb_rows / ((double)nmax * qg);
-            const double score = build + (nmax == 64 ? 0.5 : (nmax == 128 ? 0.15 : 0.0));
-            if (score < best_score) {
-                best_score = score;
-                best = C;
-                found = true;
+    double best = 1e300;
+    TcPlan bestP{};
+    for (int nmax : {256, 128}) {
+        for (int ns : {2, 1}) {
+            for (int qg = 1; qg <= P.nkb; ++qg) {
+                TcPlan C = P;
+                C.nmax = nmax;
+                C.n_stages = ns;
+                C.qg = qg;
+                C.rb_rows = (qg - 1) * P.epr + nmax;
+                // at least 120 KB, so that two CTAs never share an SM
+                C.smem = std::max<size_t>(plan_smem(C), 120 * 1024);
+                if (C.smem > kTcSmemLimit) break;
+                if (nmax + m + P.epr > 6 * kBuildThreads) continue;  // the builders' tile prefetch
+                const double per_col = plan_clocks(C, m) / nmax;
+                if (per_col < best) {
+                    best = per_col;
+                    bestP = C;
+                    found = true;
+                }
             }
         }
     }
-    if (found) *out = best;
+    if (found) *out = bestP;
     return found;
 }
 
@@ -432,8 +635,6 @@ struct TcPack {
 struct TcPacks {
     std::vector<TcPack> packs;
 };
-
-int tune_choice_m = -1;
 
 }  // namespace
 
@@ -530,14 +731,16 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     A.part = part;
     A.err = err;
     A.ra_rows = P.ra_rows;
-    A.rb_rows = P.rb_rows;
-    A.qg = P.qg;
+    A.nmax = P.nmax;
     A.nkb = P.nkb;
+    A.qg = P.qg;
+    A.rb_rows = P.rb_rows;
+    A.n_stages = P.n_stages;
     cudaError_t e;
     auto launch = [&](auto kern) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
         if (e == cudaSuccess) {
-            kern<<<(unsigned)(n_row_blocks * ng), kTcThreads, P.smem, st>>>(A);
+            kern<<<(unsigned)(n_row_blocks * ng), kTcThreadsP, P.smem, st>>>(A);
             e = cudaGetLastError();
         }
     };
