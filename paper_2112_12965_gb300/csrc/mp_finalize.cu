@@ -42,6 +42,13 @@ __device__ __forceinline__ double pair_distance(const T *a, int64_t i, Split<T> 
     return (double)sqrt(acc);
 }
 
+// k values staged per pass of the re-scoring, and the padded shared-memory
+// index (one pad slot every 8 values: lanes reading with a stride of 8 values
+// hit distinct banks).
+constexpr int kFinChunk = 256;
+__device__ __forceinline__ int fpad(int e) { return e + (e >> 3); }
+constexpr int kFinWarpVals = (kFinChunk + kChunk) + ((kFinChunk + kChunk) >> 3) + 1;
+
 template <typename T>
 __device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
 {
@@ -52,7 +59,10 @@ __device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
 template <typename T>
 __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
 {
+    __shared__ T fin_smem[8][2 * kFinWarpVals];
     const int lane = threadIdx.x & 31;
+    T *wa = fin_smem[threadIdx.x >> 5];
+    T *wb = wa + kFinWarpVals;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double sqrt_m = sqrt((double)p.m);
@@ -91,32 +101,45 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                 }
             } else {
                 if (g >= 0) {
-                    // 2. re-score the chunk's windows g .. g + kChunk - 1. Lane l sums the
-                    // products of a contiguous range of k for all candidates (a sliding
-                    // window of dictionary samples in registers), then a transposing
-                    // butterfly leaves candidate (l & 15)'s total in lane l.
+                    // 2. re-score the chunk's windows g .. g + kChunk - 1. The warp stages
+                    // the shifted query window and the candidates' samples in shared
+                    // memory with coalesced loads, kFinChunk values of k at a time; lane l
+                    // then sums the products of a contiguous range of k for all
+                    // candidates (a sliding window of dictionary samples in registers),
+                    // and a transposing butterfly leaves candidate (l & 15)'s total in lane l.
                     const Split<T> ma = p.ms_a[i];
                     const T sa = ma.hi, sb = p.ms_b[g].hi;
-                    const int kpl = (m + 31) >> 5;
-                    const int k0 = lane * kpl;
-                    const int k1 = min(m, k0 + kpl);
-                    T acc[kChunk], bw[kChunk];
+                    T acc[kChunk];
 #pragma unroll
-                    for (int c = 0; c < kChunk; ++c) {
-                        acc[c] = T(0);
-                        const int64_t j = (int64_t)g + k0 + c;
-                        bw[c] = (k0 < k1 && j < p.nb) ? p.b[j] - sb : T(0);
-                    }
-                    for (int kb = k0; kb < k1; kb += kChunk) {
-#pragma unroll
-                        for (int u = 0; u < kChunk; ++u) {
-                            const int k = kb + u;
-                            const T av = (k < k1) ? p.a[i + k] - sa : T(0);
-#pragma unroll
-                            for (int c = 0; c < kChunk; ++c) acc[c] = fma(av, bw[(c + u) & (kChunk - 1)], acc[c]);
-                            const int64_t j = (int64_t)g + k + kChunk;
-                            bw[u] = (k < k1 && j < p.nb) ? p.b[j] - sb : T(0);
+                    for (int c = 0; c < kChunk; ++c) acc[c] = T(0);
+                    for (int kc = 0; kc < m; kc += kFinChunk) {
+                        const int len = min(kFinChunk, m - kc);
+                        for (int e = lane; e < len; e += 32) wa[fpad(e)] = p.a[i + kc + e] - sa;
+                        for (int e = lane; e < len + kChunk; e += 32) {
+                            const int64_t j = (int64_t)g + kc + e;
+                            wb[fpad(e)] = (j < p.nb) ? p.b[j] - sb : T(0);
                         }
+                        __syncwarp();
+                        const int kpl = (len + 31) >> 5;
+                        const int k0 = lane * kpl;
+                        const int k1 = min(len, k0 + kpl);
+                        T bw[kChunk];
+#pragma unroll
+                        for (int c = 0; c < kChunk; ++c) bw[c] = (k0 < k1) ? wb[fpad(k0 + c)] : T(0);
+                        for (int kb = k0; kb < k1; kb += kChunk) {
+#pragma unroll
+                            for (int u = 0; u < kChunk; ++u) {
+                                const int k = kb + u;
+                                if (k < k1) {
+                                    const T av = wa[fpad(k)];
+#pragma unroll
+                                    for (int c = 0; c < kChunk; ++c)
+                                        acc[c] = fma(av, bw[(c + u) & (kChunk - 1)], acc[c]);
+                                    bw[u] = wb[fpad(k + kChunk)];
+                                }
+                            }
+                        }
+                        __syncwarp();  // the next chunk overwrites the staged samples
                     }
 #pragma unroll
                     for (int s = kChunk / 2; s >= 1; s >>= 1) {

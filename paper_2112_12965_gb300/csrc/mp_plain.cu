@@ -255,8 +255,11 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     }
 }
 
+// Four CTAs (16 warps) per SM for FP32 data: the kernel then fits in 128
+// registers without spilling, and the extra warps hide the shuffle and
+// shared-memory latencies of the recurrence.
 template <typename T, int kRows>
-__global__ void __launch_bounds__(128) k_plain(PlainParams<T> p)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_plain(PlainParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     plain_item<T, kRows>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(128) k_plain(PlainParams<T> p)
 // may belong to different requests (different query, dictionary and m). Items
 // are claimed in list order with a global counter.
 template <typename T, int kRows>
-__global__ void __launch_bounds__(128) k_plain_batched(const PlainParams<T> *__restrict__ reqs,
+__global__ void __launch_bounds__(128, 2) k_plain_batched(const PlainParams<T> *__restrict__ reqs,
                                                        const BatchItem *__restrict__ items, int32_t n_items,
                                                        int32_t *__restrict__ counter)
 {
