@@ -310,6 +310,98 @@ def serving_run(mp, n_requests, seed=7):
         mp.mp_shutdown(ctx)
 
 
+def _device_join_timed(mp, ctx, d, q, m, reps=3):
+    """Join a host query on the device; returns (dist, idx, join-kernel ms per launch)."""
+    import torch
+
+    qt = torch.from_numpy(q).cuda()
+    nq = len(q) - m + 1
+    dd = torch.empty(nq, dtype=torch.float64, device="cuda")
+    di = torch.empty(nq, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    mp.mp_ab_join_device(ctx, d, qt.data_ptr(), mp.MP_F32, len(q), m, dd.data_ptr(), di.data_ptr(), s.cuda_stream)
+    s.synchronize()
+    mp.mp_profile(ctx, True)
+    mp.mp_profile_read(ctx, reset=True)
+    for _ in range(reps):
+        mp.mp_ab_join_device(ctx, d, qt.data_ptr(), mp.MP_F32, len(q), m, dd.data_ptr(), di.data_ptr(),
+                             s.cuda_stream)
+    s.synchronize()
+    ms, n = mp.mp_profile_read(ctx, reset=True)
+    mp.mp_profile(ctx, False)
+    return dd.cpu().numpy(), di.cpu().numpy(), float(ms[mp.MP_PHASE_JOIN] / max(1, n[mp.MP_PHASE_JOIN]))
+
+
+def study_precision(mp, rows=256):
+    """Per-result distance error of each join form against the FP64 oracle (transportation workload)."""
+    import oracle
+    import synthetic
+
+    w = synthetic.workload("transport_4m_m512")
+    r = np.linspace(0, w.n_rows - 1, rows).astype(np.int64)
+    od, oi, od2 = oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=r)
+    ctx = mp.mp_init(device=0)
+    out = {"study": "precision", "workload": "transportation-like query 2^22 (seed 4), dictionary 256 x 2048 "
+           "(seed 5), m=512", "rows_checked": rows, "pairs": w.pairs, "forms": {}}
+    try:
+        d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+        for kname in ("plain", "bf16x3", "tf32"):
+            mp.mp_set_kernel(ctx, kernel_id(mp, kname))
+            dist, idx, jm = _device_join_timed(mp, ctx, d, w.query, w.m, reps=2)
+            err = np.abs(dist[r] - od)
+            uniq = (od2 - od) > 1e-3
+            out["forms"][kname] = {
+                "join_ms": jm, "pairs_per_s": w.pairs / (jm / 1e3),
+                "abs_err_max": float(err.max()), "abs_err_p99": float(np.percentile(err, 99)),
+                "abs_err_median": float(np.median(err)), "abs_err_mean": float(err.mean()),
+                "index_match": float(np.mean(idx[r] == oi)),
+                "index_match_where_gap_gt_1e-3": float(np.mean(idx[r][uniq] == oi[uniq])) if uniq.any() else None}
+        mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)
+    return out
+
+
+def study_dict_vs_orig(mp, k_discords=200, with_tf32=False):
+    """Join a 2^24 ECG-like query against the 128-segment dictionary and against the whole training series."""
+    import synthetic
+
+    wd = synthetic.workload("ecg_16m_m1024_dict")
+    wo = synthetic.workload("ecg_16m_m1024_orig")
+    m = wd.m
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    out = {"study": "dictionary vs original", "workload": "ECG-like query 2^24 (seed 7, 200 malformed beats); "
+           "dictionary 128 x 2048 cut from a normal-beat 2^22 training series (seed 6) vs that whole series; m=1024",
+           "pairs_dict": wd.pairs, "pairs_orig": wo.pairs}
+    try:
+        dd = mp.mp_dict_load(ctx, wd.dict_samples, wd.offsets, [m])
+        do = mp.mp_dict_load(ctx, wo.dict_samples, wo.offsets, [m])
+        Ph, _, ms_d = _device_join_timed(mp, ctx, dd, wd.query, m, reps=1)
+        P, _, ms_o = _device_join_timed(mp, ctx, do, wo.query, m, reps=1)
+        e_max, _ = mp.mp_emax(ctx, dd, wo.dict_samples, m)
+        diff = Ph - P
+        ih, _, cert = mp.mp_top_discords(Ph, k_discords, m // 2, e_max)
+        io, _, _ = mp.mp_top_discords(P, k_discords, m // 2)
+        overlap = float(np.mean([np.min(np.abs(io - i)) <= m // 2 for i in ih])) if len(ih) else 0.0
+        out.update({
+            "join_ms_dict": ms_d, "join_ms_orig": ms_o, "speedup": ms_o / ms_d,
+            "pairs_per_s_dict": wd.pairs / (ms_d / 1e3), "pairs_per_s_orig": wo.pairs / (ms_o / 1e3),
+            "e_max": e_max, "max_P_hat_minus_P": float(diff.max()), "min_P_hat_minus_P": float(diff.min()),
+            "mean_P_hat_minus_P": float(diff.mean()),
+            "lemma1_holds": bool(np.all(diff >= -2e-4)), "lemma2_holds": bool(np.all(diff <= e_max + 2e-4)),
+            "top_discord_overlap": overlap, "k_discords": len(ih), "top1_certified": cert})
+        if with_tf32:
+            mp.mp_set_kernel(ctx, mp.MP_KERNEL_TC_TF32)
+            Pt, _, ms_t = _device_join_timed(mp, ctx, dd, wd.query, m, reps=1)
+            out["tf32_dict_join_ms"] = ms_t
+            out["tf32_vs_plain_max_abs_diff"] = float(np.max(np.abs(Pt - Ph)))
+        mp.mp_dict_free(ctx, dd)
+        mp.mp_dict_free(ctx, do)
+    finally:
+        mp.mp_shutdown(ctx)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,6 +411,8 @@ def main():
     ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "auto"])
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--study", choices=["precision", "dict-vs-orig"], default=None,
+                    help="run a study instead of the headline benchmark (one JSON line)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the query (profiling captures of a small case); 1.0 = the full workload")
     args = ap.parse_args()
@@ -344,6 +438,12 @@ def main():
     g.build()
     import paper_2112_12965_gb300 as mp
     import synthetic
+
+    if args.study:
+        res = study_precision(mp) if args.study == "precision" else study_dict_vs_orig(mp, with_tf32=True)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
 
     w = synthetic.workload(WORKLOAD, scale=args.scale)
     if rank > 0:  # weak scaling: each rank joins its own query of the same size

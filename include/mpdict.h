@@ -86,7 +86,7 @@ typedef struct mp_config {
     int32_t max_inflight;  /* serving: requests whose work may be on the device at once */
     int32_t max_batch;     /* serving: requests merged into one persistent launch */
     size_t mem_budget;     /* serving: device bytes that admitted requests may hold; 0 = half the free memory at init */
-    const char *tune_cache;/* autotune cache file (JSON lines), or NULL for none */
+    const char *tune_cache;/* autotuner cache file (JSON lines, see mp_autotune), or NULL for none */
 } mp_config;
 
 /* Default configuration (device 0, AUTO kernel, 8 in flight, batch 64). */
@@ -206,6 +206,49 @@ int mp_poll(mp_ctx *ctx, uint64_t ticket, int32_t *state, double *latency_s);
 
 /* Block until every submitted request has finished or timeout_s passes (MP_E_TIMEOUT). */
 int mp_drain(mp_ctx *ctx, double timeout_s);
+
+/*
+ * e_max of Sec. 3.3: the largest distance from a length-m window of the
+ * series T_B the dictionary was learned from to its nearest dictionary window,
+ * e_max = max_i NNDist(T_B[i : i+m], D_{B,m}), computed with the join
+ * (mp_ab_join of T_B against the dictionary). By Lemma 2 every approximate
+ * profile value exceeds the exact one by at most e_max when the dictionary's
+ * windows are windows of T_B (Proposition 1). t_b is a host series of n_b
+ * samples; *argmax (may be NULL) receives the window attaining the maximum.
+ */
+int mp_emax(mp_ctx *ctx, const mp_dict *dict, const void *t_b, int32_t dtype, int64_t n_b, int32_t m, double *e_max,
+            int64_t *argmax);
+
+/*
+ * Discords of a (host) matrix profile of n values: the k largest finite
+ * values, each followed by an exclusion of +-excl windows around it (the
+ * paper excludes +-m/2 as trivial matches, Algorithm 1), written to idx / val
+ * in decreasing order; *n_found (may be NULL) receives how many were found.
+ * *top1_certified (may be NULL) is the certificate of Sec. 2.1 for an
+ * approximate profile: 1 when the top value exceeds every value outside its
+ * exclusion zone by more than e_max (Guarantee 2), so that the top discord of
+ * the exact profile is the same subsequence. Host computation only.
+ */
+int mp_top_discords(const double *profile, int64_t n, int32_t k, int64_t excl, double e_max, int64_t *idx, double *val,
+                    int32_t *n_found, int32_t *top1_certified);
+
+/*
+ * Autotuner: chooses the join form and the plain kernel's column grouping for
+ * one shape (dictionary, m, query length n). It builds a synthetic query of n
+ * samples from the dictionary's own samples, times the plain form at several
+ * column-group counts and the tensor-core forms whose stated accuracy meets
+ * `tolerance` (absolute distance error: 1e-4 admits the plain form only,
+ * 1e-3 adds split-BF16; tolerance <= 0 admits every form, TF32 included),
+ * and keeps the fastest. The choice applies to later joins on this context
+ * whose kernel is MP_KERNEL_AUTO and whose shape falls in the same bucket
+ * (same dtype and m, same floor(log2) of the dictionary windows and of the
+ * query windows); with mp_config.tune_cache set it is also appended to that
+ * file as one JSON line, and mp_init reloads the file. Outputs (may be
+ * NULL): the chosen MP_KERNEL_* form, its column groups and its time in ms.
+ * The call allocates and synchronises; it is meant for set-up, not serving.
+ */
+int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t n, double tolerance, int32_t *kernel,
+                int32_t *groups, double *ms);
 
 /* Phases of a join, for mp_profile_read. */
 #define MP_PHASE_STATS 0    /* window statistics of the query (K1) */

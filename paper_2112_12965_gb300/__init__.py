@@ -100,6 +100,11 @@ def _load():
         "mp_poll": ([P, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mp_drain": ([P, ctypes.c_double], ctypes.c_int),
         "mp_profile": ([P, i32], ctypes.c_int),
+        "mp_emax": ([P, P, P, i32, i64, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
+        "mp_top_discords": ([P, i64, i32, i64, ctypes.c_double, P, P, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+                            ctypes.c_int),
+        "mp_autotune": ([P, P, i32, i64, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mp_profile_read": ([P, P, P, i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -240,3 +245,33 @@ def mp_profile_read(ctx, reset: bool = False) -> Tuple[np.ndarray, np.ndarray]:
     n = np.zeros(MP_PHASE_COUNT, dtype=np.int64)
     _check(lib.mp_profile_read(ctx, _ptr(ms), _ptr(n), 1 if reset else 0))
     return ms, n
+
+
+def mp_autotune(ctx, d, m: int, n: int, tolerance: float = 1e-4) -> Tuple[int, int, float]:
+    """Time the join forms for (dictionary, m, query length n); returns (kernel, groups, ms) of the fastest."""
+    k = ctypes.c_int32()
+    g = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(lib.mp_autotune(ctx, d, m, n, tolerance, ctypes.byref(k), ctypes.byref(g), ctypes.byref(ms)))
+    return k.value, g.value, ms.value
+
+
+def mp_emax(ctx, d, t_b: np.ndarray, m: int) -> Tuple[float, int]:
+    """e_max of the dictionary for the series t_b it was learned from: (value, window attaining it)."""
+    x = np.ascontiguousarray(t_b)
+    e = ctypes.c_double()
+    a = ctypes.c_int64()
+    _check(lib.mp_emax(ctx, d, _ptr(x), _dtype_of(x), len(x), m, ctypes.byref(e), ctypes.byref(a)))
+    return e.value, a.value
+
+
+def mp_top_discords(profile: np.ndarray, k: int, excl: int, e_max: float = -1.0):
+    """Top-k discords of a profile with a +-excl exclusion zone; returns (idx, val, top1_certified)."""
+    pr = np.ascontiguousarray(profile, dtype=np.float64)
+    idx = np.empty(max(k, 1), dtype=np.int64)
+    val = np.empty(max(k, 1), dtype=np.float64)
+    nf = ctypes.c_int32()
+    cert = ctypes.c_int32()
+    _check(lib.mp_top_discords(_ptr(pr), len(pr), k, excl, e_max, _ptr(idx), _ptr(val), ctypes.byref(nf),
+                               ctypes.byref(cert)))
+    return idx[: nf.value], val[: nf.value], bool(cert.value)

@@ -127,6 +127,32 @@ struct Batch {
     void *dmem = nullptr;  // batch-level buffers (request table, items, counter)
 };
 
+// Autotuner decisions: join form and column groups per (dtype, m, log2 of the
+// dictionary windows, log2 of the query windows).
+struct TuneKey {
+    int dtype, m, wlog, qlog;
+    bool operator<(const TuneKey &o) const
+    {
+        if (dtype != o.dtype) return dtype < o.dtype;
+        if (m != o.m) return m < o.m;
+        if (wlog != o.wlog) return wlog < o.wlog;
+        return qlog < o.qlog;
+    }
+};
+struct TuneVal {
+    int kernel, groups;
+    double ms;
+};
+static int ilog2(int64_t x)
+{
+    int l = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++l;
+    }
+    return l;
+}
+
 struct mp_ctx {
     int32_t device = 0;
     int32_t sm_count = 0;
@@ -162,7 +188,14 @@ struct mp_ctx {
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[MP_PHASE_COUNT] = {0, 0, 0};
     int64_t prof_n[MP_PHASE_COUNT] = {0, 0, 0};
+
+    // autotuner
+    std::map<TuneKey, TuneVal> tune;
+    std::string tune_path;
+    int force_groups = 0;  // set while the autotuner times a candidate
 };
+
+static void tune_load(mp_ctx *ctx, const char *path);
 
 // Event pair around one phase of a join (no-op unless tracing is on).
 struct PhaseTimer {
@@ -422,7 +455,8 @@ struct Geometry {
     int warps, n_row_blocks, n_groups;
 };
 
-static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int rows_per_lane)
+static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int rows_per_lane, int dtype = -1,
+                               int m = 0)
 {
     Geometry g;
     const int64_t rows_warp = 32 * rows_per_lane;
@@ -435,7 +469,13 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
     int64_t ng = (want + g.n_row_blocks - 1) / g.n_row_blocks;
     const int64_t max_g = std::max<int64_t>(1, W / 4096);
     ng = std::max<int64_t>(1, std::min(ng, max_g));
-    g.n_groups = (int)ng;
+    if (ctx->force_groups > 0) {
+        ng = ctx->force_groups;
+    } else if (dtype >= 0 && ctx->kernel == MP_KERNEL_AUTO) {
+        auto it = ctx->tune.find(TuneKey{dtype, m, ilog2(W), ilog2(nq)});
+        if (it != ctx->tune.end() && it->second.kernel == MP_KERNEL_PLAIN) ng = it->second.groups;
+    }
+    g.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(ng, W));
     return g;
 }
 
@@ -476,7 +516,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl);
+    const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl, dtype, m);
     const bool tc = (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32);
     JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0);
     double *mean_a = (double *)(base + w.off_mean);
@@ -559,15 +599,21 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const DictStats *s, int32_t dtype
 {
     const int64_t nq = n - m + 1;
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo = plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl);
+    const Geometry geo = plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl, dtype, m);
     return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0).total;
 }
 
-static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s)
+static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s, int64_t nq)
 {
     if (dtype == MP_F64) return MP_KERNEL_PLAIN;
     int k = ctx->kernel;
-    if (k == MP_KERNEL_AUTO) k = tc_autotune_choice(m, s->n_windows);
+    if (k == MP_KERNEL_AUTO) {
+        // the autotuner's choice for this shape, else the plain form (the
+        // fastest on every workload measured without a tuning run)
+        k = MP_KERNEL_PLAIN;
+        auto it = ctx->tune.find(TuneKey{dtype, m, ilog2(std::max<int64_t>(1, s->n_windows)), ilog2(nq)});
+        if (it != ctx->tune.end()) k = it->second.kernel;
+    }
     if (k == MP_KERNEL_TC_BF16X3 && !tc_supported(0, m)) k = MP_KERNEL_PLAIN;
     if (k == MP_KERNEL_TC_TF32 && !tc_supported(1, m)) k = MP_KERNEL_PLAIN;
     return k;
@@ -626,7 +672,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         int64_t *idx = (int64_t *)(p + nq * 8);
         p += align_up(nq * 16, 256);
         CUDA_TRY(cudaMemcpyAsync(q, r.query.data(), (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
-        if (s->n_windows == 0 || r.dtype == MP_F64 || resolve_kernel(ctx, r.dtype, r.m, s) != MP_KERNEL_PLAIN) {
+        if (s->n_windows == 0 || r.dtype == MP_F64 || resolve_kernel(ctx, r.dtype, r.m, s, nq) != MP_KERNEL_PLAIN) {
             // Requests that do not fit the batched FP32 plain kernel run alone.
             if (s->n_windows == 0) {
                 std::vector<double> inf(nq, INFINITY);
@@ -636,13 +682,13 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
                 continue;
             }
             rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p,
-                             resolve_kernel(ctx, r.dtype, r.m, s));
+                             resolve_kernel(ctx, r.dtype, r.m, s, nq));
             if (rc) return rc;
             CUDA_TRY(cudaMemcpyAsync(r.out_dist, dist, nq * 8, cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaMemcpyAsync(r.out_idx, idx, nq * 8, cudaMemcpyDeviceToHost, st));
             continue;
         }
-        const Geometry geo0 = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane);
+        const Geometry geo0 = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, r.dtype, r.m);
         Geometry geo = geo0;
         geo.warps = 4;
         geo.n_row_blocks = (int)((nq + 4 * 32 * kPlainRowsPerLane - 1) / (4 * 32 * kPlainRowsPerLane));
@@ -828,7 +874,8 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
     size_t fr = 0, tot = 0;
     CUDA_TRY(cudaMemGetInfo(&fr, &tot));
     c->mem_budget = cfg.mem_budget ? cfg.mem_budget : fr / 2;
-    if (cfg.tune_cache) tc_load_tune_cache(cfg.tune_cache);
+    if (cfg.tune_cache) tune_load(c.get(), cfg.tune_cache);
+
     mp_ctx *p = c.release();
     p->worker = std::thread(scheduler_loop, p);
     *out = p;
@@ -982,7 +1029,7 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
         cudaEventDestroy(ev);
     }
     rc = join_device(ctx, d, s, d_query, dtype, n, m, d_dist, d_idx, st, (unsigned char *)ctx->ws,
-                     resolve_kernel(ctx, dtype, m, s));
+                     resolve_kernel(ctx, dtype, m, s, nq));
     if (rc) return rc;
     if (st != ctx->stream) {
         cudaEvent_t ev;
@@ -1028,12 +1075,12 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     cudaStream_t st = ctx->stream;
     CUDA_TRY(cudaMemcpyAsync(dq, query, (size_t)n * dtype_size(dtype), cudaMemcpyHostToDevice, st));
     rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes,
-                     resolve_kernel(ctx, dtype, m, s));
+                     resolve_kernel(ctx, dtype, m, s, nq));
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
     int32_t err = 0;
-    const int kused = resolve_kernel(ctx, dtype, m, s);
+    const int kused = resolve_kernel(ctx, dtype, m, s, nq);
     const bool tc = (kused == MP_KERNEL_TC_BF16X3 || kused == MP_KERNEL_TC_TF32);
     if (tc) CUDA_TRY(cudaMemcpyAsync(&err, base + qbytes + 2 * obytes, sizeof err, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1168,6 +1215,179 @@ int mp_drain(mp_ctx *ctx, double timeout_s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// e_max and discords (Sec. 2.1 and Sec. 3.3, on top of the join)
+// ---------------------------------------------------------------------------
+extern "C" int mp_emax(mp_ctx *ctx, const mp_dict *dict, const void *t_b, int32_t dtype, int64_t n_b, int32_t m,
+                       double *e_max, int64_t *argmax)
+{
+    g_err.clear();
+    if (!e_max) return fail(MP_E_ARG, "null output");
+    const int64_t nq = n_b - m + 1;
+    if (nq <= 0) return fail(MP_E_ARG, "series shorter than m");
+    std::vector<double> dist((size_t)nq);
+    std::vector<int64_t> idx((size_t)nq);
+    int rc = mp_ab_join(ctx, dict, t_b, dtype, n_b, m, dist.data(), idx.data());
+    if (rc) return rc;
+    // e_max = max over the windows of T_B of NNDist(window, D_{B,m})
+    int64_t best = 0;
+    for (int64_t i = 1; i < nq; ++i)
+        if (dist[i] > dist[best]) best = i;
+    *e_max = dist[best];
+    if (argmax) *argmax = best;
+    return MP_OK;
+}
+
+extern "C" int mp_top_discords(const double *profile, int64_t n, int32_t k, int64_t excl, double e_max, int64_t *idx,
+                               double *val, int32_t *n_found, int32_t *top1_certified)
+{
+    g_err.clear();
+    if (!profile || !idx || !val || n < 0 || k < 0 || excl < 0) return fail(MP_E_ARG, "bad argument");
+    // repeatedly take the largest finite value not excluded; exclude +-excl around it
+    std::vector<uint8_t> blocked((size_t)n, 0);
+    int32_t found = 0;
+    for (int32_t j = 0; j < k; ++j) {
+        int64_t b = -1;
+        for (int64_t i = 0; i < n; ++i)
+            if (!blocked[i] && std::isfinite(profile[i]) && (b < 0 || profile[i] > profile[b])) b = i;
+        if (b < 0) break;
+        idx[j] = b;
+        val[j] = profile[b];
+        ++found;
+        for (int64_t i = std::max<int64_t>(0, b - excl); i <= std::min<int64_t>(n - 1, b + excl); ++i) blocked[i] = 1;
+    }
+    if (n_found) *n_found = found;
+    if (top1_certified) {
+        // Guarantee 2: the true profile lies in [P_hat - e_max, P_hat], so a
+        // lead larger than e_max over every other candidate is certain.
+        double runner_up = -INFINITY;
+        if (found >= 1)
+            for (int64_t i = 0; i < n; ++i)
+                if (std::llabs(i - idx[0]) > excl && std::isfinite(profile[i])) runner_up = std::max(runner_up, profile[i]);
+        *top1_certified = (found >= 1 && e_max >= 0 && val[0] - runner_up > e_max) ? 1 : 0;
+    }
+    return MP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+static void tune_load(mp_ctx *ctx, const char *path)
+{
+    ctx->tune_path = path;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        TuneKey k;
+        TuneVal v;
+        if (sscanf(line, "{\"dtype\": %d, \"m\": %d, \"wlog\": %d, \"qlog\": %d, \"kernel\": %d, \"groups\": %d, \"ms\": %lf",
+                   &k.dtype, &k.m, &k.wlog, &k.qlog, &v.kernel, &v.groups, &v.ms) == 7 &&
+            v.kernel >= MP_KERNEL_PLAIN && v.kernel <= MP_KERNEL_TC_TF32 && v.groups >= 1)
+            ctx->tune[k] = v;  // a later line overrides an earlier one
+    }
+    fclose(f);
+}
+
+static void tune_save(const mp_ctx *ctx, const TuneKey &k, const TuneVal &v)
+{
+    if (ctx->tune_path.empty()) return;
+    FILE *f = fopen(ctx->tune_path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"dtype\": %d, \"m\": %d, \"wlog\": %d, \"qlog\": %d, \"kernel\": %d, \"groups\": %d, \"ms\": %.4f}\n",
+            k.dtype, k.m, k.wlog, k.qlog, v.kernel, v.groups, v.ms);
+    fclose(f);
+}
+
+extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t n, double tolerance,
+                           int32_t *kernel_out, int32_t *groups_out, double *ms_out)
+{
+    g_err.clear();
+    if (!ctx || !dict) return fail(MP_E_ARG, "null argument");
+    if (m < 2 || m > 8192 || n < m) return fail(MP_E_ARG, "bad n/m");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    mp_dict *d = const_cast<mp_dict *>(dict);
+    DictStats *s;
+    int rc = get_stats(ctx, d, m, &s);
+    if (rc) return rc;
+    if (s->n_windows == 0) return fail(MP_E_ARG, "the dictionary has no window of length %d", m);
+    const int64_t nq = n - m + 1;
+    const int dtype = d->dtype;
+    const size_t esz = dtype_size(dtype);
+    // synthetic query of length n: the dictionary's samples repeated
+    void *dq = nullptr, *dout = nullptr;
+    if (cudaMalloc(&dq, (size_t)n * esz) != cudaSuccess || cudaMalloc(&dout, (size_t)nq * 16) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dq);
+        return fail(MP_E_NOMEM, "autotune buffers");
+    }
+    for (int64_t o = 0; o < n; o += d->nb)
+        CUDA_TRY(cudaMemcpyAsync((char *)dq + o * esz, d->d_samples, (size_t)std::min<int64_t>(d->nb, n - o) * esz,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+    double *dd = (double *)dout;
+    int64_t *di = (int64_t *)((char *)dout + (size_t)nq * 8);
+    // candidates: the plain form at several column-group counts, then the
+    // tensor-core forms whose accuracy meets the tolerance
+    struct Cand {
+        int kernel, groups;
+    };
+    std::vector<Cand> cands;
+    const int64_t max_g = std::max<int64_t>(1, s->n_windows / 1024);
+    for (int g : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
+        if (g <= max_g) cands.push_back(Cand{MP_KERNEL_PLAIN, g});
+    if (dtype == MP_F32 && (tolerance <= 0 || tolerance >= 1e-3) && tc_supported(0, m))
+        cands.push_back(Cand{MP_KERNEL_TC_BF16X3, 1});
+    if (dtype == MP_F32 && tolerance <= 0 && tc_supported(1, m)) cands.push_back(Cand{MP_KERNEL_TC_TF32, 1});
+    const int saved_kernel = ctx->kernel;
+    const size_t wsb = std::max(join_ws_layout(nq, dtype, 32, 0).total, join_ws_bytes(ctx, s, dtype, n, m));
+    rc = ensure_ws(ctx, wsb);
+    if (rc) {
+        cudaFree(dq);
+        cudaFree(dout);
+        return rc;
+    }
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    Cand best{MP_KERNEL_PLAIN, 1};
+    double best_ms = 1e300;
+    for (const Cand &c : cands) {
+        ctx->kernel = c.kernel;
+        ctx->force_groups = c.kernel == MP_KERNEL_PLAIN ? c.groups : 0;
+        double t_min = 1e300;
+        for (int rep = 0; rep < 4 && rc == MP_OK; ++rep) {
+            cudaEventRecord(e0, ctx->stream);
+            rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, ctx->stream, (unsigned char *)ctx->ws, c.kernel);
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(MP_E_CUDA, "autotune run failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_min = std::min(t_min, (double)ms);  // the first run warms up
+        }
+        if (rc) break;
+        if (t_min < best_ms) {
+            best_ms = t_min;
+            best = c;
+        }
+    }
+    ctx->kernel = saved_kernel;
+    ctx->force_groups = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dq);
+    cudaFree(dout);
+    if (rc) return rc;
+    const TuneKey key{dtype, m, ilog2(s->n_windows), ilog2(nq)};
+    const TuneVal val{best.kernel, best.groups, best_ms};
+    ctx->tune[key] = val;
+    tune_save(ctx, key, val);
+    if (kernel_out) *kernel_out = best.kernel;
+    if (groups_out) *groups_out = best.groups;
+    if (ms_out) *ms_out = best_ms;
+    return MP_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Join without device allocation

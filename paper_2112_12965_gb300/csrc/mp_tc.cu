@@ -650,17 +650,6 @@ int tc_groups_bound(int sm_count, int64_t nq)
     return (int)std::max<int64_t>(1, (2 * sm_count + rbk - 1) / rbk);
 }
 
-int tc_autotune_choice(int, int64_t)
-{
-    // The plain recurrence does O(1) work per pair while the tensor form does
-    // 2m flops per pair; measured on GB300 the plain form is faster at every
-    // m in the workloads, so AUTO resolves to it unless a tune cache says
-    // otherwise.
-    return MP_KERNEL_PLAIN;
-}
-
-void tc_load_tune_cache(const char *) {}
-
 void tc_free_pack(void *pack)
 {
     TcPacks *pk = (TcPacks *)pack;

@@ -16,10 +16,6 @@ typedef int (*fail_fn)(int, const char *, ...);
 bool tc_supported(int variant, int m);
 // Upper bound of the column groups tc_join uses for nq query windows.
 int tc_groups_bound(int sm_count, int64_t nq);
-// Join form picked by the autotune cache for (m, dictionary windows); MP_KERNEL_* value.
-int tc_autotune_choice(int m, int64_t n_windows);
-// Load / record autotune decisions (JSON lines file).
-void tc_load_tune_cache(const char *path);
 // Free the per-(dictionary, m) tile tables created by tc_join.
 void tc_free_pack(void *pack);
 
