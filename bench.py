@@ -40,6 +40,35 @@ PLAIN_OPS_PER_PAIR = 4
 SMS, LANES_PER_SM = 152, 128
 
 
+def shard_rows(n: int, m: int, world: int, rank: int):
+    """Sample range [lo, hi) of rank's shard of a query of n samples.
+
+    Query windows 0 .. n-m are split into `world` contiguous runs; a shard
+    carries its windows' samples plus the m - 1 samples of halo they reach
+    into, so the per-rank profiles concatenate to the whole profile with no
+    exchange between ranks.
+    """
+    nq = max(0, n - m + 1)
+    w_lo = nq * rank // world
+    w_hi = nq * (rank + 1) // world
+    if w_hi <= w_lo:
+        return w_lo, w_lo
+    return w_lo, w_hi + m - 1
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (all ranks get it); the identity for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -50,7 +79,7 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -64,7 +93,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -402,16 +431,105 @@ def study_dict_vs_orig(mp, k_discords=200, with_tf32=False):
     return out
 
 
+def study_serving(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256, window=64):
+    """Continuous-batching serving: capacity, then Poisson load at fractions of it; p50/p99 latency."""
+    import synthetic
+
+    rng = np.random.default_rng(seed)
+    dicts = synthetic.serving_dictionaries(n_dicts=16, seed=100)
+    # a pool of queries, log-uniform in [2^10, 2^20] samples, random walk / ECG-like 50:50
+    pool = []
+    for k in range(pool_size):
+        n = int(2 ** rng.uniform(10, 20))
+        sd = int(rng.integers(0, 2**31 - 1))
+        q = synthetic.random_walk(n, sd) if k % 2 == 0 else synthetic.ecg_like(n, sd)
+        pool.append(q.astype(np.float32))
+    reqs = [(int(rng.integers(0, pool_size)), int(rng.integers(0, 16)), int(rng.choice([64, 128, 256])))
+            for _ in range(n_requests)]
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=16, max_batch=32)
+    out = {"study": "serving", "requests": n_requests,
+           "mix": "query 2^U samples, U ~ U(10, 20), random walk / ECG-like 50:50 from a pool of "
+                  f"{pool_size} series; m uniform in {{64, 128, 256}}; 16 resident dictionaries of 2^14..2^18 "
+                  "samples cut into segments of 512..4096", "loads": {}}
+    try:
+        handles = [mp.mp_dict_load(ctx, b, offs, [64, 128, 256]) for b, offs in dicts]
+        W = {(di, m): mp.mp_dict_windows(handles[di], m) for di in range(16) for m in (64, 128, 256)}
+
+        def submit(r):
+            q = pool[r[0]]
+            nq = len(q) - r[2] + 1
+            od, oi = np.empty(nq), np.empty(nq, dtype=np.int64)
+            t = mp.mp_submit(ctx, handles[r[1]], q, r[2], od, oi)
+            return t, (od, oi), nq * W[(r[1], r[2])]
+
+        # capacity: keep `window` requests outstanding
+        t0 = time.perf_counter()
+        live, pairs, done = {}, 0, 0
+        it = iter(reqs)
+        exhausted = False
+        while live or not exhausted:
+            while not exhausted and len(live) < window:
+                try:
+                    r = next(it)
+                except StopIteration:
+                    exhausted = True
+                    break
+                t, bufs, pr = submit(r)
+                live[t] = bufs
+                pairs += pr
+            for t in list(live):
+                st, _ = mp.mp_poll(ctx, t)
+                if st != mp.MP_PENDING:
+                    assert st == mp.MP_DONE
+                    del live[t]
+                    done += 1
+            time.sleep(0.0001)
+        cap_s = time.perf_counter() - t0
+        capacity = n_requests / cap_s
+        out["capacity_rps"] = capacity
+        out["capacity_pairs_per_s"] = pairs / cap_s
+        for frac in loads:
+            rate = frac * capacity
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+            lat, live = [], {}
+            t0 = time.perf_counter()
+            k = 0
+            while k < n_requests or live:
+                now = time.perf_counter() - t0
+                while k < n_requests and arrivals[k] <= now:
+                    t, bufs, _ = submit(reqs[k])
+                    live[t] = bufs
+                    k += 1
+                for t in list(live):
+                    st, l = mp.mp_poll(ctx, t)
+                    if st != mp.MP_PENDING:
+                        assert st == mp.MP_DONE
+                        lat.append(l)
+                        del live[t]
+                time.sleep(0.0001)
+            wall = time.perf_counter() - t0
+            lat = np.array(lat) * 1e3
+            out["loads"][f"{frac:.1f}x"] = {"offered_rps": rate, "throughput_rps": n_requests / wall,
+                                            "p50_ms": float(np.percentile(lat, 50)),
+                                            "p99_ms": float(np.percentile(lat, 99)),
+                                            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+        for h in handles:
+            mp.mp_dict_free(ctx, h)
+    finally:
+        mp.mp_shutdown(ctx)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "auto"])
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", choices=["precision", "dict-vs-orig"], default=None,
+    ap.add_argument("--study", choices=["precision", "dict-vs-orig", "serving"], default=None,
                     help="run a study instead of the headline benchmark (one JSON line)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the query (profiling captures of a small case); 1.0 = the full workload")
@@ -440,7 +558,12 @@ def main():
     import synthetic
 
     if args.study:
-        res = study_precision(mp) if args.study == "precision" else study_dict_vs_orig(mp, with_tf32=True)
+        if args.study == "precision":
+            res = study_precision(mp)
+        elif args.study == "serving":
+            res = study_serving(mp)
+        else:
+            res = study_dict_vs_orig(mp, with_tf32=True)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return
@@ -458,12 +581,7 @@ def main():
     with ClockSampler(local_rank) as clk:
         step_ms, phase_ms, phase_n, _ = time_device_join(mp, ctx, d, w, args.steps, args.warmup, flush)
     torch.cuda.synchronize()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, device="cuda")
     ms_per_step = total_ms / args.steps
     pairs = w.pairs
     value = world * pairs * args.steps / (total_ms / 1e3)

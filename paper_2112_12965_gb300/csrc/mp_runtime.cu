@@ -110,7 +110,11 @@ struct Request {
     int32_t dtype = MP_F32;
     int64_t n = 0;
     int32_t m = 0;
-    std::vector<unsigned char> query;  // host copy
+    // pinned staging: the query at submit, then the result (dist, idx) until
+    // the host copies it to out_dist / out_idx at completion
+    void *h_stage = nullptr;
+    size_t stage_bytes = 0;
+    bool no_windows = false;  // dictionary without a window of length m
     double *out_dist = nullptr;
     int64_t *out_idx = nullptr;
     double t_submit = 0, t_done = 0;
@@ -188,6 +192,9 @@ struct mp_ctx {
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[MP_PHASE_COUNT] = {0, 0, 0};
     int64_t prof_n[MP_PHASE_COUNT] = {0, 0, 0};
+
+    // pinned staging buffers, free lists by power-of-two size class
+    std::map<size_t, std::vector<void *>> pinned_free;
 
     // autotuner
     std::map<TuneKey, TuneVal> tune;
@@ -629,8 +636,54 @@ static size_t request_bytes(const mp_ctx *ctx, const Request &r, const DictStats
            join_ws_bytes(ctx, s, r.dtype, r.n, r.m);
 }
 
+// Pinned host buffer of at least `bytes` (caller holds ctx->smu or is the
+// only user of the pool at that time).
+static size_t pinned_class(size_t bytes)
+{
+    size_t c = 1 << 16;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+
+static void *pinned_take(mp_ctx *ctx, size_t bytes)
+{
+    const size_t c = pinned_class(bytes);
+    auto &fl = ctx->pinned_free[c];
+    if (!fl.empty()) {
+        void *p = fl.back();
+        fl.pop_back();
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, c, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void pinned_give(mp_ctx *ctx, void *p, size_t bytes)
+{
+    if (p) ctx->pinned_free[pinned_class(bytes)].push_back(p);
+}
+
 static void finish_request(mp_ctx *ctx, Request &r, int32_t state, cudaStream_t st)
 {
+    if (state == MP_DONE) {
+        // the result waits in the pinned staging buffer: dist then idx
+        const int64_t nq = r.n - r.m + 1;
+        if (r.no_windows) {
+            for (int64_t i = 0; i < nq; ++i) {
+                r.out_dist[i] = INFINITY;
+                r.out_idx[i] = -1;
+            }
+        } else {
+            memcpy(r.out_dist, r.h_stage, (size_t)nq * 8);
+            memcpy(r.out_idx, (char *)r.h_stage + (size_t)nq * 8, (size_t)nq * 8);
+        }
+    }
+    pinned_give(ctx, r.h_stage, r.stage_bytes);
+    r.h_stage = nullptr;
     r.t_done = now_s();
     r.state = state;
     // stream-ordered free: no device-wide synchronisation in the serving loop
@@ -671,21 +724,17 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         double *dist = (double *)p;
         int64_t *idx = (int64_t *)(p + nq * 8);
         p += align_up(nq * 16, 256);
-        CUDA_TRY(cudaMemcpyAsync(q, r.query.data(), (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(q, r.h_stage, (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
         if (s->n_windows == 0 || r.dtype == MP_F64 || resolve_kernel(ctx, r.dtype, r.m, s, nq) != MP_KERNEL_PLAIN) {
             // Requests that do not fit the batched FP32 plain kernel run alone.
             if (s->n_windows == 0) {
-                std::vector<double> inf(nq, INFINITY);
-                std::vector<int64_t> neg(nq, -1);
-                memcpy(r.out_dist, inf.data(), nq * 8);
-                memcpy(r.out_idx, neg.data(), nq * 8);
+                r.no_windows = true;  // +inf / -1, written at completion
                 continue;
             }
             rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p,
                              resolve_kernel(ctx, r.dtype, r.m, s, nq));
             if (rc) return rc;
-            CUDA_TRY(cudaMemcpyAsync(r.out_dist, dist, nq * 8, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(cudaMemcpyAsync(r.out_idx, idx, nq * 8, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
             continue;
         }
         const Geometry geo0 = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, r.dtype, r.m);
@@ -751,8 +800,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
                                   (const float4 *)(ps.base + w.off_rs), (const Split<float> *)(ps.base + w.off_ms),
                                   (const uint8_t *)(ps.base + w.off_cflag), r.dict, ps.s, ps.dist, ps.idx),
                 st));
-            CUDA_TRY(cudaMemcpyAsync(r.out_dist, ps.dist, nq * 8, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(cudaMemcpyAsync(r.out_idx, ps.idx, nq * 8, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(r.h_stage, ps.dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
         }
     }
     CUDA_TRY(cudaEventRecord(bt.done, st));
@@ -790,6 +838,8 @@ static void scheduler_loop(mp_ctx *ctx)
             ctx->pending.pop_front();
             if (cudaMallocAsync(&r->dmem, r->bytes, bt.stream) != cudaSuccess) {
                 cudaGetLastError();
+                pinned_give(ctx, r->h_stage, r->stage_bytes);
+                r->h_stage = nullptr;
                 r->t_done = now_s();
                 r->state = MP_FAILED;
                 r->dict->refs.fetch_sub(1);
@@ -905,6 +955,8 @@ int mp_shutdown(mp_ctx *ctx)
         cudaEventDestroy(mk.t1);
     }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (auto &kv : ctx->pinned_free)
+        for (void *p : kv.second) cudaFreeHost(p);
     cudaStreamDestroy(ctx->stream);
     cudaStreamDestroy(ctx->sstreams[0]);
     cudaStreamDestroy(ctx->sstreams[1]);
@@ -1120,7 +1172,7 @@ int mp_submit(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype
     r->dtype = dtype;
     r->n = n;
     r->m = m;
-    r->query.assign((const unsigned char *)query, (const unsigned char *)query + (size_t)n * dtype_size(dtype));
+    const int64_t nq = n - m + 1;
     r->out_dist = out_dist;
     r->out_idx = out_idx;
     {
@@ -1133,6 +1185,13 @@ int mp_submit(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype
     }
     if (r->bytes > ctx->mem_budget) return fail(MP_E_NOMEM, "request needs %zu bytes, budget %zu", r->bytes,
                                                  ctx->mem_budget);
+    r->stage_bytes = std::max((size_t)n * dtype_size(dtype), (size_t)nq * 16);
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        r->h_stage = pinned_take(ctx, r->stage_bytes);
+    }
+    if (!r->h_stage) return fail(MP_E_NOMEM, "pinned staging of %zu bytes", r->stage_bytes);
+    memcpy(r->h_stage, query, (size_t)n * dtype_size(dtype));
     d->refs.fetch_add(1);
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
@@ -1206,7 +1265,9 @@ int mp_drain(mp_ctx *ctx, double timeout_s)
     while (true) {
         {
             std::lock_guard<std::mutex> lk(ctx->smu);
-            if (ctx->pending.empty() && ctx->inflight.empty()) return MP_OK;
+            // admitted requests are counted from admission to completion; a
+            // batch being launched is in neither the queue nor the list
+            if (ctx->pending.empty() && ctx->inflight.empty() && ctx->n_inflight_reqs == 0) return MP_OK;
         }
         if (now_s() > t_end) return fail(MP_E_TIMEOUT, "requests still in flight after %.3f s", timeout_s);
         ctx->scv.notify_all();

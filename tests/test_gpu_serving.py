@@ -83,3 +83,26 @@ def test_serving_matches_sync_join_and_is_mix_invariant(mp):
             mp.mp_dict_free(ctx, h)
     finally:
         mp.mp_shutdown(ctx)
+
+
+def test_drain_returns_only_after_every_result_is_written(mp):
+    """mp_drain must not return while a batch is being launched (its outputs unwritten)."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=4, max_batch=4)
+    try:
+        b, offs = synthetic.serving_dictionaries(n_dicts=1, seed=300, min_log2=12, max_log2=12)[0]
+        h = mp.mp_dict_load(ctx, b, offs, [64])
+        for rnd in range(5):
+            outs = []
+            for k in range(40):
+                q = synthetic.random_walk(2000 + 37 * k, 7000 + 100 * rnd + k).astype(np.float32)
+                od = np.full(len(q) - 63, np.nan)
+                oi = np.full(len(q) - 63, -7, dtype=np.int64)
+                outs.append((od, oi, mp.mp_submit(ctx, h, q, 64, od, oi)))
+            mp.mp_drain(ctx, 60.0)
+            for od, oi, t in outs:
+                assert np.all(np.isfinite(od)) and np.all(oi >= 0), "drain returned before a result was written"
+                st, _ = mp.mp_poll(ctx, t)
+                assert st == mp.MP_DONE
+        mp.mp_dict_free(ctx, h)
+    finally:
+        mp.mp_shutdown(ctx)
