@@ -43,11 +43,11 @@ __device__ __forceinline__ double pair_distance(const T *a, int64_t i, Split<T> 
 }
 
 // k values staged per pass of the re-scoring, and the padded shared-memory
-// index (one pad slot every 8 values: lanes reading with a stride of 8 values
-// hit distinct banks).
+// index (one pad slot every 16 values: lanes reading with a stride of 16
+// values hit distinct banks).
 constexpr int kFinChunk = 256;
-__device__ __forceinline__ int fpad(int e) { return e + (e >> 3); }
-constexpr int kFinWarpVals = (kFinChunk + kChunk) + ((kFinChunk + kChunk) >> 3) + 1;
+__device__ __forceinline__ int fpad(int e) { return e + (e >> 4); }
+constexpr int kFinWarpVals = (kFinChunk + kChunk) + ((kFinChunk + kChunk) >> 4) + 1;
 
 template <typename T>
 __device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
@@ -103,15 +103,17 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                 if (g >= 0) {
                     // 2. re-score the chunk's windows g .. g + kChunk - 1. The warp stages
                     // the shifted query window and the candidates' samples in shared
-                    // memory with coalesced loads, kFinChunk values of k at a time; lane l
-                    // then sums the products of a contiguous range of k for all
-                    // candidates (a sliding window of dictionary samples in registers),
-                    // and a transposing butterfly leaves candidate (l & 15)'s total in lane l.
+                    // memory with coalesced loads, kFinChunk values of k at a time. Each
+                    // half-warp takes 8 candidates; lane l of a half sums the products of
+                    // a contiguous run of k for its 8 candidates (a sliding window of
+                    // dictionary samples in registers), and a transposing butterfly
+                    // leaves candidate 8 * half + (l & 7)'s total in lane l.
                     const Split<T> ma = p.ms_a[i];
                     const T sa = ma.hi, sb = p.ms_b[g].hi;
-                    T acc[kChunk];
+                    const int half = lane >> 4, lg = lane & 15;
+                    T acc[8];
 #pragma unroll
-                    for (int c = 0; c < kChunk; ++c) acc[c] = T(0);
+                    for (int c = 0; c < 8; ++c) acc[c] = T(0);
                     for (int kc = 0; kc < m; kc += kFinChunk) {
                         const int len = min(kFinChunk, m - kc);
                         for (int e = lane; e < len; e += 32) wa[fpad(e)] = p.a[i + kc + e] - sa;
@@ -120,29 +122,28 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                             wb[fpad(e)] = (j < p.nb) ? p.b[j] - sb : T(0);
                         }
                         __syncwarp();
-                        const int kpl = (len + 31) >> 5;
-                        const int k0 = lane * kpl;
+                        const int kpl = (len + 15) >> 4;
+                        const int k0 = lg * kpl;
                         const int k1 = min(len, k0 + kpl);
-                        T bw[kChunk];
+                        T bw[8];
 #pragma unroll
-                        for (int c = 0; c < kChunk; ++c) bw[c] = (k0 < k1) ? wb[fpad(k0 + c)] : T(0);
-                        for (int kb = k0; kb < k1; kb += kChunk) {
+                        for (int c = 0; c < 8; ++c) bw[c] = (k0 < k1) ? wb[fpad(8 * half + k0 + c)] : T(0);
+                        for (int kb = k0; kb < k1; kb += 8) {
 #pragma unroll
-                            for (int u = 0; u < kChunk; ++u) {
+                            for (int u = 0; u < 8; ++u) {
                                 const int k = kb + u;
                                 if (k < k1) {
                                     const T av = wa[fpad(k)];
 #pragma unroll
-                                    for (int c = 0; c < kChunk; ++c)
-                                        acc[c] = fma(av, bw[(c + u) & (kChunk - 1)], acc[c]);
-                                    bw[u] = wb[fpad(k + kChunk)];
+                                    for (int c = 0; c < 8; ++c) acc[c] = fma(av, bw[(c + u) & 7], acc[c]);
+                                    bw[u] = wb[fpad(8 * half + k + 8)];
                                 }
                             }
                         }
                         __syncwarp();  // the next chunk overwrites the staged samples
                     }
 #pragma unroll
-                    for (int s = kChunk / 2; s >= 1; s >>= 1) {
+                    for (int s = 4; s >= 1; s >>= 1) {
 #pragma unroll
                         for (int c = 0; c < s; ++c) {
                             const bool up = (lane & s) != 0;
@@ -151,8 +152,8 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                             acc[c] = keep + __shfl_xor_sync(0xffffffffu, send, s);
                         }
                     }
-                    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 16);
-                    const int cand = lane & (kChunk - 1);
+                    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);  // the two k-halves of the 16 lanes
+                    const int cand = 8 * half + (lane & 7);
                     const int64_t gc = (int64_t)g + cand;
                     bool ok = gc < p.npos_b;
                     vec4_t<T> r;
