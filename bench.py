@@ -211,6 +211,20 @@ def roofline(kname, pairs, m, join_ms, peaks, peak_src):
             "peak_source": src, "flops_per_pair": 2 * m * mult}
 
 
+def seed_roofline(w, seeds_ms, peaks, peak_src):
+    """Tensor roofline of the plain join's seed kernel (K2s): one seed row per 512 query
+    windows against every dictionary window, K = m, three TF32 products per term."""
+    if seeds_ms <= 0:
+        return None
+    n_srows = -(-w.n_rows // 512)
+    flops = n_srows * w.n_dict_windows * 2 * w.m * 3
+    peak = peaks.get("bf16_tflops", 1900.0) / 2.0
+    achieved = flops / (seeds_ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "k_seed", "ms": seeds_ms, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_launch": flops,
+            "peak_source": f"{peak_src} bf16 burst / 2 (nominal TF32:BF16 ratio)"}
+
+
 def kernel_id(mp, name):
     return {"plain": mp.MP_KERNEL_PLAIN, "bf16x3": mp.MP_KERNEL_TC_BF16X3, "tf32": mp.MP_KERNEL_TC_TF32,
             "auto": mp.MP_KERNEL_AUTO}[name]
@@ -340,7 +354,8 @@ def serving_run(mp, n_requests, seed=7):
 
 
 def _device_join_timed(mp, ctx, d, q, m, reps=3):
-    """Join a host query on the device; returns (dist, idx, join-kernel ms per launch)."""
+    """Join a host query on the device; returns (dist, idx, join ms per call: the join kernel plus, for
+    the plain form, its tensor-core seed kernel)."""
     import torch
 
     qt = torch.from_numpy(q).cuda()
@@ -358,7 +373,8 @@ def _device_join_timed(mp, ctx, d, q, m, reps=3):
     s.synchronize()
     ms, n = mp.mp_profile_read(ctx, reset=True)
     mp.mp_profile(ctx, False)
-    return dd.cpu().numpy(), di.cpu().numpy(), float(ms[mp.MP_PHASE_JOIN] / max(1, n[mp.MP_PHASE_JOIN]))
+    per_call = (ms[mp.MP_PHASE_JOIN] + ms[mp.MP_PHASE_SEEDS]) / max(1, n[mp.MP_PHASE_JOIN])
+    return dd.cpu().numpy(), di.cpu().numpy(), float(per_call)
 
 
 def study_precision(mp, rows=256):
@@ -616,9 +632,10 @@ def main():
                    "pairs_per_step_per_gpu": pairs, "kernel": args.kernel, "scale": args.scale,
                    "l2": "flushed between timed steps (512 MB write outside the timed events)",
                    "parallelism": f"{world} independent queries (weak scaling)" if world > 1 else "1 GPU"},
-        "phases_ms": {"stats": phase_ms[0] / max(1, phase_n[0]), "join": join_ms,
-                      "finalize": phase_ms[2] / max(1, phase_n[2])},
+        "phases_ms": {"stats": phase_ms[0] / max(1, phase_n[0]), "seeds": phase_ms[3] / max(1, phase_n[3]),
+                      "join": join_ms, "finalize": phase_ms[2] / max(1, phase_n[2])},
         "roofline": roof,
+        "seed_roofline": seed_roofline(w, phase_ms[3] / max(1, phase_n[3]), peaks, peak_src),
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(np.sum(phase_n)),

@@ -144,7 +144,9 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
  * query buffer must stay unchanged until then. Scratch memory comes from the
  * context's workspace, so calls on one context must not overlap on the GPU
  * (the context serialises them on the host; use one context per concurrent
- * stream).
+ * stream). The tensor-core kernels bound every wait on the device; if one runs
+ * out (about 2 s), every output distance is NaN and every index -1 (mp_ab_join
+ * returns MP_E_TIMEOUT instead).
  */
 int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int32_t dtype, int64_t n, int32_t m,
                       double *d_out_dist, int64_t *d_out_idx, void *stream);
@@ -158,7 +160,7 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
  * latency jitter, and applications that own the device allocator (a caching
  * allocator or pool whose accounting a foreign cudaMalloc would break).
  *
- * Its scratch is one fixed array of about 30 MB inside this library, held by
+ * Its scratch is one fixed array of about 46 MB inside this library, held by
  * every GPU that loads the library until the process exits. Limits: float32
  * samples only, at most 2^19 query windows (n - m + 1), and a dictionary cut
  * into at most 2^16 runs of windows; larger calls return MP_E_ARG with a
@@ -254,7 +256,8 @@ int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t n, double t
 #define MP_PHASE_STATS 0    /* window statistics of the query (K1) */
 #define MP_PHASE_JOIN 1     /* the join kernel: plain (K2) or tensor-core (K3) */
 #define MP_PHASE_FINALIZE 2 /* reduction, constant-window rule and exact distance of the pick (K4) */
-#define MP_PHASE_COUNT 3
+#define MP_PHASE_SEEDS 3    /* the plain join's top seeds on the tensor cores (K2s; FP32 plain joins) */
+#define MP_PHASE_COUNT 4
 
 /*
  * Tracing: with enable = 1, synchronous and device joins on this context

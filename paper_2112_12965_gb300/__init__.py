@@ -40,7 +40,8 @@ MP_KERNEL_TC_TF32 = 3
 MP_PHASE_STATS = 0
 MP_PHASE_JOIN = 1
 MP_PHASE_FINALIZE = 2
-MP_PHASE_COUNT = 3
+MP_PHASE_SEEDS = 3
+MP_PHASE_COUNT = 4
 
 MP_PENDING = 0
 MP_DONE = 1

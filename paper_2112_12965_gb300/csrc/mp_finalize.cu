@@ -7,6 +7,8 @@
 //   2. re-scores the kChunk dictionary windows of the winning chunk with
 //      direct dot products (the join kernels keep only a running maximum and
 //      the chunk that raised it) and takes their argmax, lowest g on ties;
+//      with the plain kernel's near-tie records it re-scores every chunk whose
+//      approximate score came within the near-tie width of the best as well;
 //   3. applies the constant-window convention (a constant window normalises
 //      to the zero vector: d = sqrt(m) against a non-constant window, 0
 //      against a constant one);
@@ -56,8 +58,100 @@ __device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
     return g1 >= 0 && (g2 < 0 || q1 > q2 || (q1 == q2 && g1 < g2));
 }
 
+
+// Re-score the kChunk windows g .. g + kChunk - 1 of one chunk (dictionary
+// samples pb) against query window i (samples pa, split mean ma) with direct
+// dot products and return (in every lane) the largest score cov * invstd_b
+// among its valid non-constant windows and that window, lowest g on ties
+// (-inf / -1 if none). The warp stages the shifted query
+// window and the candidates' samples in shared memory (wa, wb) with
+// coalesced loads, kFinChunk values of k at a time. Each half-warp takes 8
+// candidates; lane l of a half sums the products of a contiguous run of k
+// for its 8 candidates (a sliding window of dictionary samples in
+// registers), and a transposing butterfly leaves candidate 8 * half + (l & 7)'s
+// total in lane l.
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
+__device__ __forceinline__ void rescore_chunk(const T *__restrict__ pa, const T *__restrict__ pb, int64_t nb,
+                                              int64_t npos_b, int m, const Split<T> *__restrict__ ms_b,
+                                              const vec4_t<T> *__restrict__ rs_b, int64_t i, int32_t g,
+                                              const Split<T> ma, int lane, T *wa, T *wb, T &sc_out,
+                                              int32_t &g_out)
+{
+    const T sa = ma.hi, sb = ms_b[g].hi;
+    const int half = lane >> 4, lg = lane & 15;
+    T acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = T(0);
+    for (int kc = 0; kc < m; kc += kFinChunk) {
+        const int len = min(kFinChunk, m - kc);
+        for (int e = lane; e < len; e += 32) wa[fpad(e)] = pa[i + kc + e] - sa;
+        for (int e = lane; e < len + kChunk; e += 32) {
+            const int64_t j = (int64_t)g + kc + e;
+            wb[fpad(e)] = (j < nb) ? pb[j] - sb : T(0);
+        }
+        __syncwarp();
+        const int kpl = (len + 15) >> 4;
+        const int k0 = lg * kpl;
+        const int k1 = min(len, k0 + kpl);
+        T bw[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) bw[c] = (k0 < k1) ? wb[fpad(8 * half + k0 + c)] : T(0);
+        for (int kb = k0; kb < k1; kb += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = kb + u;
+                if (k < k1) {
+                    const T av = wa[fpad(k)];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[c] = fma(av, bw[(c + u) & 7], acc[c]);
+                    bw[u] = wb[fpad(8 * half + k + 8)];
+                }
+            }
+        }
+        __syncwarp();  // the next pass (or chunk) overwrites the staged samples
+    }
+#pragma unroll
+    for (int s = 4; s >= 1; s >>= 1) {
+#pragma unroll
+        for (int c = 0; c < s; ++c) {
+            const bool up = (lane & s) != 0;
+            const T send = up ? acc[c] : acc[c + s];
+            const T keep = up ? acc[c + s] : acc[c];
+            acc[c] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);  // the two k-halves of the 16 lanes
+    const int cand = 8 * half + (lane & 7);
+    const int64_t gc = (int64_t)g + cand;
+    bool ok = gc < npos_b;
+    vec4_t<T> r;
+    if (ok) {
+        r = rs_b[gc];
+        ok = r.w == T(0);
+    }
+    T sc = T(-INFINITY);
+    if (ok) {
+        // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
+        const Split<T> mb = ms_b[gc];
+        const T cov = acc[0] - T(m) * ma.lo * ((mb.hi - sb) + mb.lo);
+        sc = cov * r.z;
+    }
+    int32_t gw = ok ? (int32_t)gc : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+        const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
+        if (better(s2, g2, sc, gw)) {
+            sc = s2;
+            gw = g2;
+        }
+    }
+    sc_out = sc;
+    g_out = gw;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(FinalizeParams<T> p)
 {
     __shared__ T fin_smem[8][2 * kFinWarpVals];
     const int lane = threadIdx.x & 31;
@@ -67,6 +161,15 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double sqrt_m = sqrt((double)p.m);
     const int m = p.m;
+    if (p.err != nullptr && *p.err != 0) {
+        // a bounded wait of a tensor-core kernel ran out: the partials are incomplete
+        for (int64_t i = warp_global; i < p.nq; i += nwarps)
+            if (lane == 0) {
+                p.out_dist[i] = NAN;
+                p.out_idx[i] = -1;
+            }
+        return;
+    }
     for (int64_t i = warp_global; i < p.nq; i += nwarps) {
         // 1. reduce the column groups: largest q, then lowest chunk start
         T q = T(-INFINITY);
@@ -101,81 +204,49 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams<T> p)
                 }
             } else {
                 if (g >= 0) {
-                    // 2. re-score the chunk's windows g .. g + kChunk - 1. The warp stages
-                    // the shifted query window and the candidates' samples in shared
-                    // memory with coalesced loads, kFinChunk values of k at a time. Each
-                    // half-warp takes 8 candidates; lane l of a half sums the products of
-                    // a contiguous run of k for its 8 candidates (a sliding window of
-                    // dictionary samples in registers), and a transposing butterfly
-                    // leaves candidate 8 * half + (l & 7)'s total in lane l.
+                    // 2. re-score the winning chunk, and every chunk whose
+                    // approximate score came within the near-tie width of the
+                    // best (other groups' winners and the plain kernel's
+                    // near-tie records), so that the recurrence's rounding
+                    // cannot decide between near-tied windows
                     const Split<T> ma = p.ms_a[i];
-                    const T sa = ma.hi, sb = p.ms_b[g].hi;
-                    const int half = lane >> 4, lg = lane & 15;
-                    T acc[8];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) acc[c] = T(0);
-                    for (int kc = 0; kc < m; kc += kFinChunk) {
-                        const int len = min(kFinChunk, m - kc);
-                        for (int e = lane; e < len; e += 32) wa[fpad(e)] = p.a[i + kc + e] - sa;
-                        for (int e = lane; e < len + kChunk; e += 32) {
-                            const int64_t j = (int64_t)g + kc + e;
-                            wb[fpad(e)] = (j < p.nb) ? p.b[j] - sb : T(0);
-                        }
-                        __syncwarp();
-                        const int kpl = (len + 15) >> 4;
-                        const int k0 = lg * kpl;
-                        const int k1 = min(len, k0 + kpl);
-                        T bw[8];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) bw[c] = (k0 < k1) ? wb[fpad(8 * half + k0 + c)] : T(0);
-                        for (int kb = k0; kb < k1; kb += 8) {
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const int k = kb + u;
-                                if (k < k1) {
-                                    const T av = wa[fpad(k)];
-#pragma unroll
-                                    for (int c = 0; c < 8; ++c) acc[c] = fma(av, bw[(c + u) & 7], acc[c]);
-                                    bw[u] = wb[fpad(8 * half + k + 8)];
+                    T sc;
+                    int32_t gw;
+                    rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, g, ma, lane, wa, wb, sc,
+                                     gw);
+                    if (p.near != nullptr) {
+                        const T lim = q - T(kNearTieRho) * T(m) / p.rs_a[i].z;  // the row is not constant: z > 0
+                        for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
+                            const int k = k0 + lane;
+                            int32_t c0 = -1, c1 = -1, c2 = -1;
+                            if (k < p.n_groups) {
+                                const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+                                if (v.g >= 0 && v.g != g && v.q >= lim) c0 = v.g;
+                                const NearTies nt = p.near[(int64_t)k * p.nq + i];
+                                if (nt.g0 >= 0 && nt.g0 != g && T(nt.q0) >= lim) c1 = nt.g0;
+                                if (nt.g1 >= 0 && nt.g1 != g && T(nt.q1) >= lim) c2 = nt.g1;
+                            }
+                            unsigned pend = __ballot_sync(0xffffffffu, c0 >= 0 || c1 >= 0 || c2 >= 0);
+                            while (pend) {
+                                const int src = __ffs(pend) - 1;
+                                pend &= pend - 1;
+                                const int32_t s0 = __shfl_sync(0xffffffffu, c0, src);
+                                const int32_t s1 = __shfl_sync(0xffffffffu, c1, src);
+                                const int32_t s2c = __shfl_sync(0xffffffffu, c2, src);
+#pragma unroll 1
+                                for (int u = 0; u < 3; ++u) {
+                                    const int32_t cu = u == 0 ? s0 : (u == 1 ? s1 : s2c);
+                                    if (cu < 0) continue;
+                                    T s2;
+                                    int32_t g2;
+                                    rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, cu, ma, lane,
+                                                     wa, wb, s2, g2);
+                                    if (better(s2, g2, sc, gw)) {
+                                        sc = s2;
+                                        gw = g2;
+                                    }
                                 }
                             }
-                        }
-                        __syncwarp();  // the next chunk overwrites the staged samples
-                    }
-#pragma unroll
-                    for (int s = 4; s >= 1; s >>= 1) {
-#pragma unroll
-                        for (int c = 0; c < s; ++c) {
-                            const bool up = (lane & s) != 0;
-                            const T send = up ? acc[c] : acc[c + s];
-                            const T keep = up ? acc[c + s] : acc[c];
-                            acc[c] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-                        }
-                    }
-                    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);  // the two k-halves of the 16 lanes
-                    const int cand = 8 * half + (lane & 7);
-                    const int64_t gc = (int64_t)g + cand;
-                    bool ok = gc < p.npos_b;
-                    vec4_t<T> r;
-                    if (ok) {
-                        r = p.rs_b[gc];
-                        ok = r.w == T(0);
-                    }
-                    T sc = T(-INFINITY);
-                    if (ok) {
-                        // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
-                        const Split<T> mb = p.ms_b[gc];
-                        const T cov = acc[0] - T(m) * ma.lo * ((mb.hi - sb) + mb.lo);
-                        sc = cov * r.z;
-                    }
-                    int32_t gw = ok ? (int32_t)gc : -1;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
-                        const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
-                        if (better(s2, g2, sc, gw)) {
-                            sc = s2;
-                            gw = g2;
                         }
                     }
                     if (gw >= 0) {

@@ -76,6 +76,22 @@ template <typename T> struct Partial {
     int32_t g;
 };
 
+// Near-tie records of the FP32 plain kernel for one (column group, query
+// window): up to two chunks (first window g, -1 if unused) whose approximate
+// score q came within kNearTieRho (in Pearson correlation) below the running
+// best, or that were the best until overtaken by less than that. The
+// recurrence's rounding can misorder such chunks; the finalisation re-scores
+// each of them exactly, so the pick does not depend on that rounding.
+struct __align__(16) NearTies {
+    int32_t g0;
+    float q0;
+    int32_t g1;
+    float q1;
+};
+// Near-tie width in correlation, many times the FP32 recurrence's error
+// (about 1e-6 to 5e-6 in rho over 512-step diagonals).
+constexpr float kNearTieRho = 4e-5f;
+
 struct PlainLaunch {
     int64_t nq;            // query windows
     int32_t m;
@@ -86,10 +102,16 @@ struct PlainLaunch {
 
 // Plain diagonal-recurrence join (kernel K2). Writes part[group * nq + row].
 // spans[group_start[k] .. group_start[k+1]) are the spans of column group k.
+// seed_top (may be null): the centred covariances of each warp's first query
+// window, row r / (32 * rows per lane) at column g, row stride seed_ld (as
+// written by tc_seeds); null makes the kernel compute them itself.
+// near (may be null; FP32 only): [n_groups][nq] near-tie records, written
+// for every query window.
 template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
-                         const int32_t *group_start, Partial<T> *part, cudaStream_t st);
+                         const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
+                         NearTies *near, cudaStream_t st);
 template <typename T> size_t plain_smem_bytes(int warps, int m);
 
 // Serving: one request of a persistent batched launch (FP32 data). The layout
@@ -109,6 +131,9 @@ struct PlainRequest {
     const Span *spans;
     const int32_t *group_start;
     Partial<float> *part;
+    const float *seed_top;  // always null: batched work computes its own seeds
+    int64_t seed_ld;
+    NearTies *near;         // [n_groups][nq] near-tie records (required)
 };
 struct BatchItem {
     int32_t req;  // index into the request array
@@ -143,6 +168,8 @@ template <typename T> struct FinalizeParams {
     int64_t g_first;          // lowest valid dictionary window, or -1 (no window at all)
     double *out_dist;
     int64_t *out_idx;
+    const int32_t *err;       // may be null; if *err != 0 a tensor-core wait ran out: NaN / -1 everywhere
+    const NearTies *near;     // may be null; [n_groups][nq] near-tie records of the plain kernel
 };
 template <typename T> cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st);
 

@@ -55,7 +55,47 @@ template <typename T> struct PlainParams {
     const Span *spans;
     const int32_t *group_start;
     Partial<T> *part;
+    const T *seed_top;  // top seeds from the tensor cores, or null
+    int64_t seed_ld;
+    NearTies *near;     // near-tie records, or null
 };
+
+// Add a near-tie record (chunk g, approximate score q) to a slot; with both
+// entries in use, the lower-scoring one is replaced if q is higher.
+__device__ __forceinline__ void near_record(NearTies *slot, int32_t g, float q)
+{
+    NearTies v = *slot;
+    if (v.g0 < 0) {
+        v.g0 = g;
+        v.q0 = q;
+    } else if (v.g1 < 0) {
+        v.g1 = g;
+        v.q1 = q;
+    } else if (q > fminf(v.q0, v.q1)) {
+        if (v.q0 <= v.q1) {
+            v.g0 = g;
+            v.q0 = q;
+        } else {
+            v.g1 = g;
+            v.q1 = q;
+        }
+    }
+    *slot = v;
+}
+
+// Asynchronous copy of one element from global to shared memory; zero-fills
+// the destination when !valid (src is then not read).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const uint32_t n = valid ? (uint32_t)sizeof(T) : 0u;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Padded shared-memory index: one pad slot every P elements, so that lanes
 // reading with a stride of P (or P+...) hit distinct banks.
@@ -63,7 +103,10 @@ template <int P> __device__ __forceinline__ int pad(int e) { return e + e / P; }
 
 // One work item: query rows [rb * rows_cta, (rb + 1) * rows_cta) against the
 // spans of column group grp.
-template <typename T, int kRows>
+// kSeeds: the top seeds come from p.seed_top (the tensor cores) instead of
+// direct dot products; kNear: near ties are recorded in p.near. Both are
+// compile-time so that each form carries only its own code.
+template <typename T, int kRows, bool kSeeds, bool kNear>
 __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, int grp, unsigned char *smem_raw)
 {
     constexpr int CB = kPlainColBlock;
@@ -100,6 +143,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     const int64_t r0 = r_w + (int64_t)lane * kRows;       // first row of this lane
     T dfa[kRows], dga[kRows], C[kRows], best[kRows];
     int32_t bchunk[kRows];  // first window of the chunk holding the row's best score
+    T sig_max = T(0);       // largest std of the lane's (non-constant) rows
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
         const int64_t r = r0 + j;
@@ -107,6 +151,10 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             const vec4_t<T> v = p.rs_a[r];
             dfa[j] = v.x;
             dga[j] = v.y;
+            if (kNear) {
+                if (v.z > T(0)) sig_max = fmax(sig_max, T(1) / v.z);
+                p.near[(int64_t)grp * p.nq + r] = NearTies{-1, 0.f, -1, 0.f};
+            }
         } else {
             dfa[j] = T(0);
             dga[j] = T(0);
@@ -115,6 +163,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
         best[j] = T(-INFINITY);
         bchunk[j] = -1;
     }
+    // near-tie width in units of the score q = C * invstd_b (q = rho * m * std_a),
+    // taken with the lane's largest std so that it covers every row of the lane
+    const T tq = T(kNearTieRho) * T(m) * sig_max;
     const Split<T> mw = p.ms_a[r_w < p.nq ? r_w : p.nq - 1];
     const T da_w = (mw.hi - shift_a) + mw.lo;
     const int sa_w = warp * 32 * kRows;      // sa index of this warp's first row
@@ -127,6 +178,20 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             const int ncb = min(CB, sp.ncols - cb);
             const int64_t gblk = sp.g0 + cb;
             const T shift_b = p.ms_b[gblk].hi;
+            // top seeds from the tensor cores: this warp's row of them for the
+            // block's columns, copied to shared memory asynchronously so the
+            // latency overlaps the staging (zeros past the block / the rows)
+            if (kSeeds) {
+                __syncwarp();  // lane 0 has read this warp's seeds of the previous block
+                const bool wok = r_w < p.nq;
+                const T *src = p.seed_top + (wok ? r_w / (32 * kRows) : 0) * p.seed_ld + gblk;
+#pragma unroll
+                for (int t = 0; t < CB / 32; ++t) {
+                    const int c = lane + 32 * t;
+                    const bool v = wok && c < ncb;
+                    cp_async_elem(&stop[warp * CB + c], v ? src + c : p.seed_top, v);
+                }
+            }
             __syncthreads();  // previous block's sb / stop no longer in use
             for (int e = threadIdx.x; e < NB; e += blockDim.x) {
                 const int64_t j = gblk + e;
@@ -148,7 +213,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             __syncthreads();
 
             // ---- top seeds: C(r_w, gblk + c) for c in [8*lane, 8*lane + 8) ----
-            {
+            if (kSeeds) {
+                cp_async_wait_all();  // the __syncwarp below publishes them to lane 0
+            } else {
                 T acc[8], bw[8];
                 const int c0 = 8 * lane;
 #pragma unroll
@@ -232,12 +299,30 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fma(C[j], cs.z, cs.w));
                 }
                 const int32_t gch = (int32_t)(gblk + c0);
+                if (kNear) {
+                    // near ties: a chunk within tq below the running best, or a
+                    // best overtaken by less than tq (-inf on either side gives
+                    // inf or NaN, which fmin skips: no tie). One test per row,
+                    // one branch per chunk.
+                    T mn = T(INFINITY);
+#pragma unroll
+                    for (int j = 0; j < kRows; ++j) mn = fmin(mn, fabs(cm[j] - best[j]));
+                    if (mn <= tq) {
+#pragma unroll
+                        for (int j = 0; j < kRows; ++j) {
+                            if (fabs(cm[j] - best[j]) <= tq && r0 + j < p.nq) {
+                                const bool upd = cm[j] > best[j];
+                                near_record(p.near + (int64_t)grp * p.nq + r0 + j, upd ? bchunk[j] : gch,
+                                            (float)(upd ? best[j] : cm[j]));
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < kRows; ++j) {
-                    if (cm[j] > best[j]) {
-                        best[j] = cm[j];
-                        bchunk[j] = gch;
-                    }
+                    const bool upd = cm[j] > best[j];
+                    best[j] = upd ? cm[j] : best[j];
+                    bchunk[j] = upd ? gch : bchunk[j];
                 }
             }
         }
@@ -258,17 +343,17 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 // Four CTAs (16 warps) per SM for FP32 data: the kernel then fits in 128
 // registers without spilling, and the extra warps hide the shuffle and
 // shared-memory latencies of the recurrence.
-template <typename T, int kRows>
+template <typename T, int kRows, bool kSeeds, bool kNear>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_plain(PlainParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    plain_item<T, kRows>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
+    plain_item<T, kRows, kSeeds, kNear>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
 }
 
 // Persistent batched form for serving: the CTAs walk a list of work items that
 // may belong to different requests (different query, dictionary and m). Items
 // are claimed in list order with a global counter.
-template <typename T, int kRows>
+template <typename T, int kRows, bool kNear>
 __global__ void __launch_bounds__(128, 2) k_plain_batched(const PlainParams<T> *__restrict__ reqs,
                                                        const BatchItem *__restrict__ items, int32_t n_items,
                                                        int32_t *__restrict__ counter)
@@ -283,7 +368,7 @@ __global__ void __launch_bounds__(128, 2) k_plain_batched(const PlainParams<T> *
         if (it >= n_items) break;
         const BatchItem bi = items[it];
         const PlainParams<T> p = reqs[bi.req];
-        plain_item<T, kRows>(p, bi.rb, bi.grp, smem_raw);
+        plain_item<T, kRows, false, kNear>(p, bi.rb, bi.grp, smem_raw);  // seeds computed here
     }
 }
 
@@ -304,9 +389,10 @@ size_t plain_smem_bytes(int warps, int m)
 template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
-                         const int32_t *group_start, Partial<T> *part, cudaStream_t st)
+                         const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
+                         NearTies *near, cudaStream_t st)
 {
-    PlainParams<T> p;
+    PlainParams<T> p{};
     p.a = a;
     p.na = na;
     p.nq = L.nq;
@@ -321,14 +407,27 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     p.spans = spans;
     p.group_start = group_start;
     p.part = part;
+    p.seed_top = seed_top;
+    p.seed_ld = seed_ld;
+    p.near = near;
     const size_t smem = plain_smem_bytes<T>(L.warps, L.m);
     constexpr int R = plain_rows_per_lane<T>();
-    auto kern = k_plain<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)L.n_row_blocks * L.n_groups;
-    kern<<<(unsigned)grid, 32 * L.warps, smem, st>>>(p);
-    return cudaGetLastError();
+    auto launch = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)grid, 32 * L.warps, smem, st>>>(p);
+        return cudaGetLastError();
+    };
+    if constexpr (sizeof(T) == 8) {
+        // FP64 data: seeds from direct dot products, no near-tie records
+        if (seed_top != nullptr || near != nullptr) return cudaErrorInvalidValue;
+        return launch(k_plain<T, R, false, false>);
+    } else {
+        if (seed_top != nullptr)
+            return near != nullptr ? launch(k_plain<T, R, true, true>) : launch(k_plain<T, R, true, false>);
+        return near != nullptr ? launch(k_plain<T, R, false, true>) : launch(k_plain<T, R, false, false>);
+    }
 }
 
 cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *items, int32_t n_items,
@@ -336,7 +435,7 @@ cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *
 {
     static_assert(sizeof(PlainRequest) == sizeof(PlainParams<float>), "request layout");
     const size_t smem = plain_smem_bytes<float>(warps, max_m);
-    auto kern = k_plain_batched<float, kPlainRowsPerLane>;
+    auto kern = k_plain_batched<float, kPlainRowsPerLane, true>;  // every request carries near-tie slots
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 32 * warps, smem, st>>>(reinterpret_cast<const PlainParams<float> *>(reqs_dev), items, n_items,
@@ -349,10 +448,10 @@ template size_t plain_smem_bytes<double>(int, int);
 template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,
                                          const Split<float> *, const float *, int64_t, const float4 *,
                                          const Split<float> *, const Span *, const int32_t *, Partial<float> *,
-                                         cudaStream_t);
+                                         const float *, int64_t, NearTies *, cudaStream_t);
 template cudaError_t launch_plain<double>(const PlainLaunch &, const double *, int64_t, const dvec4 *,
                                           const Split<double> *, const double *, int64_t, const dvec4 *,
                                           const Split<double> *, const Span *, const int32_t *, Partial<double> *,
-                                          cudaStream_t);
+                                          const double *, int64_t, NearTies *, cudaStream_t);
 
 }  // namespace mpd

@@ -190,8 +190,8 @@ struct mp_ctx {
     };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> ev_pool;
-    double prof_ms[MP_PHASE_COUNT] = {0, 0, 0};
-    int64_t prof_n[MP_PHASE_COUNT] = {0, 0, 0};
+    double prof_ms[MP_PHASE_COUNT] = {};
+    int64_t prof_n[MP_PHASE_COUNT] = {};
 
     // pinned staging buffers, free lists by power-of-two size class
     std::map<size_t, std::vector<void *>> pinned_free;
@@ -454,6 +454,8 @@ static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const P
     f.g_first = s->g_first;
     f.out_dist = dist;
     f.out_idx = idx;
+    f.err = nullptr;
+    f.near = nullptr;
     return f;
 }
 
@@ -486,15 +488,33 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
     return g;
 }
 
-// Workspace layout of one join.
-struct JoinWs {
-    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, total;
+// Top seeds of the plain FP32 kernel computed on the tensor cores: one row
+// per warp of query windows (every 32 * kPlainRowsPerLane-th window), one
+// column per dictionary window position.
+struct SeedGeo {
+    int64_t n_srows, ld;
+    size_t bytes;
 };
 
-static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front)
+static SeedGeo seed_geometry(int64_t nq, int64_t npos_b)
+{
+    SeedGeo g;
+    const int64_t stride = 32 * kPlainRowsPerLane;
+    g.n_srows = (nq + stride - 1) / stride;
+    g.ld = (std::max<int64_t>(1, npos_b) + 3) & ~(int64_t)3;
+    g.bytes = (size_t)g.n_srows * (size_t)g.ld * sizeof(float);
+    return g;
+}
+
+// Workspace layout of one join.
+struct JoinWs {
+    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_seed, total;
+};
+
+static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front, size_t seed_bytes = 0)
 {
     JoinWs w;
-    // error word of the tensor-core kernel at the front
+    // error word of the tensor-core kernels at the front
     const size_t e = dtype == MP_F64 ? 8 : 4;
     size_t o = align_up(extra_front, 256);
     w.off_err = o;
@@ -511,21 +531,42 @@ static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t ext
     o = align_up(o + nq * 2 * e, 256);
     w.off_part = o;
     o = align_up(o + (size_t)n_groups * nq * (e == 8 ? sizeof(Partial<double>) : sizeof(Partial<float>)), 256);
+    // near-tie records of the FP32 plain kernel, one per (column group, query window)
+    w.off_near = o;
+    if (dtype == MP_F32) o = align_up(o + (size_t)n_groups * nq * sizeof(NearTies), 256);
+    w.off_seed = o;
+    o = align_up(o + seed_bytes, 256);
     w.total = o;
     return w;
 }
 
+// Seed bytes a join of this shape reserves (FP32 joins that may take the
+// plain kernel with tensor-core seeds).
+static size_t join_seed_bytes(const mp_dict *d, int32_t dtype, int64_t nq, int32_t m, bool seeds)
+{
+    if (!seeds || dtype != MP_F32) return 0;
+    return seed_geometry(nq, d->nb - m + 1).bytes;
+}
+
 // The join on device buffers; `base` is a device workspace of at least
 // join_ws_layout(...).total bytes. Everything is enqueued on `st`.
+// With `seeds`, an FP32 plain join takes its top seeds from the tensor cores
+// (the workspace then holds join_seed_bytes(..., true) more bytes). The
+// error word at the front of the workspace is zeroed first; tensor-core
+// kernels set it when a bounded wait runs out.
 static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, int32_t dtype, int64_t n, int32_t m,
-                       double *d_dist, int64_t *d_idx, cudaStream_t st, unsigned char *base, int kernel)
+                       double *d_dist, int64_t *d_idx, cudaStream_t st, unsigned char *base, int kernel,
+                       bool seeds = true)
 {
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl, dtype, m);
     const bool tc = (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32);
-    JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0);
+    JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0,
+                              join_seed_bytes(d, dtype, nq, m, seeds));
+    int32_t *err = (int32_t *)(base + w.off_err);
+    CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
     double *mean_a = (double *)(base + w.off_mean);
     double *inv_a = (double *)(base + w.off_inv);
     uint8_t *cf_a = (uint8_t *)(base + w.off_cflag);
@@ -551,7 +592,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
             CUDA_TRY(launch_plain<double>(L, a, n, rs_a, ms_a, (const double *)d->d_samples, d->nb,
                                           (const dvec4 *)s->rs, (const Split<double> *)s->ms, gr->spans,
-                                          gr->group_start, part, st));
+                                          gr->group_start, part, nullptr, 0, nullptr, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
@@ -568,9 +609,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         }
         if (tc) {
             Partial<float> *part = (Partial<float> *)(base + w.off_part);
-            int32_t *err = (int32_t *)(base + w.off_err);
             int ng = 1;
-            CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
             {
                 PhaseTimer t(ctx, MP_PHASE_JOIN, st);
                 int rc = tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
@@ -581,33 +620,53 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             }
             {
                 PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
-                CUDA_TRY(launch_finalize<float>(
-                    fin_params<float>(nq, m, ng, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx), st));
+                FinalizeParams<float> f = fin_params<float>(nq, m, ng, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
+                f.err = err;
+                CUDA_TRY(launch_finalize<float>(f, st));
             }
             return MP_OK;
         }
         Partial<float> *part = (Partial<float> *)(base + w.off_part);
+        NearTies *near = (NearTies *)(base + w.off_near);
+        float *seed_top = nullptr;
+        int64_t seed_ld = 0;
+        if (seeds) {
+            PhaseTimer t(ctx, MP_PHASE_SEEDS, st);
+            const SeedGeo sg = seed_geometry(nq, d->nb - m + 1);
+            seed_top = (float *)(base + w.off_seed);
+            seed_ld = sg.ld;
+            int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb, s->seg_spans.data(),
+                              (int32_t)s->seg_spans.size(), s->ms, a, n, m, ms_a, 32 * kPlainRowsPerLane, seed_top,
+                              seed_ld, err, st, fail);
+            if (rc) return rc;
+        }
         {
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
             CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb,
                                          (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
-                                         gr->group_start, part, st));
+                                         gr->group_start, part, seed_top, seed_ld, near, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
-            CUDA_TRY(launch_finalize<float>(
-                fin_params<float>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx), st));
+            FinalizeParams<float> f =
+                fin_params<float>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
+            f.err = seeds ? err : nullptr;
+            f.near = near;
+            CUDA_TRY(launch_finalize<float>(f, st));
         }
     }
     return MP_OK;
 }
 
-static size_t join_ws_bytes(const mp_ctx *ctx, const DictStats *s, int32_t dtype, int64_t n, int32_t m)
+static size_t join_ws_bytes(const mp_ctx *ctx, const mp_dict *d, const DictStats *s, int32_t dtype, int64_t n,
+                            int32_t m, bool seeds = true)
 {
     const int64_t nq = n - m + 1;
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     const Geometry geo = plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl, dtype, m);
-    return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0).total;
+    return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0,
+                          join_seed_bytes(d, dtype, nq, m, seeds))
+        .total;
 }
 
 static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s, int64_t nq)
@@ -633,7 +692,7 @@ static size_t request_bytes(const mp_ctx *ctx, const Request &r, const DictStats
 {
     const int64_t nq = r.n - r.m + 1;
     return align_up((size_t)r.n * dtype_size(r.dtype), 256) + align_up(nq * 16, 256) +
-           join_ws_bytes(ctx, s, r.dtype, r.n, r.m);
+           join_ws_bytes(ctx, r.dict, s, r.dtype, r.n, r.m, false);
 }
 
 // Pinned host buffer of at least `bytes` (caller holds ctx->smu or is the
@@ -732,7 +791,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
                 continue;
             }
             rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p,
-                             resolve_kernel(ctx, r.dtype, r.m, s, nq));
+                             resolve_kernel(ctx, r.dtype, r.m, s, nq), false);
             if (rc) return rc;
             CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
             continue;
@@ -752,8 +811,9 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         float4 *rs_a = (float4 *)(p + w.off_rs);
         Split<float> *ms_a = (Split<float> *)(p + w.off_ms);
         Partial<float> *part = (Partial<float> *)(p + w.off_part);
+        NearTies *near = (NearTies *)(p + w.off_near);
         CUDA_TRY(launch_window_stats<float>(a, r.n, r.m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
-        PlainRequest pr;
+        PlainRequest pr{};  // seed_top null: the batched kernel computes its seeds
         pr.a = a;
         pr.na = r.n;
         pr.nq = nq;
@@ -768,6 +828,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         pr.spans = gr->spans;
         pr.group_start = gr->group_start;
         pr.part = part;
+        pr.near = near;
         const int ridx = (int)preqs.size();
         preqs.push_back(pr);
         for (int64_t rb = 0; rb < geo.n_row_blocks; ++rb)
@@ -795,11 +856,12 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
             Request &r = *ps.r;
             const int64_t nq = r.n - r.m + 1;
             JoinWs w = join_ws_layout(nq, r.dtype, ps.n_groups, 0);
-            CUDA_TRY(launch_finalize<float>(
+            FinalizeParams<float> f =
                 fin_params<float>(nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part), ps.a,
                                   (const float4 *)(ps.base + w.off_rs), (const Split<float> *)(ps.base + w.off_ms),
-                                  (const uint8_t *)(ps.base + w.off_cflag), r.dict, ps.s, ps.dist, ps.idx),
-                st));
+                                  (const uint8_t *)(ps.base + w.off_cflag), r.dict, ps.s, ps.dist, ps.idx);
+            f.near = (const NearTies *)(ps.base + w.off_near);
+            CUDA_TRY(launch_finalize<float>(f, st));
             CUDA_TRY(cudaMemcpyAsync(r.h_stage, ps.dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
         }
     }
@@ -1070,7 +1132,7 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
         CUDA_TRY(cudaStreamSynchronize(st));
         return MP_OK;
     }
-    rc = ensure_ws(ctx, join_ws_bytes(ctx, s, dtype, n, m));
+    rc = ensure_ws(ctx, join_ws_bytes(ctx, d, s, dtype, n, m));
     if (rc) return rc;
     if (st != ctx->stream) {
         // the workspace may still be in use by earlier work on the context stream
@@ -1117,7 +1179,7 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     }
     const size_t qbytes = align_up((size_t)n * dtype_size(dtype), 256);
     const size_t obytes = align_up((size_t)nq * 8, 256);
-    const size_t jb = join_ws_bytes(ctx, s, dtype, n, m);
+    const size_t jb = join_ws_bytes(ctx, d, s, dtype, n, m);
     rc = ensure_ws(ctx, qbytes + 2 * obytes + jb);
     if (rc) return rc;
     unsigned char *base = (unsigned char *)ctx->ws;
@@ -1131,10 +1193,9 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
+    // the error word of the tensor-core kernels (zeroed by join_device)
     int32_t err = 0;
-    const int kused = resolve_kernel(ctx, dtype, m, s, nq);
-    const bool tc = (kused == MP_KERNEL_TC_BF16X3 || kused == MP_KERNEL_TC_TF32);
-    if (tc) CUDA_TRY(cudaMemcpyAsync(&err, base + qbytes + 2 * obytes, sizeof err, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&err, base + qbytes + 2 * obytes, sizeof err, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     if (err) return fail(MP_E_TIMEOUT, "a tensor-core wait timed out on the device; results are invalid");
     return MP_OK;
@@ -1402,7 +1463,8 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
         cands.push_back(Cand{MP_KERNEL_TC_BF16X3, 1});
     if (dtype == MP_F32 && tolerance <= 0 && tc_supported(1, m)) cands.push_back(Cand{MP_KERNEL_TC_TF32, 1});
     const int saved_kernel = ctx->kernel;
-    const size_t wsb = std::max(join_ws_layout(nq, dtype, 32, 0).total, join_ws_bytes(ctx, s, dtype, n, m));
+    const size_t wsb = std::max(join_ws_layout(nq, dtype, 32, 0, join_seed_bytes(d, dtype, nq, m, true)).total,
+                                join_ws_bytes(ctx, d, s, dtype, n, m));
     rc = ensure_ws(ctx, wsb);
     if (rc) {
         cudaFree(dq);
@@ -1472,14 +1534,15 @@ constexpr size_t kNoAllocFlagOff = kNoAllocInvOff + kNoAllocMaxWindows * sizeof(
 constexpr size_t kNoAllocRsOff = kNoAllocFlagOff + kNoAllocMaxWindows;
 constexpr size_t kNoAllocMsOff = kNoAllocRsOff + kNoAllocMaxWindows * sizeof(float4);
 constexpr size_t kNoAllocPartOff = kNoAllocMsOff + kNoAllocMaxWindows * sizeof(Split<float>);
-constexpr size_t kNoAllocSpanOff = kNoAllocPartOff + kNoAllocMaxPartials * sizeof(Partial<float>);
+constexpr size_t kNoAllocNearOff = kNoAllocPartOff + kNoAllocMaxPartials * sizeof(Partial<float>);
+constexpr size_t kNoAllocSpanOff = kNoAllocNearOff + kNoAllocMaxPartials * sizeof(NearTies);
 constexpr size_t kNoAllocGroupOff = kNoAllocSpanOff + kNoAllocMaxSpans * sizeof(Span);
 constexpr size_t kNoAllocBytes = kNoAllocGroupOff + (kNoAllocMaxSpans + 1) * sizeof(int32_t);
 constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
-// About 30 MB: statistics of 2^19 query windows, 2^20 partial results and
-// 2^16 spans. Host code must not use this name as an address: it is a
+// About 46 MB: statistics of 2^19 query windows, 2^20 partial results with
+// their near-tie records, and 2^16 spans. Host code must not use this name as an address: it is a
 // host-side stand-in; the device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 static unsigned char *g_noalloc_dev[kNoAllocMaxDevices];
@@ -1533,6 +1596,7 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
     float4 *rs_a = (float4 *)(base + kNoAllocRsOff);
     Split<float> *ms_a = (Split<float> *)(base + kNoAllocMsOff);
     Partial<float> *part = (Partial<float> *)(base + kNoAllocPartOff);
+    NearTies *near = (NearTies *)(base + kNoAllocNearOff);
     CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
     int n_groups = 0;
     if (s->n_windows > 0) {
@@ -1572,11 +1636,13 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
         L.n_groups = geo.n_groups;
         L.warps = geo.warps;
         CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb, (const float4 *)s->rs,
-                                     (const Split<float> *)s->ms, d_spans, d_gstart, part, st));
+                                     (const Split<float> *)s->ms, d_spans, d_gstart, part, nullptr, 0, near, st));
         n_groups = geo.n_groups;
     }
     // with no dictionary window (n_groups = 0, g_first = -1) this writes +inf / -1
-    CUDA_TRY(launch_finalize<float>(
-        fin_params<float>(nq, m, n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_out_dist, d_out_idx), st));
+    FinalizeParams<float> f =
+        fin_params<float>(nq, m, n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_out_dist, d_out_idx);
+    f.near = n_groups > 0 ? near : nullptr;
+    CUDA_TRY(launch_finalize<float>(f, st));
     return MP_OK;
 }

@@ -187,8 +187,8 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
-// Write one 16-byte chunk (EPC values) of a Hankel row: BF16 hi and lo
-// halves, or TF32 values.
+// Write one 16-byte chunk (EPC values) of an operand row: BF16 hi and lo
+// halves (VARIANT 0), TF32 values (1), or TF32 hi and lo halves (2).
 template <int VARIANT>
 __device__ __forceinline__ void put_chunk(const float *x, unsigned char *hi, unsigned char *lo, uint32_t off)
 {
@@ -205,8 +205,18 @@ __device__ __forceinline__ void put_chunk(const float *x, unsigned char *hi, uns
         }
         *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    } else {
+    } else if (VARIANT == 1) {
         *reinterpret_cast<float4 *>(hi + off) = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+    } else {
+        // TF32 hi and lo halves (x - hi is exact in FP32)
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = to_tf32(x[e]);
+            l[e] = to_tf32(x[e] - h[e]);
+        }
+        *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -552,6 +562,191 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
 }
 
 // ---------------------------------------------------------------------------
+// K2s: the plain kernel's top seeds on the tensor cores
+// ---------------------------------------------------------------------------
+// The plain recurrence (kernel K2) starts the diagonals of each warp's first
+// query window from a direct dot product per dictionary window. Those "top
+// seeds" form a dense product: for the query windows r_s = s * stride (s = 0,
+// 1, ...) and every valid dictionary window g,
+//     S[s, g] = sum_k (a[r_s + k] - mean_a[r_s]) * (b[g + k] - mean_b[g]),
+// the centred covariance of the two windows (the C of Sec. 3.2's per-segment
+// AB-join). A CTA owns 128 seed rows (the TMEM lanes) and walks the tiles of
+// one column group. Per tile and K-block (32 values of k) the 128 query
+// windows' samples are gathered into a K-major operand and the tile's
+// dictionary samples form a row-shifted Hankel operand as in K3. The products
+// are TF32 with a hi/lo split of both operands (hi*hi + hi*lo + lo*hi): each
+// value is split with a residual below 2^-22 of it, so a seed carries about
+// FP32's error, not the 2^-16 of a BF16 split; the recurrence adds its own
+// rounding to that seed for up to 32 * 16 rows. The epilogue removes the
+// shifts and stores S in FP32. A CTA builds and multiplies in turn; two CTAs
+// share an SM, so one CTA's operand build overlaps the other's MMAs.
+struct SeedArgs {
+    const float *a;
+    int64_t nq;
+    int32_t m;
+    int32_t n_groups;
+    int32_t stride;   // query windows from one seed row to the next
+    int64_t n_srows;  // seed rows: ceil(nq / stride)
+    const Split<float> *ms_a;
+    const float *b;
+    int64_t nb;
+    const Split<float> *ms_b;
+    const TcTile *tiles;
+    const int32_t *group_start;
+    float *seeds;  // [n_srows][ld]; column = global dictionary window g
+    int64_t ld;
+    int32_t *err;
+};
+
+constexpr int kSeedVariant = 2;  // TF32 hi/lo
+constexpr int kSeedThreads = 128;
+constexpr int kSeedRows = 128;
+constexpr int kSeedEpr = 32;  // TF32 values of K per 128-byte operand row
+constexpr int kSeedKstep = 8;  // K per MMA
+constexpr long long kSeedWaitCycles = 4000000000LL;  // about 2 s
+
+size_t seed_smem_bytes()
+{
+    // 1024-byte alignment slack, query operand (hi, lo), dictionary operand
+    // (hi, lo), staged samples, column terms, barrier and TMEM slot
+    return 1024 + 2 * (size_t)kSeedRows * 128 + 2 * (size_t)kTcMaxN * 128 + (kTcMaxN + kSeedEpr + 8) * 4 +
+           kTcMaxN * 4 + 16;
+}
+
+__global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *a_hi = base, *a_lo = base + kSeedRows * 128;
+    unsigned char *b_hi = base + 2 * kSeedRows * 128, *b_lo = b_hi + kTcMaxN * 128;
+    float *raw = reinterpret_cast<float *>(b_lo + kTcMaxN * 128);  // a tile's samples for one K-block
+    float *colp = raw + kTcMaxN + kSeedEpr + 8;                     // m * (mean_b - s_b) per column
+    uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t rb = blockIdx.x / p.n_groups;
+    const int grp = blockIdx.x % p.n_groups;
+    const int m = p.m;
+    const int nkb = (m + kSeedEpr - 1) / kSeedEpr;
+    const int t_lo = p.group_start[grp], t_hi = p.group_start[grp + 1];
+
+    if (warp == 0) tmem_alloc(tmem_slot, kTcMaxN);
+    if (tid == 0) mbar_init(bar, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+
+    // the accumulator row this thread reads back (TMEM lane tid)
+    const int64_t srow = rb * kSeedRows + tid;
+    const bool row_ok = srow < p.n_srows;
+    // the query rows are centred on their own mean's hi part; mean - hi = lo
+    const float da = row_ok ? p.ms_a[srow * p.stride].lo : 0.f;
+
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int t = t_lo; ok && t < t_hi; ++t) {
+        const TcTile tile = p.tiles[t];
+        const float s_b = p.ms_b[tile.g0].hi;
+        for (int n = tid; n < kTcMaxN; n += kSeedThreads) {
+            float v = 0.f;
+            if (n < tile.nvalid) {
+                const Split<float> mb = p.ms_b[tile.g0 + n];
+                v = (float)m * ((mb.hi - s_b) + mb.lo);
+            }
+            colp[n] = v;
+        }
+        const uint32_t idesc = instr_desc<kSeedVariant>(tile.nmma);
+        for (int q = 0; q < nkb; ++q) {
+            const int k0 = q * kSeedEpr;
+            // query operand: row rho holds a[r + k0 .. r + k0 + 31] - mean_hi(r)
+            // for seed window r (0 past m and past the last seed row)
+            {
+                const int c = tid & 7;
+                for (int rho = tid >> 3; rho < kSeedRows; rho += kSeedThreads / 8) {
+                    const int64_t sr = rb * kSeedRows + rho;
+                    float x[4];
+                    if (sr < p.n_srows) {
+                        const int64_t r = sr * p.stride;
+                        const float sa = p.ms_a[r].hi;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int k = k0 + 4 * c + e;
+                            x[e] = k < m ? p.a[r + k] - sa : 0.f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) x[e] = 0.f;
+                    }
+                    put_chunk<kSeedVariant>(x, a_hi, a_lo, (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4));
+                }
+            }
+            // dictionary operand: Hankel rows of b[g0 + k0 ..] - s_b
+            const int nraw = tile.nmma + kSeedEpr;
+            for (int e = tid; e < nraw; e += kSeedThreads) {
+                const int64_t j = tile.g0 + k0 + e;
+                raw[e] = j < p.nb ? p.b[j] - s_b : 0.f;
+            }
+            __syncthreads();
+            build_hankel<kSeedVariant>(raw, tile.nmma, b_hi, b_lo, tid, kSeedThreads);
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(a_hi), a1 = smem_u32(a_lo);
+                const uint32_t b0 = smem_u32(b_hi), b1 = smem_u32(b_lo);
+                // the query operand is 0 past m
+                const int ksteps = (min(kSeedEpr, m - k0) + kSeedKstep - 1) / kSeedKstep;
+                for (int k = 0; k < ksteps; ++k) {
+                    const uint32_t acc = (q == 0 && k == 0) ? 0u : 1u;
+                    mma<kSeedVariant>(taddr, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, acc);
+                    mma<kSeedVariant>(taddr, smem_desc(a0 + 32u * k), smem_desc(b1 + 32u * k), idesc, 1u);
+                    mma<kSeedVariant>(taddr, smem_desc(a1 + 32u * k), smem_desc(b0 + 32u * k), idesc, 1u);
+                }
+                mma_commit(bar);
+            }
+            // the next K-block rewrites the operands: wait for these MMAs
+            const bool w = mbar_wait(bar, phase, kSeedWaitCycles);
+            phase ^= 1u;
+            ok = __syncthreads_and(w ? 1 : 0) != 0;
+            tc_fence_after();
+            if (!ok) break;
+        }
+        if (!ok) break;
+        // epilogue: accumulator row tid, 32 columns per TMEM load
+        const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
+        const int ncols = (tile.nmma + 31) & ~31;
+        float *dst = p.seeds + (row_ok ? srow : 0) * p.ld + tile.g0;
+        for (int c32 = 0; c32 < ncols; c32 += 32) {
+            uint32_t v[32];
+            tmem_ld32(t_lane + (uint32_t)c32, v);
+            if (row_ok) {
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const int n = c32 + u;
+                    if (n < tile.nvalid) dst[n] = fmaf(-da, colp[n], __uint_as_float(v[u]));
+                }
+            }
+        }
+        // TMEM and colp are read before the next tile's MMAs and column terms
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok) {
+        // a wait ran out: give the MMAs in flight time to finish before the
+        // TMEM and shared memory are released, and report the error
+        mbar_wait(bar, phase ^ 1u, kSeedWaitCycles);
+        if (tid == 0) atomicExch(p.err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, kTcMaxN);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct TcPlan {
@@ -636,6 +831,46 @@ struct TcPacks {
     std::vector<TcPack> packs;
 };
 
+// Tiles of up to nmax consecutive windows that never cross a segment.
+std::vector<TcTile> make_tiles(const Span *seg_spans, int32_t n_seg, int nmax)
+{
+    std::vector<TcTile> tiles;
+    for (int32_t s = 0; s < n_seg; ++s)
+        for (int32_t c = 0; c < seg_spans[s].ncols; c += nmax) {
+            TcTile t;
+            t.g0 = seg_spans[s].g0 + c;
+            t.nvalid = std::min(nmax, seg_spans[s].ncols - c);
+            t.nmma = (t.nvalid + 15) & ~15;
+            tiles.push_back(t);
+        }
+    return tiles;
+}
+
+// The device tile table of this tile width split into ng column groups
+// (cached per dictionary and m); nullptr if device memory runs out.
+TcPack *get_pack(TcPacks *pk, const std::vector<TcTile> &tiles, int nmax, int ng)
+{
+    for (auto &p : pk->packs)
+        if (p.nmax == nmax && p.n_groups == ng) return &p;
+    const int n_tiles = (int)tiles.size();
+    TcPack np;
+    np.nmax = nmax;
+    np.n_groups = ng;
+    np.n_tiles = n_tiles;
+    std::vector<int32_t> gs(ng + 1);
+    for (int k = 0; k <= ng; ++k) gs[k] = (int32_t)((int64_t)n_tiles * k / ng);
+    if (cudaMalloc(&np.tiles, std::max<size_t>(1, tiles.size()) * sizeof(TcTile)) != cudaSuccess ||
+        cudaMalloc(&np.group_start, gs.size() * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(np.tiles);
+        return nullptr;
+    }
+    if (n_tiles) cudaMemcpy(np.tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice);
+    cudaMemcpy(np.group_start, gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    pk->packs.push_back(np);
+    return &pk->packs.back();
+}
+
 }  // namespace
 
 bool tc_supported(int variant, int m)
@@ -672,38 +907,11 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     const int64_t n_row_blocks = (nq + 127) / 128;
     if (!*pack) *pack = new TcPacks();
     TcPacks *pk = (TcPacks *)*pack;
-    // tiles of this dictionary for this tile width
-    std::vector<TcTile> tiles;
-    for (int32_t s = 0; s < n_seg; ++s)
-        for (int32_t c = 0; c < seg_spans[s].ncols; c += P.nmax) {
-            TcTile t;
-            t.g0 = seg_spans[s].g0 + c;
-            t.nvalid = std::min(P.nmax, seg_spans[s].ncols - c);
-            t.nmma = (t.nvalid + 15) & ~15;
-            tiles.push_back(t);
-        }
+    const std::vector<TcTile> tiles = make_tiles(seg_spans, n_seg, P.nmax);
     const int n_tiles = (int)tiles.size();
     int ng = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (2 * sm_count + n_row_blocks - 1) / n_row_blocks));
-    TcPack *use = nullptr;
-    for (auto &p : pk->packs)
-        if (p.nmax == P.nmax && p.n_groups == ng) use = &p;
-    if (!use) {
-        TcPack np;
-        np.nmax = P.nmax;
-        np.n_groups = ng;
-        np.n_tiles = n_tiles;
-        std::vector<int32_t> gs(ng + 1);
-        for (int k = 0; k <= ng; ++k) gs[k] = (int32_t)((int64_t)n_tiles * k / ng);
-        if (cudaMalloc(&np.tiles, std::max<size_t>(1, tiles.size()) * sizeof(TcTile)) != cudaSuccess ||
-            cudaMalloc(&np.group_start, gs.size() * sizeof(int32_t)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(MP_E_NOMEM, "tensor-core tile table");
-        }
-        if (n_tiles) cudaMemcpy(np.tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice);
-        cudaMemcpy(np.group_start, gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-        pk->packs.push_back(np);
-        use = &pk->packs.back();
-    }
+    TcPack *use = get_pack(pk, tiles, P.nmax, ng);
+    if (!use) return fail(MP_E_NOMEM, "tensor-core tile table");
     TcArgs A;
     A.a = a;
     A.na = n;
@@ -739,6 +947,49 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
         launch(k_tc<1>);
     if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core kernel launch: %s", cudaGetErrorString(e));
     *n_groups_out = ng;
+    return MP_OK;
+}
+
+int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
+             const void *ms_b, const float *a, int64_t n, int32_t m, const void *ms_a, int32_t stride, float *seeds,
+             int64_t ld, int32_t *err, cudaStream_t st, fail_fn fail)
+{
+    if (m < 1 || stride < 1) return fail(MP_E_ARG, "tensor-core seeds: bad m or stride");
+    const int64_t nq = n - m + 1;
+    const int64_t n_srows = (nq + stride - 1) / stride;
+    const int64_t n_rb = (n_srows + kSeedRows - 1) / kSeedRows;
+    if (!*pack) *pack = new TcPacks();
+    TcPacks *pk = (TcPacks *)*pack;
+    const std::vector<TcTile> tiles = make_tiles(seg_spans, n_seg, kTcMaxN);
+    const int n_tiles = (int)tiles.size();
+    if (n_tiles == 0 || n_srows <= 0) return MP_OK;
+    // about eight CTAs per SM over the launch (four waves of two per SM)
+    const int ng = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (8 * sm_count + n_rb - 1) / n_rb));
+    TcPack *use = get_pack(pk, tiles, kTcMaxN, ng);
+    if (!use) return fail(MP_E_NOMEM, "tensor-core tile table");
+    SeedArgs A;
+    A.a = a;
+    A.nq = nq;
+    A.m = m;
+    A.n_groups = ng;
+    A.stride = stride;
+    A.n_srows = n_srows;
+    A.ms_a = (const Split<float> *)ms_a;
+    A.b = b;
+    A.nb = nb;
+    A.ms_b = (const Split<float> *)ms_b;
+    A.tiles = use->tiles;
+    A.group_start = use->group_start;
+    A.seeds = seeds;
+    A.ld = ld;
+    A.err = err;
+    const size_t smem = seed_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        k_seed<<<(unsigned)(n_rb * ng), kSeedThreads, smem, st>>>(A);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core seed kernel launch: %s", cudaGetErrorString(e));
     return MP_OK;
 }
 

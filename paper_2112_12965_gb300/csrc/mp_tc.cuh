@@ -27,4 +27,15 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
             const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
             Partial<float> *part, int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail);
 
+// Top seeds of the plain kernel (K2s) on the tensor cores: for the query
+// windows r_s = s * stride, s < ceil(nq / stride), and every valid dictionary
+// window g, seeds[s * ld + g] = the centred covariance
+// sum_k (a[r_s + k] - mean_a[r_s]) (b[g + k] - mean_b[g]) in FP32 (three TF32
+// products of a hi/lo split). Positions g of windows that cross a segment end
+// are not written; ld >= nb - m + 1. *err is set to 1 on a device-side
+// timeout. Any m >= 1.
+int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
+             const void *ms_b, const float *a, int64_t n, int32_t m, const void *ms_a, int32_t stride, float *seeds,
+             int64_t ld, int32_t *err, cudaStream_t st, fail_fn fail);
+
 }  // namespace mpd
