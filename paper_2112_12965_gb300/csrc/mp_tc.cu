@@ -573,12 +573,14 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
 // AB-join). A CTA owns 128 seed rows (the TMEM lanes) and walks the tiles of
 // one column group. Per tile and K-block (32 values of k) the 128 query
 // windows' samples are gathered into a K-major operand and the tile's
-// dictionary samples form a row-shifted Hankel operand as in K3. The products
+// dictionary samples form a row-shifted Hankel operand as in K3 (the samples of
+// the next stage are loaded into registers while the MMAs run). The products
 // are TF32 with a hi/lo split of both operands (hi*hi + hi*lo + lo*hi): each
 // value is split with a residual below 2^-22 of it, so a seed carries about
 // FP32's error, not the 2^-16 of a BF16 split; the recurrence adds its own
 // rounding to that seed for up to 32 * 16 rows. The epilogue removes the
-// shifts and stores S in FP32. A CTA builds and multiplies in turn; two CTAs
+// shifts and stores S in FP32, transposed through shared memory so that the
+// stores are row-contiguous. A CTA builds and multiplies in turn; two CTAs
 // share an SM, so one CTA's operand build overlaps the other's MMAs.
 struct SeedArgs {
     const float *a;
@@ -624,8 +626,9 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
     float *colp = raw + kTcMaxN + kSeedEpr + 8;                     // m * (mean_b - s_b) per column
     uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    float *ost = reinterpret_cast<float *>(base);  // epilogue staging (operands are idle then): 128 x 33
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t rb = blockIdx.x / p.n_groups;
     const int grp = blockIdx.x % p.n_groups;
     const int m = p.m;
@@ -639,55 +642,89 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
     tc_fence_after();
     const uint32_t taddr = *tmem_slot;
 
+    // Query operand: this thread fills 16-byte chunk c of rows rho_i = tid / 8 + 16 i
+    // (4 values of k each); the rows are centred on their own mean's hi part.
+    const int c = tid & 7;
+    int64_t r_i[8];
+    float sa_i[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t sr = rb * kSeedRows + (tid >> 3) + 16 * i;
+        r_i[i] = sr < p.n_srows ? sr * p.stride : -1;
+        sa_i[i] = r_i[i] >= 0 ? p.ms_a[r_i[i]].hi : 0.f;
+    }
+    const bool a16 = (reinterpret_cast<uintptr_t>(p.a) & 15) == 0;
+    // Raw samples of one stage (tile t, K-block q) and, for a tile's first
+    // stage, its column terms, loaded into registers one stage ahead. Nothing
+    // consumes them until the next stage, so their latency overlaps the MMAs.
+    // Positions past m or past the series hold the shift itself (x - shift = 0).
+    float xa[8][4], xb[3];
+    Split<float> mbv[2];
+    TcTile tl_next;
+    float sb_next = 0.f;
+    const int n_st = (t_hi - t_lo) * nkb;
+    auto load_stage = [&](int j) {
+        tl_next = p.tiles[t_lo + j / nkb];
+        const int k0 = (j % nkb) * kSeedEpr;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = k0 + 4 * c;
+            if (r_i[i] >= 0 && a16 && k + 3 < m) {
+                const float4 v = *reinterpret_cast<const float4 *>(p.a + r_i[i] + k);
+                xa[i][0] = v.x;
+                xa[i][1] = v.y;
+                xa[i][2] = v.z;
+                xa[i][3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) xa[i][e] = (r_i[i] >= 0 && k + e < m) ? p.a[r_i[i] + k + e] : sa_i[i];
+            }
+        }
+        sb_next = p.ms_b[tl_next.g0].hi;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int e = tid + u * kSeedThreads;
+            const int64_t jj = tl_next.g0 + k0 + e;
+            xb[u] = (e < tl_next.nmma + kSeedEpr && jj < p.nb) ? p.b[jj] : sb_next;
+        }
+        if (j % nkb == 0) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int n = tid + u * kSeedThreads;
+                mbv[u] = n < tl_next.nvalid ? p.ms_b[tl_next.g0 + n] : Split<float>{sb_next, 0.f};
+            }
+        }
+    };
+    if (n_st > 0) load_stage(0);
+
     // the accumulator row this thread reads back (TMEM lane tid)
     const int64_t srow = rb * kSeedRows + tid;
-    const bool row_ok = srow < p.n_srows;
-    // the query rows are centred on their own mean's hi part; mean - hi = lo
-    const float da = row_ok ? p.ms_a[srow * p.stride].lo : 0.f;
+    const float da = srow < p.n_srows ? p.ms_a[srow * p.stride].lo : 0.f;  // mean - hi = lo
 
     uint32_t phase = 0;
     bool ok = true;
+    int j = 0;
     for (int t = t_lo; ok && t < t_hi; ++t) {
-        const TcTile tile = p.tiles[t];
-        const float s_b = p.ms_b[tile.g0].hi;
-        for (int n = tid; n < kTcMaxN; n += kSeedThreads) {
-            float v = 0.f;
-            if (n < tile.nvalid) {
-                const Split<float> mb = p.ms_b[tile.g0 + n];
-                v = (float)m * ((mb.hi - s_b) + mb.lo);
-            }
-            colp[n] = v;
-        }
+        const TcTile tile = tl_next;  // loaded with the tile's first stage
+        const float s_b = sb_next;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) colp[tid + u * kSeedThreads] = (float)m * ((mbv[u].hi - s_b) + mbv[u].lo);
         const uint32_t idesc = instr_desc<kSeedVariant>(tile.nmma);
-        for (int q = 0; q < nkb; ++q) {
+        for (int q = 0; q < nkb; ++q, ++j) {
             const int k0 = q * kSeedEpr;
-            // query operand: row rho holds a[r + k0 .. r + k0 + 31] - mean_hi(r)
-            // for seed window r (0 past m and past the last seed row)
-            {
-                const int c = tid & 7;
-                for (int rho = tid >> 3; rho < kSeedRows; rho += kSeedThreads / 8) {
-                    const int64_t sr = rb * kSeedRows + rho;
-                    float x[4];
-                    if (sr < p.n_srows) {
-                        const int64_t r = sr * p.stride;
-                        const float sa = p.ms_a[r].hi;
+            // write this stage's operands from the registers
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int k = k0 + 4 * c + e;
-                            x[e] = k < m ? p.a[r + k] - sa : 0.f;
-                        }
-                    } else {
+            for (int i = 0; i < 8; ++i) {
+                const int rho = (tid >> 3) + 16 * i;
+                float x[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) x[e] = 0.f;
-                    }
-                    put_chunk<kSeedVariant>(x, a_hi, a_lo, (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4));
-                }
+                for (int e = 0; e < 4; ++e) x[e] = xa[i][e] - sa_i[i];
+                put_chunk<kSeedVariant>(x, a_hi, a_lo, (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4));
             }
-            // dictionary operand: Hankel rows of b[g0 + k0 ..] - s_b
-            const int nraw = tile.nmma + kSeedEpr;
-            for (int e = tid; e < nraw; e += kSeedThreads) {
-                const int64_t j = tile.g0 + k0 + e;
-                raw[e] = j < p.nb ? p.b[j] - s_b : 0.f;
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int e = tid + u * kSeedThreads;
+                if (e < kTcMaxN + kSeedEpr) raw[e] = xb[u] - s_b;
             }
             __syncthreads();
             build_hankel<kSeedVariant>(raw, tile.nmma, b_hi, b_lo, tid, kSeedThreads);
@@ -707,7 +744,8 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
                 }
                 mma_commit(bar);
             }
-            // the next K-block rewrites the operands: wait for these MMAs
+            if (j + 1 < n_st) load_stage(j + 1);  // overlaps the MMAs
+            // the next stage rewrites the operands: wait for these MMAs
             const bool w = mbar_wait(bar, phase, kSeedWaitCycles);
             phase ^= 1u;
             ok = __syncthreads_and(w ? 1 : 0) != 0;
@@ -715,20 +753,22 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
             if (!ok) break;
         }
         if (!ok) break;
-        // epilogue: accumulator row tid, 32 columns per TMEM load
+        // epilogue: accumulator row tid, 32 columns per TMEM load, staged in
+        // shared memory so that each warp stores contiguous runs of a row
         const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
         const int ncols = (tile.nmma + 31) & ~31;
-        float *dst = p.seeds + (row_ok ? srow : 0) * p.ld + tile.g0;
         for (int c32 = 0; c32 < ncols; c32 += 32) {
             uint32_t v[32];
             tmem_ld32(t_lane + (uint32_t)c32, v);
-            if (row_ok) {
 #pragma unroll
-                for (int u = 0; u < 32; ++u) {
-                    const int n = c32 + u;
-                    if (n < tile.nvalid) dst[n] = fmaf(-da, colp[n], __uint_as_float(v[u]));
-                }
+            for (int u = 0; u < 32; ++u) ost[tid * 33 + u] = fmaf(-da, colp[c32 + u], __uint_as_float(v[u]));
+            __syncthreads();
+            const int n = c32 + lane;
+            for (int rr = warp; rr < kSeedRows; rr += kSeedThreads / 32) {
+                const int64_t sr = rb * kSeedRows + rr;
+                if (sr < p.n_srows && n < tile.nvalid) p.seeds[sr * p.ld + tile.g0 + n] = ost[rr * 33 + lane];
             }
+            __syncthreads();  // ost is rewritten by the next group (or the next tile's operands)
         }
         // TMEM and colp are read before the next tile's MMAs and column terms
         tc_fence_before();
