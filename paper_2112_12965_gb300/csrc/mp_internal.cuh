@@ -113,6 +113,8 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
                          const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
                          NearTies *near, cudaStream_t st);
 template <typename T> size_t plain_smem_bytes(int warps, int m);
+// Resident CTAs per SM of the plain kernel for this shape (occupancy API).
+template <typename T> int plain_ctas_per_sm(int warps, int m);
 
 // Serving: one request of a persistent batched launch (FP32 data). The layout
 // mirrors the kernel's parameter block.

@@ -103,6 +103,80 @@ template <int P> __device__ __forceinline__ int pad(int e) { return e + e / P; }
 
 // One work item: query rows [rb * rows_cta, (rb + 1) * rows_cta) against the
 // spans of column group grp.
+// Covariances C of a lane's kRows rows with their recurrence terms, and one
+// step of the recurrence (one column to the right). The generic form is
+// scalar. The FP32 form packs rows j and j + kRows/2 into one float2, so
+// that one packed FMA (fma.rn.f32x2: each half rounded once, exactly as
+// fmaf) advances two rows: moving one column right shifts every row down by
+// one, which maps pair k-1 onto pair k, and only pair 0 takes new inputs
+// (the row above the lane, and row kRows/2 - 1).
+template <typename T, int kRows> struct Rows {
+    T C[kRows], df[kRows], dg[kRows];
+    __device__ __forceinline__ void set_terms(int j, T f, T g)
+    {
+        df[j] = f;
+        dg[j] = g;
+    }
+    __device__ __forceinline__ void set(int j, T v) { C[j] = v; }
+    __device__ __forceinline__ T last() const { return C[kRows - 1]; }
+    // x, y: df_b, dg_b of the new column; up: the row above the lane's first
+    __device__ __forceinline__ void step(T x, T y, T up, bool take_seed, T seed)
+    {
+#pragma unroll
+        for (int j = kRows - 1; j >= 1; --j) C[j] = fma(df[j], y, fma(x, dg[j], C[j - 1]));
+        const T c0 = fma(df[0], y, fma(x, dg[0], up));
+        C[0] = take_seed ? seed : c0;
+    }
+    // cm[j] = max(cm[j], C[j] * z + w)
+    __device__ __forceinline__ void score_max(T z, T w, T *cm) const
+    {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fma(C[j], z, w));
+    }
+};
+
+template <int kRows> struct Rows<float, kRows> {
+    static constexpr int H = kRows / 2;
+    float2 C[H], df[H], dg[H];
+    __device__ __forceinline__ void set_terms(int j, float f, float g)
+    {
+        if (j < H) {
+            df[j].x = f;
+            dg[j].x = g;
+        } else {
+            df[j - H].y = f;
+            dg[j - H].y = g;
+        }
+    }
+    __device__ __forceinline__ void set(int j, float v)
+    {
+        if (j < H)
+            C[j].x = v;
+        else
+            C[j - H].y = v;
+    }
+    __device__ __forceinline__ float last() const { return C[H - 1].y; }
+    // X = (df_b, df_b), Y = (dg_b, dg_b) of the new column
+    __device__ __forceinline__ void step(float2 X, float2 Y, float up, bool take_seed, float seed)
+    {
+        const float2 in0 = make_float2(up, C[H - 1].x);
+#pragma unroll
+        for (int k = H - 1; k >= 1; --k) C[k] = __ffma2_rn(df[k], Y, __ffma2_rn(X, dg[k], C[k - 1]));
+        C[0] = __ffma2_rn(df[0], Y, __ffma2_rn(X, dg[0], in0));
+        C[0].x = take_seed ? seed : C[0].x;
+    }
+    // Z = (1/std_b, 1/std_b), W = (penalty, penalty)
+    __device__ __forceinline__ void score_max(float2 Z, float2 W, float *cm) const
+    {
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float2 q = __ffma2_rn(C[k], Z, W);
+            cm[k] = fmaxf(cm[k], q.x);
+            cm[k + H] = fmaxf(cm[k + H], q.y);
+        }
+    }
+};
+
 // kSeeds: the top seeds come from p.seed_top (the tensor cores) instead of
 // direct dot products; kNear: near ties are recorded in p.near. Both are
 // compile-time so that each form carries only its own code.
@@ -129,9 +203,16 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     const int NB_pad = pad<8>(NB) + 1;
     // stop: top seeds, one per (warp, column of the block)
     T *stop = sb + NB_pad;
-    // scs: recurrence terms of the block's columns (padded to whole chunks)
-    vec4_t<T> *scs = reinterpret_cast<vec4_t<T> *>(
-        (reinterpret_cast<uintptr_t>(stop + nwarps * CB) + 31) & ~static_cast<uintptr_t>(31));
+    // scs: recurrence terms of the block's columns (padded to whole chunks),
+    // 32 bytes per column, 32-byte aligned: (df, dg, 1/std, penalty) for FP64
+    // data; for FP32 the pairs (df, df, dg, dg) and (1/std, 1/std, penalty,
+    // penalty), so that 128-bit loads yield the packed FMA operands directly.
+    // Offset arithmetic on smem_raw keeps the shared address space visible to
+    // the compiler (shared, not generic, loads).
+    const size_t scs_off = ((size_t)(reinterpret_cast<unsigned char *>(stop + nwarps * CB) - smem_raw) + 31) &
+                           ~static_cast<size_t>(31);
+    vec4_t<T> *scs = reinterpret_cast<vec4_t<T> *>(smem_raw + scs_off);
+    float4 *scs2 = reinterpret_cast<float4 *>(smem_raw + scs_off);
 
     const T shift_a = p.ms_a[R0 < p.nq ? R0 : p.nq - 1].hi;
     for (int e = threadIdx.x; e < NA; e += blockDim.x) {
@@ -141,7 +222,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 
     const int64_t r_w = R0 + (int64_t)warp * 32 * kRows;  // first row of this warp
     const int64_t r0 = r_w + (int64_t)lane * kRows;       // first row of this lane
-    T dfa[kRows], dga[kRows], C[kRows], best[kRows];
+    Rows<T, kRows> R;
+    T best[kRows];
     int32_t bchunk[kRows];  // first window of the chunk holding the row's best score
     T sig_max = T(0);       // largest std of the lane's (non-constant) rows
 #pragma unroll
@@ -149,17 +231,15 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
         const int64_t r = r0 + j;
         if (r < p.nq) {
             const vec4_t<T> v = p.rs_a[r];
-            dfa[j] = v.x;
-            dga[j] = v.y;
+            R.set_terms(j, v.x, v.y);
             if (kNear) {
                 if (v.z > T(0)) sig_max = fmax(sig_max, T(1) / v.z);
                 p.near[(int64_t)grp * p.nq + r] = NearTies{-1, 0.f, -1, 0.f};
             }
         } else {
-            dfa[j] = T(0);
-            dga[j] = T(0);
+            R.set_terms(j, T(0), T(0));
         }
-        C[j] = T(0);
+        R.set(j, T(0));
         best[j] = T(-INFINITY);
         bchunk[j] = -1;
     }
@@ -208,7 +288,12 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     v.z = T(0);
                     v.w = T(-INFINITY);
                 }
-                scs[c] = v;
+                if constexpr (sizeof(T) == 4) {
+                    scs2[2 * c] = make_float4(v.x, v.x, v.y, v.y);
+                    scs2[2 * c + 1] = make_float4(v.z, v.z, v.w, v.w);
+                } else {
+                    scs[c] = v;
+                }
             }
             __syncthreads();
 
@@ -248,9 +333,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 
             // ---- left seeds at the first column of the span ----
             if (cb == 0) {
-                T aw[16];
+                T aw[16], acc[kRows];
 #pragma unroll
-                for (int j = 0; j < kRows; ++j) C[j] = T(0);
+                for (int j = 0; j < kRows; ++j) acc[j] = T(0);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) aw[t] = sa[pad<16>(sa_l + t)];
                 for (int k0 = 0; k0 < m_up16; k0 += 16) {
@@ -259,7 +344,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                         const int k = k0 + u;
                         const T bk = (k < m) ? sb[pad<8>(k)] : T(0);
 #pragma unroll
-                        for (int j = 0; j < kRows; ++j) C[j] = fma(aw[(j + u) & 15], bk, C[j]);
+                        for (int j = 0; j < kRows; ++j) acc[j] = fma(aw[(j + u) & 15], bk, acc[j]);
                         aw[u] = sa[pad<16>(sa_l + 16 + k)];
                     }
                 }
@@ -269,7 +354,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     const int64_t r = r0 + j;
                     const Split<T> ma = p.ms_a[r < p.nq ? r : p.nq - 1];
                     const T da = (ma.hi - shift_a) + ma.lo;
-                    C[j] -= T(m) * da * db0;
+                    R.set(j, acc[j] - T(m) * da * db0);
                 }
             }
             __syncwarp();
@@ -287,16 +372,21 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u) {
                     const int c = c0 + u;
-                    const vec4_t<T> cs = scs[c];
-                    if (cb > 0 || c > 0) {
-                        const T up = __shfl_up_sync(0xffffffffu, C[kRows - 1], 1);
-#pragma unroll
-                        for (int j = kRows - 1; j >= 1; --j) C[j] = fma(dfa[j], cs.y, fma(cs.x, dga[j], C[j - 1]));
-                        const T c0v = fma(dfa[0], cs.y, fma(cs.x, dga[0], up));
-                        C[0] = (lane == 0) ? stop_w[c] : c0v;
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 cxy = scs2[2 * c], czw = scs2[2 * c + 1];
+                        if (cb > 0 || c > 0) {
+                            const float up = __shfl_up_sync(0xffffffffu, R.last(), 1);
+                            R.step(make_float2(cxy.x, cxy.y), make_float2(cxy.z, cxy.w), up, lane == 0, stop_w[c]);
+                        }
+                        R.score_max(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), cm);
+                    } else {
+                        const vec4_t<T> cs = scs[c];
+                        if (cb > 0 || c > 0) {
+                            const T up = __shfl_up_sync(0xffffffffu, R.last(), 1);
+                            R.step(cs.x, cs.y, up, lane == 0, stop_w[c]);
+                        }
+                        R.score_max(cs.z, cs.w, cm);
                     }
-#pragma unroll
-                    for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fma(C[j], cs.z, cs.w));
                 }
                 const int32_t gch = (int32_t)(gblk + c0);
                 if (kNear) {
@@ -382,8 +472,8 @@ size_t plain_smem_bytes(int warps, int m)
     const int NA = rows_cta + m_up16 + 32;
     const int NB = kPlainColBlock + m_up8 + 16;
     const size_t scalars = (size_t)(NA + NA / 16 + 1) + (size_t)(NB + NB / 8 + 1) + (size_t)warps * kPlainColBlock;
-    // + 32: the column-stat array is aligned up to 32 bytes inside the block
-    return sizeof(T) * scalars + 32 + sizeof(vec4_t<T>) * kPlainColBlock;
+    // + 32: the column-term array (32 bytes per column) is aligned up to 32 bytes
+    return sizeof(T) * scalars + 32 + 32 * (size_t)kPlainColBlock;
 }
 
 template <typename T>
@@ -443,6 +533,26 @@ cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *
     return cudaGetLastError();
 }
 
+template <typename T>
+int plain_ctas_per_sm(int warps, int m)
+{
+    int n = 0;
+    const size_t smem = plain_smem_bytes<T>(warps, m);
+    constexpr int R = plain_rows_per_lane<T>();
+    cudaError_t e;
+    if constexpr (sizeof(T) == 8)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plain<T, R, false, false>, 32 * warps, smem);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plain<T, R, true, true>, 32 * warps, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+template int plain_ctas_per_sm<float>(int, int);
+template int plain_ctas_per_sm<double>(int, int);
 template size_t plain_smem_bytes<float>(int, int);
 template size_t plain_smem_bytes<double>(int, int);
 template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,

@@ -465,19 +465,32 @@ struct Geometry {
 };
 
 static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int rows_per_lane, int dtype = -1,
-                               int m = 0)
+                               int m = 0, int64_t n_segments = 1)
 {
     Geometry g;
     const int64_t rows_warp = 32 * rows_per_lane;
     g.warps = nq <= rows_warp ? 1 : (nq <= 2 * rows_warp ? 2 : 4);
     const int64_t rows_cta = rows_warp * g.warps;
     g.n_row_blocks = (int)((nq + rows_cta - 1) / rows_cta);
-    // Enough CTAs for several waves, while keeping each column group long
-    // enough (>= 4096 windows) to amortise its seeds.
-    const int64_t want = (int64_t)ctx->sm_count * 12;
-    int64_t ng = (want + g.n_row_blocks - 1) / g.n_row_blocks;
-    const int64_t max_g = std::max<int64_t>(1, W / 4096);
-    ng = std::max<int64_t>(1, std::min(ng, max_g));
+    // Column groups: each keeps >= 4096 windows (to amortise its left seeds),
+    // and the count is chosen by a cost model of whole waves: a launch of
+    // n_row_blocks * ng CTAs takes ceil(CTAs / resident CTAs) waves, each as
+    // long as one CTA's columns plus its left seeds (about m/4 columns' work
+    // per span). The smallest ng within 2 % of the cheapest wins.
+    const int64_t max_g = std::max<int64_t>(1, std::min<int64_t>(64, W / 4096));
+    const int per_sm = m > 0 ? (dtype == MP_F64 ? plain_ctas_per_sm<double>(g.warps, m)
+                                                : plain_ctas_per_sm<float>(g.warps, m))
+                             : 4;
+    const double slots = (double)ctx->sm_count * per_sm;
+    const double nseg = std::max<double>(1.0, (double)n_segments);
+    auto cost = [&](int64_t k) {
+        const double waves = std::ceil((double)g.n_row_blocks * (double)k / slots);
+        return waves * ((double)W / (double)k + (double)std::max(m, 16) / 4.0 * (nseg / (double)k + 1.0));
+    };
+    double best_c = 1e300;
+    for (int64_t k = 1; k <= max_g; ++k) best_c = std::min(best_c, cost(k));
+    int64_t ng = 1;
+    while (ng < max_g && cost(ng) > 1.02 * best_c) ++ng;
     if (ctx->force_groups > 0) {
         ng = ctx->force_groups;
     } else if (dtype >= 0 && ctx->kernel == MP_KERNEL_AUTO) {
@@ -561,7 +574,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl, dtype, m);
+    const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl, dtype, m, (int64_t)s->seg_spans.size());
     const bool tc = (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32);
     JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0,
                               join_seed_bytes(d, dtype, nq, m, seeds));
@@ -663,7 +676,8 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const mp_dict *d, const DictStats
 {
     const int64_t nq = n - m + 1;
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo = plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl, dtype, m);
+    const Geometry geo =
+        plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl, dtype, m, (int64_t)s->seg_spans.size());
     return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0,
                           join_seed_bytes(d, dtype, nq, m, seeds))
         .total;
@@ -796,7 +810,8 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
             CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
             continue;
         }
-        const Geometry geo0 = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, r.dtype, r.m);
+        const Geometry geo0 =
+            plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, r.dtype, r.m, (int64_t)s->seg_spans.size());
         Geometry geo = geo0;
         geo.warps = 4;
         geo.n_row_blocks = (int)((nq + 4 * 32 * kPlainRowsPerLane - 1) / (4 * 32 * kPlainRowsPerLane));
@@ -1600,7 +1615,8 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
     CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
     int n_groups = 0;
     if (s->n_windows > 0) {
-        Geometry geo = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane);
+        Geometry geo = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, MP_F32, m,
+                                      (int64_t)s->seg_spans.size());
         geo.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(geo.n_groups, kNoAllocMaxPartials / nq));
         // the same cut into column groups as get_grouping, staged through the scratch
         std::vector<Span> spans;
