@@ -268,12 +268,260 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
     }
 }
 
+// ---------------------------------------------------------------------------
+// Single-pass form for m <= kFinMaxM. Per query window the warp stages the
+// window once; per candidate chunk it stages the chunk's samples; the chosen
+// pair's distance is computed from the staged samples. Lane lg of half-warp
+// h sums k in [lg * kpl, (lg + 1) * kpl) for candidates 8h .. 8h + 7, with
+// kpl a multiple of 8 and both buffers zero-filled past their data, so the
+// inner loop runs in unmasked steps of 8. Shared memory is padded by one
+// value per 32 (qidx): a run of 8 starting at a multiple of 8 never crosses a
+// pad, and the lanes' start offsets fall in distinct banks for kpl = 8, 16, 32.
+// ---------------------------------------------------------------------------
+constexpr int kFinMaxM = 512;
+// warps per CTA: two double buffers per warp stay within 48 KB of static shared memory
+template <typename T> constexpr int fin_warps() { return sizeof(T) == 8 ? 2 : 4; }
+__device__ __forceinline__ int qidx(int e) { return e + (e >> 5); }
+constexpr int kFinQVals = kFinMaxM + kFinMaxM / 32 + 1;                           // 16 * kpl <= 512 values
+constexpr int kFinBVals = (kFinMaxM + kChunk) + (kFinMaxM + kChunk) / 32 + 1;  // plus kChunk
+
+__host__ __device__ constexpr int fin_kpl(int m) { return ((m + 15) / 16 + 7) / 8 * 8; }
+
+// Stage chunk g's samples b[g ..] - mean_hi(b_g) into wb (zero past the
+// dictionary), for every value the lanes of rescore_staged read.
+template <typename T>
+__device__ __forceinline__ void stage_chunk(const T *__restrict__ pb, int64_t nb, int nbv,
+                                            const Split<T> *__restrict__ ms_b, int32_t g, int lane, T *wb)
+{
+    __syncwarp();  // earlier reads of wb are done
+    const T sb = ms_b[g].hi;
+    const T *bg = pb + g;
+    const int lim = nb - g < nbv ? (int)(nb - g) : nbv;
+    for (int e = lane; e < nbv; e += 32) wb[qidx(e)] = e < lim ? bg[e] - sb : T(0);
+    __syncwarp();
+}
+
+// Re-score chunk g against the staged query window qa (= a - mean_hi(a)) and
+// the staged chunk wb (= b - mean_hi(b_g)); returns the chunk's best (score,
+// window) in every lane as rescore_chunk.
+template <typename T>
+__device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, const Split<T> *__restrict__ ms_b,
+                                               const vec4_t<T> *__restrict__ rs_b, const T *qa, T da, int32_t g,
+                                               int lane, const T *wb, T &sc_out, int32_t &g_out)
+{
+    const T sb = ms_b[g].hi;
+    const int half = lane >> 4, lg = lane & 15;
+    const int k0 = lg * kpl;
+    T acc[8], bw[8];
+    {
+        const T *b0 = wb + qidx(8 * half + k0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            acc[c] = T(0);
+            bw[c] = b0[c];
+        }
+    }
+    for (int kb = k0; kb < k0 + kpl; kb += 8) {
+        const T *qp = qa + qidx(kb);
+        const T *bp = wb + qidx(8 * half + kb + 8);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const T av = qp[u];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = fma(av, bw[(c + u) & 7], acc[c]);
+            bw[u] = bp[u];
+        }
+    }
+#pragma unroll
+    for (int s = 4; s >= 1; s >>= 1) {
+#pragma unroll
+        for (int c = 0; c < s; ++c) {
+            const bool up = (lane & s) != 0;
+            const T send = up ? acc[c] : acc[c + s];
+            const T keep = up ? acc[c + s] : acc[c];
+            acc[c] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);
+    const int cand = 8 * half + (lane & 7);
+    const int64_t gc = (int64_t)g + cand;
+    bool ok = gc < npos_b;
+    vec4_t<T> rv;
+    if (ok) {
+        rv = rs_b[gc];
+        ok = rv.w == T(0);
+    }
+    T sc = T(-INFINITY);
+    if (ok) {
+        // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
+        const Split<T> mb = ms_b[gc];
+        sc = (acc[0] - T(m) * da * ((mb.hi - sb) + mb.lo)) * rv.z;
+    }
+    int32_t gw = ok ? (int32_t)gc : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+        const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
+        if (better(s2, g2, sc, gw)) {
+            sc = s2;
+            gw = g2;
+        }
+    }
+    sc_out = sc;
+    g_out = gw;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k_finalize_rows(FinalizeParams<T> p)
+{
+    constexpr int kFinWarps = fin_warps<T>();
+    __shared__ T fr_smem[kFinWarps][kFinQVals + kFinBVals];
+    const int lane = threadIdx.x & 31;
+    T *const qa = fr_smem[threadIdx.x >> 5];
+    T *const wb = qa + kFinQVals;
+    const int64_t warp_global = (int64_t)blockIdx.x * kFinWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kFinWarps;
+    const int m = p.m;
+    const int kpl = fin_kpl(m);
+    const int nbv = 16 * kpl + kChunk;
+    const double sqrt_m = sqrt((double)m);
+    if (p.err != nullptr && *p.err != 0) {
+        // a bounded wait of a tensor-core kernel ran out: the partials are incomplete
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nq; i += (int64_t)gridDim.x * blockDim.x) {
+            p.out_dist[i] = NAN;
+            p.out_idx[i] = -1;
+        }
+        return;
+    }
+    for (int64_t i = warp_global; i < p.nq; i += nwarps) {
+        // 1. reduce the column groups: largest q, then lowest chunk start
+        T q = T(-INFINITY);
+        int32_t g = -1;
+        for (int k = lane; k < p.n_groups; k += 32) {
+            const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+            if (better(v.q, v.g, q, g)) {
+                q = v.q;
+                g = v.g;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T q2 = __shfl_xor_sync(0xffffffffu, q, o);
+            const int32_t g2 = __shfl_xor_sync(0xffffffffu, g, o);
+            if (better(q2, g2, q, g)) {
+                q = q2;
+                g = g2;
+            }
+        }
+        double d = INFINITY;
+        int64_t gi = -1;
+        if (p.g_first >= 0) {
+            if (p.cflag_a[i]) {
+                // 3. a constant query window is 0 from a constant window, sqrt(m) from the rest
+                if (p.g_const >= 0) {
+                    d = 0.0;
+                    gi = p.g_const;
+                } else {
+                    d = sqrt_m;
+                    gi = p.g_first;
+                }
+            } else {
+                if (g >= 0) {
+                    // 2. stage the query window, re-score the winning chunk and the near-tied ones
+                    const Split<T> ma = p.ms_a[i];
+                    const T *ai = p.a + i;
+                    for (int e = lane; e < 16 * kpl; e += 32) qa[qidx(e)] = e < m ? ai[e] - ma.hi : T(0);
+                    stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, g, lane, wb);
+                    T sc;
+                    int32_t gw;
+                    rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, g, lane, wb, sc, gw);
+                    int32_t staged = g;  // the chunk whose samples wb holds
+                    int32_t win = g;     // the chunk of the best window so far
+                    if (p.near != nullptr) {
+                        const T lim = q - T(kNearTieRho) * T(m) / p.rs_a[i].z;  // the row is not constant
+                        for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
+                            const int k = k0 + lane;
+                            int32_t c0 = -1, c1 = -1, c2 = -1;
+                            if (k < p.n_groups) {
+                                const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+                                if (v.g >= 0 && v.g != g && v.q >= lim) c0 = v.g;
+                                const NearTies nt = p.near[(int64_t)k * p.nq + i];
+                                if (nt.g0 >= 0 && nt.g0 != g && T(nt.q0) >= lim) c1 = nt.g0;
+                                if (nt.g1 >= 0 && nt.g1 != g && T(nt.q1) >= lim) c2 = nt.g1;
+                            }
+                            unsigned pend = __ballot_sync(0xffffffffu, c0 >= 0 || c1 >= 0 || c2 >= 0);
+                            while (pend) {
+                                const int src = __ffs(pend) - 1;
+                                pend &= pend - 1;
+                                const int32_t s0 = __shfl_sync(0xffffffffu, c0, src);
+                                const int32_t s1 = __shfl_sync(0xffffffffu, c1, src);
+                                const int32_t s2c = __shfl_sync(0xffffffffu, c2, src);
+#pragma unroll 1
+                                for (int u = 0; u < 3; ++u) {
+                                    const int32_t cu = u == 0 ? s0 : (u == 1 ? s1 : s2c);
+                                    if (cu < 0) continue;
+                                    T s2;
+                                    int32_t g2;
+                                    stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, cu, lane, wb);
+                                    rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2,
+                                                      g2);
+                                    staged = cu;
+                                    if (better(s2, g2, sc, gw)) {
+                                        sc = s2;
+                                        gw = g2;
+                                        win = cu;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    if (gw >= 0) {
+                        // 4. the chosen pair's distance from its definition, on the staged samples
+                        if (staged != win) stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, win, lane, wb);
+                        const Split<T> mb = p.ms_b[gw];
+                        const T db = (mb.hi - p.ms_b[win].hi) + mb.lo;  // wb holds b - mean_hi(win)
+                        const T is_a = p.rs_a[i].z, is_b = p.rs_b[gw].z;
+                        const int o = gw - win;
+                        T acc = T(0);
+                        for (int k = lane; k < m; k += 32) {
+                            const T za = (qa[qidx(k)] - ma.lo) * is_a;
+                            const T zb = (wb[qidx(o + k)] - db) * is_b;
+                            const T dd = za - zb;
+                            acc = fma(dd, dd, acc);
+                        }
+#pragma unroll
+                        for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+                        d = (double)sqrt(acc);
+                        gi = gw;
+                    }
+                    __syncwarp();  // the next row rewrites qa and wb
+                }
+                if (p.g_const >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && p.g_const < gi))) {
+                    d = sqrt_m;
+                    gi = p.g_const;
+                }
+            }
+        }
+        if (lane == 0) {
+            p.out_dist[i] = d;
+            p.out_idx[i] = gi;
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st)
 {
     if (p.nq <= 0) return cudaSuccess;
+    if (p.m <= kFinMaxM) {
+        constexpr int W = fin_warps<T>();
+        int64_t grid = (p.nq + W - 1) / W;  // one query window per warp and pass
+        if (grid > 152 * 32) grid = 152 * 32;
+        k_finalize_rows<T><<<(unsigned)grid, 32 * W, 0, st>>>(p);
+        return cudaGetLastError();
+    }
     int64_t grid = (p.nq + 7) / 8;  // 8 warps (rows) per CTA
     if (grid > 152 * 64) grid = 152 * 64;
     k_finalize<T><<<(unsigned)grid, 256, 0, st>>>(p);
