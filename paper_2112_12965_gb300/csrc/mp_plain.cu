@@ -109,8 +109,10 @@ template <int P> __device__ __forceinline__ int pad(int e) { return e + e / P; }
 // that one packed FMA (fma.rn.f32x2: each half rounded once, exactly as
 // fmaf) advances two rows: moving one column right shifts every row down by
 // one, which maps pair k-1 onto pair k, and only pair 0 takes new inputs
-// (the row above the lane, and row kRows/2 - 1).
-template <typename T, int kRows> struct Rows {
+// (the row above the lane, and row kRows/2 - 1). The packed form pays off with
+// 16 warps per SM (k_plain); the batched serving kernel, at 8 warps per SM,
+// cannot hide the packed FMA's longer pipe occupancy and stays scalar.
+template <typename T, int kRows, bool kPacked> struct Rows {
     T C[kRows], df[kRows], dg[kRows];
     __device__ __forceinline__ void set_terms(int j, T f, T g)
     {
@@ -135,7 +137,7 @@ template <typename T, int kRows> struct Rows {
     }
 };
 
-template <int kRows> struct Rows<float, kRows> {
+template <int kRows> struct Rows<float, kRows, true> {
     static constexpr int H = kRows / 2;
     float2 C[H], df[H], dg[H];
     __device__ __forceinline__ void set_terms(int j, float f, float g)
@@ -178,9 +180,10 @@ template <int kRows> struct Rows<float, kRows> {
 };
 
 // kSeeds: the top seeds come from p.seed_top (the tensor cores) instead of
-// direct dot products; kNear: near ties are recorded in p.near. Both are
-// compile-time so that each form carries only its own code.
-template <typename T, int kRows, bool kSeeds, bool kNear>
+// direct dot products; kNear: near ties are recorded in p.near; kPacked
+// (FP32 only): packed FMA on row pairs. All are compile-time so that each
+// form carries only its own code.
+template <typename T, int kRows, bool kSeeds, bool kNear, bool kPacked>
 __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, int grp, unsigned char *smem_raw)
 {
     constexpr int CB = kPlainColBlock;
@@ -222,7 +225,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 
     const int64_t r_w = R0 + (int64_t)warp * 32 * kRows;  // first row of this warp
     const int64_t r0 = r_w + (int64_t)lane * kRows;       // first row of this lane
-    Rows<T, kRows> R;
+    constexpr bool kPack = kPacked && sizeof(T) == 4;
+    Rows<T, kRows, kPack> R;
     T best[kRows];
     int32_t bchunk[kRows];  // first window of the chunk holding the row's best score
     T sig_max = T(0);       // largest std of the lane's (non-constant) rows
@@ -288,7 +292,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     v.z = T(0);
                     v.w = T(-INFINITY);
                 }
-                if constexpr (sizeof(T) == 4) {
+                if constexpr (kPack) {
                     scs2[2 * c] = make_float4(v.x, v.x, v.y, v.y);
                     scs2[2 * c + 1] = make_float4(v.z, v.z, v.w, v.w);
                 } else {
@@ -372,7 +376,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u) {
                     const int c = c0 + u;
-                    if constexpr (sizeof(T) == 4) {
+                    if constexpr (kPack) {
                         const float4 cxy = scs2[2 * c], czw = scs2[2 * c + 1];
                         if (cb > 0 || c > 0) {
                             const float up = __shfl_up_sync(0xffffffffu, R.last(), 1);
@@ -437,7 +441,7 @@ template <typename T, int kRows, bool kSeeds, bool kNear>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_plain(PlainParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    plain_item<T, kRows, kSeeds, kNear>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
+    plain_item<T, kRows, kSeeds, kNear, true>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
 }
 
 // Persistent batched form for serving: the CTAs walk a list of work items that
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(128, 2) k_plain_batched(const PlainParams<T> *
         if (it >= n_items) break;
         const BatchItem bi = items[it];
         const PlainParams<T> p = reqs[bi.req];
-        plain_item<T, kRows, false, kNear>(p, bi.rb, bi.grp, smem_raw);  // seeds computed here
+        plain_item<T, kRows, false, kNear, false>(p, bi.rb, bi.grp, smem_raw);  // seeds computed here, scalar FMA
     }
 }
 

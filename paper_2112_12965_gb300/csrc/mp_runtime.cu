@@ -32,6 +32,7 @@
 #include <set>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -464,6 +465,21 @@ struct Geometry {
     int warps, n_row_blocks, n_groups;
 };
 
+// Resident CTAs per SM of the plain kernel, from the occupancy API, cached per
+// (dtype, warps, m): the serving scheduler sizes every request with it.
+static int plain_ctas_cached(bool f64, int warps, int m)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<bool, int, int>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(f64, warps, m);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const int n = f64 ? plain_ctas_per_sm<double>(warps, m) : plain_ctas_per_sm<float>(warps, m);
+    cache[key] = n;
+    return n;
+}
+
 static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int rows_per_lane, int dtype = -1,
                                int m = 0, int64_t n_segments = 1)
 {
@@ -478,9 +494,7 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
     // long as one CTA's columns plus its left seeds (about m/4 columns' work
     // per span). The smallest ng within 2 % of the cheapest wins.
     const int64_t max_g = std::max<int64_t>(1, std::min<int64_t>(64, W / 4096));
-    const int per_sm = m > 0 ? (dtype == MP_F64 ? plain_ctas_per_sm<double>(g.warps, m)
-                                                : plain_ctas_per_sm<float>(g.warps, m))
-                             : 4;
+    const int per_sm = m > 0 ? plain_ctas_cached(dtype == MP_F64, g.warps, m) : 4;
     const double slots = (double)ctx->sm_count * per_sm;
     const double nseg = std::max<double>(1.0, (double)n_segments);
     auto cost = [&](int64_t k) {
