@@ -78,6 +78,7 @@ extern "C" {
 
 typedef struct mp_ctx mp_ctx;
 typedef struct mp_dict mp_dict;
+typedef struct mp_stream mp_stream;
 
 /* Context configuration. Fill with mp_config_default() and override fields. */
 typedef struct mp_config {
@@ -135,6 +136,45 @@ int mp_dict_windows(const mp_dict *dict, int32_t m, int64_t *n_windows);
  */
 int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
                double *out_dist, int64_t *out_idx);
+
+/*
+ * The join of mp_ab_join reported as a bounded similarity (Sec. 2.1 names the
+ * Pearson correlation coefficient as the alternative to the distance; with it
+ * the profile keeps the largest value and Guarantee 1 reads P_hat <= P).
+ *   out_corr  host, n - m + 1 doubles: rho = 1 - d^2 / (2m) for the nearest
+ *             window, which is Pearson's r of the two windows when neither is
+ *             constant; under the zero-vector convention for constant windows
+ *             it is 0.5 between a constant and a non-constant window and 1
+ *             between two constant ones. -inf where the dictionary has no
+ *             window of length m.
+ *   out_idx   host, n - m + 1 int64: the same window index as mp_ab_join's
+ *             (the largest rho is the smallest d).
+ */
+int mp_ab_join_corr(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+                    double *out_corr, int64_t *out_idx);
+
+/*
+ * Streaming join (Sec. 1: arriving data compared with a resident "normal"
+ * dictionary, flagging windows without a close neighbour). A stream joins
+ * windows of length m as samples arrive; each window is joined once, when
+ * its last sample arrives.
+ *   mp_stream_open    the stream of one dictionary, dtype (the dictionary's)
+ *                     and m (>= 2); the dictionary must outlive the stream.
+ *   mp_stream_append  appends n_new host samples and joins the windows that
+ *                     end in them: *n_out of them (n_new once m - 1 samples
+ *                     have been seen before; fewer at the start), written to
+ *                     out_dist / out_idx (host, room for n_new values each) as
+ *                     mp_ab_join writes them. *first_window (may be NULL) is
+ *                     the stream index of out_dist[0]: windows are numbered
+ *                     from the stream's first sample. The samples are copied;
+ *                     the call is synchronous. Errors as mp_ab_join; on error
+ *                     nothing of the append is kept.
+ *   mp_stream_close   frees the stream (the last m - 1 samples it keeps).
+ */
+int mp_stream_open(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int32_t m, mp_stream **out);
+int mp_stream_append(mp_stream *stream, const void *samples, int64_t n_new, double *out_dist, int64_t *out_idx,
+                     int64_t *n_out, int64_t *first_window);
+int mp_stream_close(mp_stream *stream);
 
 /*
  * The same join on device buffers, enqueued on `stream` (a cudaStream_t; NULL

@@ -116,3 +116,22 @@ def ab_join(query, dict_samples, offsets, m: int, rows=None, nthreads: int = 0, 
     if rc != 0:
         raise ValueError(f"mpo_ab_join failed ({rc})")
     return dist, idx, dist2
+
+
+def ab_join_corr(query, dict_samples, offsets, m: int, rows=None, nthreads: int = 0, lib=None):
+    """The join reported as a bounded similarity (Sec. 2.1 names the Pearson
+    correlation coefficient as the alternative to the distance).
+
+    For each row the largest rho over the dictionary windows, with
+    rho = 1 - d^2 / (2m): for z-normalised windows of unit population
+    variance, ||z_a - z_b||^2 = 2m - 2 sum_k z_a z_b = 2m (1 - r), so rho is
+    Pearson's r when neither window is constant. Under the zero-vector
+    convention for constant windows it is 0.5 between a constant and a
+    non-constant window and 1 between two constant ones. The largest rho is
+    the smallest d, so the index is the join's. Returns ``(rho, idx)``;
+    rows without a dictionary window get -inf / -1.
+    """
+    d, i, _ = ab_join(query, dict_samples, offsets, m, rows=rows, nthreads=nthreads, lib=lib)
+    rho = np.where(i >= 0, 1.0 - d * d / (2.0 * m), -np.inf)
+    return rho, i
+

@@ -94,6 +94,10 @@ def _load():
         "mp_dict_free": ([P, P], ctypes.c_int),
         "mp_dict_windows": ([P, i32, ctypes.POINTER(i64)], ctypes.c_int),
         "mp_ab_join": ([P, P, P, i32, i64, i32, P, P], ctypes.c_int),
+        "mp_ab_join_corr": ([P, P, P, i32, i64, i32, P, P], ctypes.c_int),
+        "mp_stream_open": ([P, P, i32, i32, ctypes.POINTER(P)], ctypes.c_int),
+        "mp_stream_append": ([P, P, i64, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "mp_stream_close": ([P], ctypes.c_int),
         "mp_ab_join_device": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
         "mp_ab_join_noalloc": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
         "mp_window_stats": ([P, P, i32, i64, i32, P, P, P, P], ctypes.c_int),
@@ -194,6 +198,41 @@ def mp_ab_join(ctx, d, query: np.ndarray, m: int) -> Tuple[np.ndarray, np.ndarra
     idx = np.empty(nq, dtype=np.int64)
     _check(lib.mp_ab_join(ctx, d, _ptr(q), _dtype_of(q), len(q), m, _ptr(dist), _ptr(idx)))
     return dist, idx
+
+
+def mp_ab_join_corr(ctx, d, query: np.ndarray, m: int) -> Tuple[np.ndarray, np.ndarray]:
+    """The join reported as correlation rho = 1 - d^2/(2m) (the largest per row); returns (rho, index)."""
+    q = np.ascontiguousarray(query)
+    nq = max(len(q) - m + 1, 0)
+    corr = np.empty(nq, dtype=np.float64)
+    idx = np.empty(nq, dtype=np.int64)
+    _check(lib.mp_ab_join_corr(ctx, d, _ptr(q), _dtype_of(q), len(q), m, _ptr(corr), _ptr(idx)))
+    return corr, idx
+
+
+def mp_stream_open(ctx, d, dtype: int, m: int):
+    """A streaming join of windows of length m against dictionary d; returns the stream handle."""
+    h = ctypes.c_void_p()
+    _check(lib.mp_stream_open(ctx, d, dtype, m, ctypes.byref(h)))
+    return h
+
+
+def mp_stream_append(stream, samples: np.ndarray) -> Tuple[np.ndarray, np.ndarray, int]:
+    """Append samples; returns (distance, index, first window) of the windows that end in them."""
+    x = np.ascontiguousarray(samples)
+    n = len(x)
+    dist = np.empty(max(n, 1), dtype=np.float64)
+    idx = np.empty(max(n, 1), dtype=np.int64)
+    n_out = ctypes.c_int64()
+    first = ctypes.c_int64()
+    _check(lib.mp_stream_append(stream, _ptr(x) if n else None, n, _ptr(dist), _ptr(idx), ctypes.byref(n_out),
+                                ctypes.byref(first)))
+    k = n_out.value
+    return dist[:k].copy(), idx[:k].copy(), first.value
+
+
+def mp_stream_close(stream) -> None:
+    _check(lib.mp_stream_close(stream))
 
 
 def mp_ab_join_device(ctx, d, d_query: int, dtype: int, n: int, m: int, d_dist: int, d_idx: int,

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
             }
         }
         if (lane == 0) {
-            p.out_dist[i] = d;
+            p.out_dist[i] = p.out_corr ? (gi >= 0 ? 1.0 - d * d / (2.0 * m) : -INFINITY) : d;
             p.out_idx[i] = gi;
         }
     }
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
             }
         }
         if (lane == 0) {
-            p.out_dist[i] = d;
+            p.out_dist[i] = p.out_corr ? (gi >= 0 ? 1.0 - d * d / (2.0 * m) : -INFINITY) : d;
             p.out_idx[i] = gi;
         }
     }

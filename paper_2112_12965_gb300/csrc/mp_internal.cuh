@@ -98,9 +98,12 @@ struct PlainLaunch {
     int32_t n_row_blocks;
     int32_t n_groups;      // column groups
     int32_t warps;         // warps per CTA (rows per CTA = warps * 32 * kPlainRowsPerLane)
+    int64_t ld_part = 0;   // row stride of the partial results and near-tie records (0: nq)
 };
 
-// Plain diagonal-recurrence join (kernel K2). Writes part[group * nq + row].
+// Plain diagonal-recurrence join (kernel K2). Writes part[group * ld_part + row]
+// (ld_part = L.ld_part, or nq): a join may run in row chunks, each launch
+// given its rows' query, statistics and partial results by pointer offsets.
 // spans[group_start[k] .. group_start[k+1]) are the spans of column group k.
 // seed_top (may be null): the centred covariances of each warp's first query
 // window, row r / (32 * rows per lane) at column g, row stride seed_ld (as
@@ -136,6 +139,7 @@ struct PlainRequest {
     const float *seed_top;  // always null: batched work computes its own seeds
     int64_t seed_ld;
     NearTies *near;         // [n_groups][nq] near-tie records (required)
+    int64_t ld_part;        // nq
 };
 struct BatchItem {
     int32_t req;  // index into the request array
@@ -172,6 +176,7 @@ template <typename T> struct FinalizeParams {
     int64_t *out_idx;
     const int32_t *err;       // may be null; if *err != 0 a tensor-core wait ran out: NaN / -1 everywhere
     const NearTies *near;     // may be null; [n_groups][nq] near-tie records of the plain kernel
+    int32_t out_corr;         // 1: write rho = 1 - d^2 / (2m) (Pearson's r for non-constant windows), -inf if none
 };
 template <typename T> cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st);
 

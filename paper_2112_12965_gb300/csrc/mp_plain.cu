@@ -58,6 +58,7 @@ template <typename T> struct PlainParams {
     const T *seed_top;  // top seeds from the tensor cores, or null
     int64_t seed_ld;
     NearTies *near;     // near-tie records, or null
+    int64_t ld_part;    // row stride of part and near (>= nq)
 };
 
 // Add a near-tie record (chunk g, approximate score q) to a slot; with both
@@ -238,7 +239,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             R.set_terms(j, v.x, v.y);
             if (kNear) {
                 if (v.z > T(0)) sig_max = fmax(sig_max, T(1) / v.z);
-                p.near[(int64_t)grp * p.nq + r] = NearTies{-1, 0.f, -1, 0.f};
+                p.near[(int64_t)grp * p.ld_part + r] = NearTies{-1, 0.f, -1, 0.f};
             }
         } else {
             R.set_terms(j, T(0), T(0));
@@ -406,7 +407,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                         for (int j = 0; j < kRows; ++j) {
                             if (fabs(cm[j] - best[j]) <= tq && r0 + j < p.nq) {
                                 const bool upd = cm[j] > best[j];
-                                near_record(p.near + (int64_t)grp * p.nq + r0 + j, upd ? bchunk[j] : gch,
+                                near_record(p.near + (int64_t)grp * p.ld_part + r0 + j, upd ? bchunk[j] : gch,
                                             (float)(upd ? best[j] : cm[j]));
                             }
                         }
@@ -429,7 +430,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             Partial<T> v;
             v.q = best[j];
             v.g = bchunk[j];
-            p.part[(int64_t)grp * p.nq + r] = v;
+            p.part[(int64_t)grp * p.ld_part + r] = v;
         }
     }
 }
@@ -504,6 +505,7 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     p.seed_top = seed_top;
     p.seed_ld = seed_ld;
     p.near = near;
+    p.ld_part = L.ld_part > 0 ? L.ld_part : L.nq;
     const size_t smem = plain_smem_bytes<T>(L.warps, L.m);
     constexpr int R = plain_rows_per_lane<T>();
     const int64_t grid = (int64_t)L.n_row_blocks * L.n_groups;

@@ -457,6 +457,7 @@ static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const P
     f.out_idx = idx;
     f.err = nullptr;
     f.near = nullptr;
+    f.out_corr = 0;
     return f;
 }
 
@@ -517,20 +518,42 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
 
 // Top seeds of the plain FP32 kernel computed on the tensor cores: one row
 // per warp of query windows (every 32 * kPlainRowsPerLane-th window), one
-// column per dictionary window position.
+// column per dictionary window position. A join whose seed matrix would
+// exceed kSeedCapBytes runs in row chunks (multiples of 2048 query windows),
+// each with its own seeds in the same buffer.
+constexpr size_t kSeedCapBytes = (size_t)2 << 30;
+
 struct SeedGeo {
-    int64_t n_srows, ld;
-    size_t bytes;
+    int64_t n_srows;     // seed rows of one chunk
+    int64_t ld;          // row stride (dictionary positions rounded up to 4)
+    int64_t chunk_rows;  // query windows per chunk (all of them without chunking)
+    size_t bytes;        // seed bytes of one chunk
 };
 
 static SeedGeo seed_geometry(int64_t nq, int64_t npos_b)
 {
     SeedGeo g;
     const int64_t stride = 32 * kPlainRowsPerLane;
-    g.n_srows = (nq + stride - 1) / stride;
     g.ld = (std::max<int64_t>(1, npos_b) + 3) & ~(int64_t)3;
-    g.bytes = (size_t)g.n_srows * (size_t)g.ld * sizeof(float);
+    const size_t row_bytes = (size_t)g.ld * sizeof(float);
+    const int64_t full = (nq + stride - 1) / stride;
+    if ((size_t)full * row_bytes <= kSeedCapBytes) {
+        g.n_srows = full;
+        g.chunk_rows = nq;
+    } else {
+        // whole CTAs of 4 warps (4 seed rows) per chunk
+        g.n_srows = std::max<int64_t>(4, (int64_t)(kSeedCapBytes / row_bytes) & ~(int64_t)3);
+        g.chunk_rows = g.n_srows * stride;
+    }
+    g.bytes = (size_t)g.n_srows * row_bytes;
     return g;
+}
+
+// Query windows per launch of the plain join (chunks only for FP32 with seeds).
+static int64_t plain_chunk_rows(const mp_dict *d, int32_t dtype, int64_t nq, int32_t m, bool seeds)
+{
+    if (!seeds || dtype != MP_F32) return nq;
+    return seed_geometry(nq, d->nb - m + 1).chunk_rows;
 }
 
 // Workspace layout of one join.
@@ -583,12 +606,13 @@ static size_t join_seed_bytes(const mp_dict *d, int32_t dtype, int64_t nq, int32
 // kernels set it when a bounded wait runs out.
 static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, int32_t dtype, int64_t n, int32_t m,
                        double *d_dist, int64_t *d_idx, cudaStream_t st, unsigned char *base, int kernel,
-                       bool seeds = true)
+                       bool seeds = true, bool corr = false)
 {
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo = plain_geometry(ctx, nq, s->n_windows, rpl, dtype, m, (int64_t)s->seg_spans.size());
+    const int64_t crow = plain_chunk_rows(d, dtype, nq, m, seeds);  // query windows per plain launch
+    const Geometry geo = plain_geometry(ctx, crow, s->n_windows, rpl, dtype, m, (int64_t)s->seg_spans.size());
     const bool tc = (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32);
     JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0,
                               join_seed_bytes(d, dtype, nq, m, seeds));
@@ -623,8 +647,10 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
-            CUDA_TRY(launch_finalize<double>(
-                fin_params<double>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx), st));
+            FinalizeParams<double> f =
+                fin_params<double>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
+            f.out_corr = corr ? 1 : 0;
+            CUDA_TRY(launch_finalize<double>(f, st));
         }
     } else {
         const float *a = (const float *)dq;
@@ -649,6 +675,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
                 PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
                 FinalizeParams<float> f = fin_params<float>(nq, m, ng, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
                 f.err = err;
+                f.out_corr = corr ? 1 : 0;
                 CUDA_TRY(launch_finalize<float>(f, st));
             }
             return MP_OK;
@@ -656,22 +683,28 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         Partial<float> *part = (Partial<float> *)(base + w.off_part);
         NearTies *near = (NearTies *)(base + w.off_near);
         float *seed_top = nullptr;
-        int64_t seed_ld = 0;
-        if (seeds) {
-            PhaseTimer t(ctx, MP_PHASE_SEEDS, st);
-            const SeedGeo sg = seed_geometry(nq, d->nb - m + 1);
-            seed_top = (float *)(base + w.off_seed);
-            seed_ld = sg.ld;
-            int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb, s->seg_spans.data(),
-                              (int32_t)s->seg_spans.size(), s->ms, a, n, m, ms_a, 32 * kPlainRowsPerLane, seed_top,
-                              seed_ld, err, st, fail);
-            if (rc) return rc;
-        }
-        {
+        const SeedGeo sg = seed_geometry(nq, d->nb - m + 1);
+        if (seeds) seed_top = (float *)(base + w.off_seed);
+        // row chunks (one chunk unless the seed matrix would exceed its cap)
+        for (int64_t r0 = 0; r0 < nq; r0 += crow) {
+            const int64_t rows = std::min<int64_t>(crow, nq - r0);
+            if (seeds) {
+                PhaseTimer t(ctx, MP_PHASE_SEEDS, st);
+                int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb, s->seg_spans.data(),
+                                  (int32_t)s->seg_spans.size(), s->ms, a + r0, rows + m - 1, m, ms_a + r0,
+                                  32 * kPlainRowsPerLane, seed_top, sg.ld, err, st, fail);
+                if (rc) return rc;
+            }
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
-            CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb,
-                                         (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
-                                         gr->group_start, part, seed_top, seed_ld, near, st));
+            PlainLaunch Lc = L;
+            const int64_t rows_cta = (int64_t)geo.warps * 32 * kPlainRowsPerLane;
+            Lc.nq = rows;
+            Lc.n_row_blocks = (int32_t)((rows + rows_cta - 1) / rows_cta);
+            Lc.ld_part = nq;
+            CUDA_TRY(launch_plain<float>(Lc, a + r0, rows + m - 1, rs_a + r0, ms_a + r0, (const float *)d->d_samples,
+                                         d->nb, (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
+                                         gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0,
+                                         near + r0, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
@@ -679,6 +712,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
                 fin_params<float>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
             f.err = seeds ? err : nullptr;
             f.near = near;
+            f.out_corr = corr ? 1 : 0;
             CUDA_TRY(launch_finalize<float>(f, st));
         }
     }
@@ -690,8 +724,9 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const mp_dict *d, const DictStats
 {
     const int64_t nq = n - m + 1;
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo =
-        plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), rpl, dtype, m, (int64_t)s->seg_spans.size());
+    const Geometry geo = plain_geometry(ctx, plain_chunk_rows(d, dtype, nq, m, seeds),
+                                        std::max<int64_t>(1, s->n_windows), rpl, dtype, m,
+                                        (int64_t)s->seg_spans.size());
     return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0,
                           join_seed_bytes(d, dtype, nq, m, seeds))
         .total;
@@ -858,6 +893,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         pr.group_start = gr->group_start;
         pr.part = part;
         pr.near = near;
+        pr.ld_part = nq;
         const int ridx = (int)preqs.size();
         preqs.push_back(pr);
         for (int64_t rb = 0; rb < geo.n_row_blocks; ++rb)
@@ -1184,8 +1220,10 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
     return MP_OK;
 }
 
-int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
-               double *out_dist, int64_t *out_idx)
+// The synchronous join with host buffers; corr: report rho = 1 - d^2 / (2m)
+// (-inf where the dictionary has no window) instead of d.
+static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+                        double *out_dist, int64_t *out_idx, bool corr)
 {
     g_err.clear();
     int rc = check_join_args(ctx, dict, query, dtype, n, m);
@@ -1201,7 +1239,7 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) {
         for (int64_t i = 0; i < nq; ++i) {
-            out_dist[i] = INFINITY;
+            out_dist[i] = corr ? -INFINITY : INFINITY;
             out_idx[i] = -1;
         }
         return MP_OK;
@@ -1218,7 +1256,7 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     cudaStream_t st = ctx->stream;
     CUDA_TRY(cudaMemcpyAsync(dq, query, (size_t)n * dtype_size(dtype), cudaMemcpyHostToDevice, st));
     rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes,
-                     resolve_kernel(ctx, dtype, m, s, nq));
+                     resolve_kernel(ctx, dtype, m, s, nq), true, corr);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
@@ -1228,6 +1266,18 @@ int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtyp
     CUDA_TRY(cudaStreamSynchronize(st));
     if (err) return fail(MP_E_TIMEOUT, "a tensor-core wait timed out on the device; results are invalid");
     return MP_OK;
+}
+
+int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+               double *out_dist, int64_t *out_idx)
+{
+    return ab_join_host(ctx, dict, query, dtype, n, m, out_dist, out_idx, false);
+}
+
+int mp_ab_join_corr(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
+                    double *out_corr, int64_t *out_idx)
+{
+    return ab_join_host(ctx, dict, query, dtype, n, m, out_corr, out_idx, true);
 }
 
 int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int32_t m, double *d_mean,
@@ -1370,6 +1420,67 @@ int mp_drain(mp_ctx *ctx, double timeout_s)
 // ---------------------------------------------------------------------------
 // e_max and discords (Sec. 2.1 and Sec. 3.3, on top of the join)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Streaming join (Sec. 1's online use: arriving data joined against a resident
+// normal dictionary). The stream keeps the last m - 1 samples; each append
+// joins [kept | new] on the device and returns the windows that end in the new
+// samples.
+// ---------------------------------------------------------------------------
+struct mp_stream {
+    mp_ctx *ctx;
+    const mp_dict *dict;
+    int32_t dtype;
+    int32_t m;
+    std::vector<unsigned char> tail;  // the last min(m - 1, seen) samples
+    int64_t n_seen = 0;               // samples appended so far
+};
+
+extern "C" int mp_stream_open(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int32_t m, mp_stream **out)
+{
+    g_err.clear();
+    if (!ctx || !dict || !out || m < 2 || (dtype != MP_F32 && dtype != MP_F64)) return fail(MP_E_ARG, "bad argument");
+    if (dtype != dict->dtype) return fail(MP_E_ARG, "stream dtype must match the dictionary's");
+    mp_stream *st = new mp_stream();
+    st->ctx = ctx;
+    st->dict = dict;
+    st->dtype = dtype;
+    st->m = m;
+    *out = st;
+    return MP_OK;
+}
+
+extern "C" int mp_stream_append(mp_stream *st, const void *samples, int64_t n_new, double *out_dist, int64_t *out_idx,
+                                int64_t *n_out, int64_t *first_window)
+{
+    g_err.clear();
+    if (!st || !n_out || n_new < 0 || (n_new > 0 && (!samples || !out_dist || !out_idx)))
+        return fail(MP_E_ARG, "bad argument");
+    const size_t es = dtype_size(st->dtype);
+    const int64_t kept = (int64_t)(st->tail.size() / es);
+    const int64_t n = kept + n_new;
+    *n_out = 0;
+    if (first_window) *first_window = std::max<int64_t>(0, st->n_seen - st->m + 1);
+    std::vector<unsigned char> buf(st->tail);
+    buf.insert(buf.end(), (const unsigned char *)samples, (const unsigned char *)samples + (size_t)n_new * es);
+    if (n >= st->m) {
+        int rc = ab_join_host(st->ctx, st->dict, buf.data(), st->dtype, n, st->m, out_dist, out_idx, false);
+        if (rc) return rc;
+        *n_out = n - st->m + 1;
+    }
+    // keep the last m - 1 samples
+    const int64_t keep = std::min<int64_t>(n, st->m - 1);
+    st->tail.assign(buf.end() - (ptrdiff_t)(keep * (int64_t)es), buf.end());
+    st->n_seen += n_new;
+    return MP_OK;
+}
+
+extern "C" int mp_stream_close(mp_stream *st)
+{
+    g_err.clear();
+    delete st;
+    return MP_OK;
+}
+
 extern "C" int mp_emax(mp_ctx *ctx, const mp_dict *dict, const void *t_b, int32_t dtype, int64_t n_b, int32_t m,
                        double *e_max, int64_t *argmax)
 {

@@ -221,6 +221,36 @@ def pin_constant_rows(lib):
     assert np.allclose(d[:3], math.sqrt(m), atol=1e-12) and np.all(i[:3] == 0)
 
 
+def pin_correlation_output(lib, seeds=range(4)):
+    """The correlation form against numpy.corrcoef maxima, and the constant-window reading."""
+    for seed in seeds:
+        rng = np.random.default_rng(2000 + seed)
+        m = int(rng.choice([4, 6, 8]))
+        na = int(rng.integers(m + 4, 40))
+        lens = rng.integers(m, 18, int(rng.integers(1, 4)))
+        offs = np.concatenate(([0], np.cumsum(lens))).astype(np.int64)
+        q = rng.standard_normal(na)
+        b = rng.standard_normal(int(offs[-1]))
+        rho, i = oracle.ab_join_corr(q, b, offs, m, lib=lib)
+        gs = _valid_windows(offs, m)
+        R = np.array([[np.corrcoef(q[r : r + m], b[g : g + m])[0, 1] for g in gs] for r in range(na - m + 1)])
+        np.testing.assert_allclose(rho, R.max(axis=1), rtol=0, atol=1e-9)
+        top2 = np.sort(R, axis=1)[:, -2:] if len(gs) > 1 else None
+        uniq = (top2[:, 1] - top2[:, 0]) > 1e-9 if top2 is not None else np.ones(len(rho), bool)
+        assert np.array_equal(i[uniq], gs[np.argmax(R, axis=1)][uniq])
+    # constant windows: 0.5 against non-constant windows, 1 against a constant one
+    m = 6
+    b = np.concatenate([np.sin(np.arange(30.0)), np.full(10, 2.0)])
+    q = np.concatenate([np.full(8, -1.0), np.cos(np.arange(20.0))])
+    rho, i = oracle.ab_join_corr(q, b[:30], np.array([0, 30]), m, lib=lib)
+    assert np.allclose(rho[:3], 0.5, atol=1e-12) and np.all(i[:3] == 0)
+    rho, i = oracle.ab_join_corr(q, b, np.array([0, 30, 40]), m, lib=lib)
+    assert np.all(rho[:3] == 1.0) and np.all(i[:3] == 30)
+    # no window at all: -inf / -1
+    rho, i = oracle.ab_join_corr(q, np.arange(9.0), np.array([0, 3, 6, 9]), m, lib=lib)
+    assert np.all(np.isneginf(rho)) and np.all(i == -1)
+
+
 ALL_PINS = (
     pin_brute_force,
     pin_closed_forms,
@@ -230,4 +260,5 @@ ALL_PINS = (
     pin_lemmas,
     pin_empty,
     pin_constant_rows,
+    pin_correlation_output,
 )

@@ -86,3 +86,69 @@ def test_discords_find_planted_malformed_beats(mp):
         mp.mp_dict_free(ctx, d)
     finally:
         mp.mp_shutdown(ctx)
+
+
+def test_correlation_output_matches_oracle(mp):
+    """mp_ab_join_corr: the largest rho = 1 - d^2/(2m) per row and the join's index (Sec. 2.1)."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        m = 96
+        q = synthetic.ecg_like(6000, 61, n_malformed=3).astype(np.float32)
+        b = synthetic.ecg_like(9000, 62).astype(np.float32)
+        b[4000:4200] = 1.5  # constant dictionary windows
+        offs = np.array([0, 2500, 2700, 6000, 9000])
+        d = mp.mp_dict_load(ctx, b, offs, [m])
+        rho, idx = mp.mp_ab_join_corr(ctx, d, q, m)
+        dist, idx2 = mp.mp_ab_join(ctx, d, q, m)
+        assert np.array_equal(idx, idx2)
+        np.testing.assert_allclose(rho, 1.0 - dist ** 2 / (2 * m), rtol=0, atol=1e-12)
+        orho, oidx = oracle.ab_join_corr(q, b, offs, m)
+        # the distance tolerance 1e-4 near d carries to rho as d * 1e-4 / m
+        tol = 1e-4 * np.maximum(dist, 1.0) / m
+        assert np.all(np.abs(rho - orho) <= tol + 1e-9)
+        assert np.all((rho <= 1.0 + 1e-9) & (rho >= -1.0 - 1e-9))
+        mp.mp_dict_free(ctx, d)
+        # no dictionary window at all: -inf / -1
+        d = mp.mp_dict_load(ctx, b[:90], np.array([0, 90]), [m])
+        rho, idx = mp.mp_ab_join_corr(ctx, d, q[:500], m)
+        assert np.all(np.isneginf(rho)) and np.all(idx == -1)
+        mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)
+
+
+def test_streaming_join_equals_one_shot_join(mp):
+    """Appending a series in uneven pieces joins every window once, as the one-shot join does."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        m = 128
+        train = synthetic.ecg_like(1 << 15, 71).astype(np.float32)
+        db, offs = synthetic.cut_dictionary(train, 16, 700)
+        d = mp.mp_dict_load(ctx, db, offs, [m])
+        x = synthetic.ecg_like(20000, 72, n_malformed=4).astype(np.float32)
+        full_d, full_i = mp.mp_ab_join(ctx, d, x, m)
+        st = mp.mp_stream_open(ctx, d, mp.MP_F32, m)
+        cuts = [0, 50, 127, 128, 900, 901, 5000, 12000, 19999, 20000]
+        got_d, got_i, firsts = [], [], []
+        for a, c in zip(cuts[:-1], cuts[1:]):
+            sd, si, first = mp.mp_stream_append(st, x[a:c])
+            assert len(sd) == max(0, c - m + 1) - max(0, a - m + 1)
+            if len(sd):
+                firsts.append(first)
+            got_d.append(sd)
+            got_i.append(si)
+        # an empty append changes nothing
+        sd, si, first = mp.mp_stream_append(st, x[:0])
+        assert len(sd) == 0 and first == len(x) - m + 1
+        mp.mp_stream_close(st)
+        got_d = np.concatenate(got_d)
+        got_i = np.concatenate(got_i)
+        assert len(got_d) == len(full_d) and firsts[0] == 0
+        np.testing.assert_allclose(got_d, full_d, rtol=0, atol=1e-4)
+        diff = got_i != full_i
+        assert diff.mean() < 1e-3 and np.all(np.abs(got_d[diff] - full_d[diff]) <= 1e-4)
+        rows = np.random.default_rng(3).choice(len(got_d), 64, replace=False)
+        parity.check(got_d, got_i, x, db, offs, m, rows=rows, atol=1e-4)
+        mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)

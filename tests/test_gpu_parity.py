@@ -253,3 +253,22 @@ def test_drifting_offset_series_all_rows(mp, ctx):
     offs = np.concatenate(([0], np.cumsum(lens))).astype(np.int64)
     dist, idx = join(mp, ctx, q, b, offs, m)
     parity.check(dist, idx, q, b, offs, m, atol=1e-4)
+
+
+def test_large_join_runs_in_row_chunks(mp, ctx):
+    """A join whose top-seed matrix would pass its 2 GiB cap runs in row chunks.
+
+    A dictionary of 2^20 samples makes each seed row about 4 MB, so a chunk is
+    512 seed rows = 262,144 query windows, and a query of 600,000 windows runs
+    in three chunks. Rows at every chunk boundary are checked against the
+    oracle.
+    """
+    m = 64
+    b = synthetic.random_walk(1 << 20, 81).astype(np.float32)
+    offs = np.array([0, 300_000, 300_100, 1 << 20])
+    q = synthetic.random_walk(600_000 + m - 1, 82).astype(np.float32)
+    dist, idx = join(mp, ctx, q, b, offs, m)
+    edges = np.array([0, 1, 511, 512, 262_143, 262_144, 262_145, 524_287, 524_288, 524_289, 599_999])
+    rows = np.unique(np.concatenate([edges, np.random.default_rng(4).choice(600_000, 40, replace=False)]))
+    parity.check(dist, idx, q, b, offs, m, rows=rows, atol=1e-4)
+    assert np.all((dist >= 0) & (dist <= 2 * math.sqrt(m) + 1e-9))
