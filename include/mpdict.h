@@ -177,6 +177,50 @@ int mp_stream_append(mp_stream *stream, const void *samples, int64_t n_new, doub
 int mp_stream_close(mp_stream *stream);
 
 /*
+ * Self-join matrix profile of one float32 series (the input of Algorithm 1,
+ * Sec. 3.1): for every window i the nearest window g with |g - i| >= excl
+ * (closer windows are trivial matches of i), its distance and index, with the
+ * conventions of mp_ab_join (a constant window is 0 from a constant window
+ * outside its zone and sqrt(m) from the rest). Host buffers of n - m + 1
+ * values; +inf / -1 where no window lies outside the zone. excl >= 1,
+ * 4 <= m <= 8192. Allocates and synchronises.
+ */
+int mp_self_join(mp_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m, int32_t excl,
+                 double *out_dist, int64_t *out_idx);
+
+/* terminal conditions of mp_learn_dictionary (Algorithm 1, lines 13-14) */
+#define MP_LEARN_MEMORY 0 /* stop once the merged dictionary holds >= term_value samples */
+#define MP_LEARN_EMAX 1   /* stop once the running bound max_i S[i] is <= term_value */
+
+/*
+ * Dictionary learning, Algorithm 1 (Sec. 3.1), on the GPU, for a float32
+ * training series t_b of n_b samples and window length m (4 <= m <= 8192).
+ *   1. P_B = mp_self_join(t_b, m, excl = ceil(m/2)).
+ *   2. Repeat: j = argmin over i of P_B[i] - S[i] outside the zones
+ *      [j' - m/2, j' + m/2) of the windows j' taken before (S = 0 at first);
+ *      add T_B[j : j + m] with floor((k_context - 1) m / 2) samples of
+ *      context on each side (clipped to the series), so an element holds
+ *      k_context * m samples; S = the distance profile of T_B against
+ *      T_B[j : j + m] (first time) or its element-wise minimum with S.
+ *   3. Stop at the terminal condition (term_kind, term_value), after
+ *      max_elements elements, or when no window is left.
+ * Overlapping elements are merged (Sec. 3.1, Fig. 5). Outputs (host):
+ *   seg_start, seg_len  the merged elements as positions in t_b, sorted,
+ *                       *n_segments of them (capacity max_elements each);
+ *                       the dictionary is t_b[seg_start[s] : seg_start[s] +
+ *                       seg_len[s]] concatenated, offsets the prefix sums
+ *   err_bound           (may be NULL) max_i S[i] at the end. Every window of
+ *                       t_b is at most this far from a taken window, so it
+ *                       bounds the learned dictionary's e_max (Sec. 3.3)
+ *   chosen, n_chosen    (may be NULL) the taken windows j in order
+ * Allocates and synchronises.
+ */
+int mp_learn_dictionary(mp_ctx *ctx, const void *t_b, int32_t dtype, int64_t n_b, int32_t m, double k_context,
+                        int32_t term_kind, double term_value, int32_t max_elements, int64_t *seg_start,
+                        int64_t *seg_len, int32_t *n_segments, double *err_bound, int64_t *chosen,
+                        int32_t *n_chosen);
+
+/*
  * The same join on device buffers, enqueued on `stream` (a cudaStream_t; NULL
  * = the context's own stream). d_query, d_out_dist and d_out_idx are device
  * pointers with the sizes of mp_ab_join. The call returns once the work is

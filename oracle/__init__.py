@@ -48,6 +48,8 @@ def load(path: Optional[str] = None):
     lib.mpo_ab_join.argtypes = [dp, ctypes.c_int64, dp, i64p, ctypes.c_int32, ctypes.c_int32,
                                 i64p, ctypes.c_int64, dp, i64p, dp, ctypes.c_int]
     lib.mpo_ab_join.restype = ctypes.c_int
+    lib.mpo_self_join.argtypes = [dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, dp, i64p, ctypes.c_int]
+    lib.mpo_self_join.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -134,4 +136,78 @@ def ab_join_corr(query, dict_samples, offsets, m: int, rows=None, nthreads: int 
     d, i, _ = ab_join(query, dict_samples, offsets, m, rows=rows, nthreads=nthreads, lib=lib)
     rho = np.where(i >= 0, 1.0 - d * d / (2.0 * m), -np.inf)
     return rho, i
+
+
+def self_join(series, m: int, excl: int, nthreads: int = 0, lib=None):
+    """Self-join matrix profile (Algorithm 1's P_B): nearest window outside +-excl. Returns (dist, idx)."""
+    lib = lib or load()
+    a = _f64(series)
+    nq = len(a) - m + 1
+    dist = np.empty(nq)
+    idx = np.empty(nq, dtype=np.int64)
+    rc = lib.mpo_self_join(_ptr(a, ctypes.c_double), len(a), m, int(excl), _ptr(dist, ctypes.c_double),
+                           _ptr(idx, ctypes.c_int64), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"mpo_self_join failed ({rc})")
+    return dist, idx
+
+
+def learn_dictionary(t_b, m: int, k_context: float = 1.5, term: str = "memory", term_value: float = 0.0,
+                     max_elements: int = 1 << 30, lib=None):
+    """Dictionary learning, Algorithm 1 (Sec. 3.1), step by step in float64.
+
+    P_B is the self-join with trivial matches |g - i| < ceil(m/2) left out
+    (line 3). Each iteration takes j = argmin (P_B - S) outside the zones
+    [j' - m/2, j' + m/2) of the windows taken before (lines 7-11, S = 0 at
+    first, lowest index on ties), adds T_B[j : j + m] with
+    floor((k - 1) m / 2) samples of context on each side (line 12), folds the
+    distance profile of T_B against T_B[j : j + m] into S by an element-wise
+    minimum (lines 15-19), and stops at the terminal condition (lines 13-14):
+    ``term="memory"`` once the merged elements hold >= term_value samples,
+    ``term="emax"`` once max(S) <= term_value; or after max_elements, or when
+    no window is left. Overlapping elements are merged (Fig. 5).
+
+    Returns ``(segments, chosen, err_bound)``: the merged elements as
+    (start, length) pairs, the taken windows in order, and max(S) at the end.
+    """
+    lib = lib or load()
+    x = _f64(t_b)
+    n = len(x)
+    nq = n - m + 1
+    P, _ = self_join(x, m, (m + 1) // 2, lib=lib)
+    S = np.zeros(nq)
+    excluded = np.zeros(nq, dtype=bool)
+    half = m // 2
+    pad = int(np.floor((k_context - 1.0) * m / 2.0))
+    elems, chosen = [], []
+    smax = np.inf
+    for it in range(max_elements):
+        Pp = np.where(excluded, np.inf, P - S)
+        finite = np.isfinite(Pp)
+        if not finite.any():
+            break
+        j = int(np.argmin(np.where(finite, Pp, np.inf)))  # argmin: lowest index on ties
+        chosen.append(j)
+        elems.append((max(0, j - pad), min(n, j + m + pad)))
+        excluded[max(0, j - half):min(nq, j + half)] = True
+        Sp, _, _ = ab_join(x, x[j:j + m], np.array([0, m]), m, lib=lib)  # distance profile of window j
+        S = Sp if it == 0 else np.minimum(S, Sp)
+        smax = float(S.max())
+        total = sum(b - a for a, b in _merge(elems))
+        if term == "memory" and total >= term_value:
+            break
+        if term == "emax" and smax <= term_value:
+            break
+    segs = [(a, b - a) for a, b in _merge(elems)]
+    return segs, chosen, smax
+
+
+def _merge(iv):
+    out = []
+    for a, b in sorted(iv):
+        if out and a < out[-1][1]:
+            out[-1] = (out[-1][0], max(out[-1][1], b))
+        else:
+            out.append((a, b))
+    return out
 

@@ -222,3 +222,53 @@ int mpo_ab_join(const double *a, int64_t na, const double *b, const int64_t *off
     free(bc);
     return MPO_OK;
 }
+
+/*
+ * The self-join matrix profile of one series (the P_B of Algorithm 1,
+ * Sec. 3.1): for every window i, the nearest window g of the same series with
+ * |g - i| >= excl (closer windows overlap i and are its trivial matches),
+ * lowest g on ties; +inf / -1 if no window lies outside the zone.
+ */
+int mpo_self_join(const double *a, int64_t na, int32_t m, int32_t excl, double *dist, int64_t *idx, int nthreads)
+{
+    if (!a || !dist || !idx || m < 1 || na < m || excl < 1)
+        return MPO_EARG;
+    const int64_t nq = na - m + 1;
+    double *mu = (double *)malloc(sizeof(double) * (size_t)nq);
+    double *sd = (double *)malloc(sizeof(double) * (size_t)nq);
+    uint8_t *cs = (uint8_t *)malloc((size_t)nq);
+    if (!mu || !sd || !cs) {
+        free(mu); free(sd); free(cs);
+        return MPO_ENOMEM;
+    }
+    for (int64_t g = 0; g < nq; ++g) {
+        cs[g] = (uint8_t)mpo_window_is_constant(a + g, m);
+        mpo_window_mean_std(a + g, m, &mu[g], &sd[g]);
+    }
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < nq; ++i) {
+        double best = INFINITY;
+        int64_t best_g = -1;
+        for (int64_t g = 0; g < nq; ++g) {
+            if (g > i - excl && g < i + excl)
+                continue; /* trivial match */
+            const double d = znorm_distance(a + i, mu[i], sd[i], cs[i], a + g, mu[g], sd[g], cs[g], m);
+            if (d < best) {
+                best = d;
+                best_g = g;
+            }
+        }
+        dist[i] = best;
+        idx[i] = best_g;
+    }
+    free(mu);
+    free(sd);
+    free(cs);
+    return MPO_OK;
+}

@@ -43,6 +43,9 @@ MP_PHASE_FINALIZE = 2
 MP_PHASE_SEEDS = 3
 MP_PHASE_COUNT = 4
 
+MP_LEARN_MEMORY = 0
+MP_LEARN_EMAX = 1
+
 MP_PENDING = 0
 MP_DONE = 1
 MP_FAILED = 2
@@ -98,6 +101,10 @@ def _load():
         "mp_stream_open": ([P, P, i32, i32, ctypes.POINTER(P)], ctypes.c_int),
         "mp_stream_append": ([P, P, i64, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "mp_stream_close": ([P], ctypes.c_int),
+        "mp_self_join": ([P, P, i32, i64, i32, i32, P, P], ctypes.c_int),
+        "mp_learn_dictionary": ([P, P, i32, i64, i32, ctypes.c_double, i32, ctypes.c_double, i32, P, P,
+                                 ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(i32)],
+                                ctypes.c_int),
         "mp_ab_join_device": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
         "mp_ab_join_noalloc": ([P, P, P, i32, i64, i32, P, P, P], ctypes.c_int),
         "mp_window_stats": ([P, P, i32, i64, i32, P, P, P, P], ctypes.c_int),
@@ -208,6 +215,33 @@ def mp_ab_join_corr(ctx, d, query: np.ndarray, m: int) -> Tuple[np.ndarray, np.n
     idx = np.empty(nq, dtype=np.int64)
     _check(lib.mp_ab_join_corr(ctx, d, _ptr(q), _dtype_of(q), len(q), m, _ptr(corr), _ptr(idx)))
     return corr, idx
+
+
+def mp_self_join(ctx, series: np.ndarray, m: int, excl: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Self-join matrix profile (float32): nearest window with |g - i| >= excl; returns (distance, index)."""
+    x = np.ascontiguousarray(series)
+    nq = max(len(x) - m + 1, 0)
+    dist = np.empty(nq, dtype=np.float64)
+    idx = np.empty(nq, dtype=np.int64)
+    _check(lib.mp_self_join(ctx, _ptr(x), _dtype_of(x), len(x), m, excl, _ptr(dist), _ptr(idx)))
+    return dist, idx
+
+
+def mp_learn_dictionary(ctx, t_b: np.ndarray, m: int, k_context: float = 1.5, term: int = MP_LEARN_MEMORY,
+                        term_value: float = 0.0, max_elements: int = 4096):
+    """Algorithm 1 on the GPU; returns (segments [(start, length)], chosen windows, error bound max S)."""
+    x = np.ascontiguousarray(t_b)
+    starts = np.empty(max_elements, dtype=np.int64)
+    lens = np.empty(max_elements, dtype=np.int64)
+    chosen = np.empty(max_elements, dtype=np.int64)
+    nseg = ctypes.c_int32()
+    nch = ctypes.c_int32()
+    bound = ctypes.c_double()
+    _check(lib.mp_learn_dictionary(ctx, _ptr(x), _dtype_of(x), len(x), m, k_context, term, term_value, max_elements,
+                                   _ptr(starts), _ptr(lens), ctypes.byref(nseg), ctypes.byref(bound),
+                                   _ptr(chosen), ctypes.byref(nch)))
+    segs = [(int(a), int(b)) for a, b in zip(starts[: nseg.value], lens[: nseg.value])]
+    return segs, [int(c) for c in chosen[: nch.value]], bound.value
 
 
 def mp_stream_open(ctx, d, dtype: int, m: int):

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmpdict.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["mp_stats.cu", "mp_plain.cu", "mp_finalize.cu", "mp_tc.cu", "mp_runtime.cu"]
+SOURCES = ["mp_stats.cu", "mp_plain.cu", "mp_finalize.cu", "mp_tc.cu", "mp_learn.cu", "mp_runtime.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *ARCH]
 

@@ -58,6 +58,27 @@ __device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
     return g1 >= 0 && (g2 < 0 || q1 > q2 || (q1 == q2 && g1 < g2));
 }
 
+// Self-join helpers (excl > 0; the dictionary is the one series, so every
+// position 0 .. npos_b - 1 is a valid window): the lowest constant window and
+// the lowest window outside query window i's exclusion zone, -1 if none.
+// With excl = 0 they are the dictionary's g_const and g_first.
+template <typename T>
+__device__ __forceinline__ int64_t const_outside(const FinalizeParams<T> &p, int64_t i)
+{
+    if (p.excl == 0 || p.g_const < 0) return p.g_const;
+    if (p.g_const <= i - p.excl) return p.g_const;  // the lowest constant window lies before the zone
+    const int64_t x = i + p.excl;
+    return x < p.npos_b ? p.next_const[x] : -1;
+}
+template <typename T>
+__device__ __forceinline__ int64_t first_outside(const FinalizeParams<T> &p, int64_t i)
+{
+    if (p.excl == 0 || p.g_first < 0) return p.g_first;
+    if (p.g_first <= i - p.excl) return p.g_first;
+    const int64_t x = i + p.excl;
+    return x < p.npos_b ? x : -1;
+}
+
 
 // Re-score the kChunk windows g .. g + kChunk - 1 of one chunk (dictionary
 // samples pb) against query window i (samples pa, split mean ma) with direct
@@ -75,7 +96,7 @@ __device__ __forceinline__ void rescore_chunk(const T *__restrict__ pa, const T 
                                               int64_t npos_b, int m, const Split<T> *__restrict__ ms_b,
                                               const vec4_t<T> *__restrict__ rs_b, int64_t i, int32_t g,
                                               const Split<T> ma, int lane, T *wa, T *wb, T &sc_out,
-                                              int32_t &g_out)
+                                              int32_t &g_out, int excl)
 {
     const T sa = ma.hi, sb = ms_b[g].hi;
     const int half = lane >> 4, lg = lane & 15;
@@ -123,7 +144,7 @@ __device__ __forceinline__ void rescore_chunk(const T *__restrict__ pa, const T 
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);  // the two k-halves of the 16 lanes
     const int cand = 8 * half + (lane & 7);
     const int64_t gc = (int64_t)g + cand;
-    bool ok = gc < npos_b;
+    bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl));
     vec4_t<T> r;
     if (ok) {
         r = rs_b[gc];
@@ -195,12 +216,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
         if (p.g_first >= 0) {
             if (p.cflag_a[i]) {
                 // 3. a constant query window is 0 from a constant window, sqrt(m) from the rest
-                if (p.g_const >= 0) {
+                const int64_t gc = const_outside(p, i), gf = first_outside(p, i);
+                if (gc >= 0) {
                     d = 0.0;
-                    gi = p.g_const;
-                } else {
+                    gi = gc;
+                } else if (gf >= 0) {
                     d = sqrt_m;
-                    gi = p.g_first;
+                    gi = gf;
                 }
             } else {
                 if (g >= 0) {
@@ -213,7 +235,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                     T sc;
                     int32_t gw;
                     rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, g, ma, lane, wa, wb, sc,
-                                     gw);
+                                     gw, p.excl);
                     if (p.near != nullptr) {
                         const T lim = q - T(kNearTieRho) * T(m) / p.rs_a[i].z;  // the row is not constant: z > 0
                         for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
@@ -240,7 +262,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                                     T s2;
                                     int32_t g2;
                                     rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, cu, ma, lane,
-                                                     wa, wb, s2, g2);
+                                                     wa, wb, s2, g2, p.excl);
                                     if (better(s2, g2, sc, gw)) {
                                         sc = s2;
                                         gw = g2;
@@ -255,9 +277,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                         gi = gw;
                     }
                 }
-                if (p.g_const >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && p.g_const < gi))) {
+                const int64_t gcst = const_outside(p, i);
+                if (gcst >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && gcst < gi))) {
                     d = sqrt_m;
-                    gi = p.g_const;
+                    gi = gcst;
                 }
             }
         }
@@ -307,7 +330,8 @@ __device__ __forceinline__ void stage_chunk(const T *__restrict__ pb, int64_t nb
 template <typename T>
 __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, const Split<T> *__restrict__ ms_b,
                                                const vec4_t<T> *__restrict__ rs_b, const T *qa, T da, int32_t g,
-                                               int lane, const T *wb, T &sc_out, int32_t &g_out)
+                                               int lane, const T *wb, T &sc_out, int32_t &g_out, int64_t i,
+                                               int excl)
 {
     const T sb = ms_b[g].hi;
     const int half = lane >> 4, lg = lane & 15;
@@ -345,7 +369,7 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, c
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);
     const int cand = 8 * half + (lane & 7);
     const int64_t gc = (int64_t)g + cand;
-    bool ok = gc < npos_b;
+    bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl));
     vec4_t<T> rv;
     if (ok) {
         rv = rs_b[gc];
@@ -418,12 +442,13 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
         if (p.g_first >= 0) {
             if (p.cflag_a[i]) {
                 // 3. a constant query window is 0 from a constant window, sqrt(m) from the rest
-                if (p.g_const >= 0) {
+                const int64_t gc = const_outside(p, i), gf = first_outside(p, i);
+                if (gc >= 0) {
                     d = 0.0;
-                    gi = p.g_const;
-                } else {
+                    gi = gc;
+                } else if (gf >= 0) {
                     d = sqrt_m;
-                    gi = p.g_first;
+                    gi = gf;
                 }
             } else {
                 if (g >= 0) {
@@ -434,7 +459,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
                     stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, g, lane, wb);
                     T sc;
                     int32_t gw;
-                    rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, g, lane, wb, sc, gw);
+                    rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, g, lane, wb, sc, gw, i, p.excl);
                     int32_t staged = g;  // the chunk whose samples wb holds
                     int32_t win = g;     // the chunk of the best window so far
                     if (p.near != nullptr) {
@@ -464,7 +489,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
                                     int32_t g2;
                                     stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, cu, lane, wb);
                                     rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2,
-                                                      g2);
+                                                      g2, i, p.excl);
                                     staged = cu;
                                     if (better(s2, g2, sc, gw)) {
                                         sc = s2;
@@ -496,9 +521,10 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
                     }
                     __syncwarp();  // the next row rewrites qa and wb
                 }
-                if (p.g_const >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && p.g_const < gi))) {
+                const int64_t gcst = const_outside(p, i);
+                if (gcst >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && gcst < gi))) {
                     d = sqrt_m;
-                    gi = p.g_const;
+                    gi = gcst;
                 }
             }
         }

@@ -99,6 +99,8 @@ struct PlainLaunch {
     int32_t n_groups;      // column groups
     int32_t warps;         // warps per CTA (rows per CTA = warps * 32 * kPlainRowsPerLane)
     int64_t ld_part = 0;   // row stride of the partial results and near-tie records (0: nq)
+    int64_t row0 = 0;      // self-join: series position of query window 0
+    int32_t excl = 0;      // self-join: exclusion zone half-width (0: an AB-join)
 };
 
 // Plain diagonal-recurrence join (kernel K2). Writes part[group * ld_part + row]
@@ -140,6 +142,8 @@ struct PlainRequest {
     int64_t seed_ld;
     NearTies *near;         // [n_groups][nq] near-tie records (required)
     int64_t ld_part;        // nq
+    int64_t row0;           // 0
+    int32_t excl;           // 0: serving joins are AB-joins
 };
 struct BatchItem {
     int32_t req;  // index into the request array
@@ -177,7 +181,30 @@ template <typename T> struct FinalizeParams {
     const int32_t *err;       // may be null; if *err != 0 a tensor-core wait ran out: NaN / -1 everywhere
     const NearTies *near;     // may be null; [n_groups][nq] near-tie records of the plain kernel
     int32_t out_corr;         // 1: write rho = 1 - d^2 / (2m) (Pearson's r for non-constant windows), -inf if none
+    // Self-join of one series (dictionary learning): windows g with |g - i| < excl are
+    // trivial matches of query window i and are left out; next_const[x] is the lowest
+    // constant window >= x (-1 if none), over the npos_b positions. excl = 0: an AB-join.
+    int32_t excl;
+    const int64_t *next_const;
 };
 template <typename T> cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st);
+
+// Dictionary learning (Algorithm 1) kernels, mp_learn.cu.
+// next_const[x] = the lowest position >= x with cflag set, or -1; scratch holds
+// next_const_scratch_elems(npos) int64 values.
+cudaError_t launch_next_const(const uint8_t *cflag, int64_t npos, int64_t *next_const, int64_t *scratch,
+                              cudaStream_t st);
+size_t next_const_scratch_elems(int64_t npos);
+// *best = (order key of min_i (P[i] - S[i]) << 32) | argmin over the positions not
+// excluded (lowest i on ties); ~0 if there is none.
+cudaError_t launch_learn_argmin(const double *P, const float *S, const uint8_t *excluded, int64_t n,
+                                unsigned long long *best, int sm_count, cudaStream_t st);
+// The float of an order key (host).
+float learn_key_float(uint32_t key);
+// S'[i] = d(window i, window j) of series x (FP32 statistics ms, rs, cflag of its
+// nq windows); S = S' if first, else min(S, S'); *smax = order key of max S.
+cudaError_t launch_learn_profile(const float *x, int64_t nq, int32_t m, const Split<float> *ms, const float4 *rs,
+                                 const uint8_t *cflag, int64_t j, float *S, bool first, uint32_t *smax, int sm_count,
+                                 cudaStream_t st);
 
 }  // namespace mpd

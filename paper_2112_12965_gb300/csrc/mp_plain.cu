@@ -59,6 +59,8 @@ template <typename T> struct PlainParams {
     int64_t seed_ld;
     NearTies *near;     // near-tie records, or null
     int64_t ld_part;    // row stride of part and near (>= nq)
+    int64_t row0;       // self-join: position in the series of query window 0
+    int32_t excl;       // self-join: pairs with |g - (row0 + r)| < excl are left out (0: none)
 };
 
 // Add a near-tie record (chunk g, approximate score q) to a slot; with both
@@ -136,6 +138,16 @@ template <typename T, int kRows, bool kPacked> struct Rows {
 #pragma unroll
         for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fma(C[j], z, w));
     }
+    // the same, leaving out rows inside the column's exclusion zone
+    // (|d0 - j| < excl, d0 = column window - the lane's first row)
+    __device__ __forceinline__ void score_max_excl(T z, T w, T *cm, int d0, int excl) const
+    {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+            const T q = fma(C[j], z, w);
+            cm[j] = fmax(cm[j], abs(d0 - j) < excl ? T(-INFINITY) : q);
+        }
+    }
 };
 
 template <int kRows> struct Rows<float, kRows, true> {
@@ -178,13 +190,23 @@ template <int kRows> struct Rows<float, kRows, true> {
             cm[k + H] = fmaxf(cm[k + H], q.y);
         }
     }
+    __device__ __forceinline__ void score_max_excl(float2 Z, float2 W, float *cm, int d0, int excl) const
+    {
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float2 q = __ffma2_rn(C[k], Z, W);
+            cm[k] = fmaxf(cm[k], abs(d0 - k) < excl ? -INFINITY : q.x);
+            cm[k + H] = fmaxf(cm[k + H], abs(d0 - k - H) < excl ? -INFINITY : q.y);
+        }
+    }
 };
 
 // kSeeds: the top seeds come from p.seed_top (the tensor cores) instead of
 // direct dot products; kNear: near ties are recorded in p.near; kPacked
-// (FP32 only): packed FMA on row pairs. All are compile-time so that each
-// form carries only its own code.
-template <typename T, int kRows, bool kSeeds, bool kNear, bool kPacked>
+// (FP32 only): packed FMA on row pairs; kSelf: a self-join whose trivial
+// matches (|g - i| < p.excl) are left out, in the column blocks that reach
+// them. All are compile-time so that each form carries only its own code.
+template <typename T, int kRows, bool kSeeds, bool kNear, bool kPacked, bool kSelf = false>
 __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, int grp, unsigned char *smem_raw)
 {
     constexpr int CB = kPlainColBlock;
@@ -370,6 +392,15 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             // recorded, and the finalisation re-scores that chunk's
             // windows to find the exact one.
             const T *stop_w = stop + warp * CB;
+            // self-join: does this block reach the exclusion zone of any of the CTA's rows?
+            bool band = false;
+            int d_lane = 0;  // column gblk - this lane's first row, clamped (only compared with small values)
+            if (kSelf) {
+                const int64_t a0 = p.row0 + R0;
+                band = gblk < a0 + rows_cta - 1 + p.excl && gblk + ncb - 1 > a0 - p.excl;
+                const int64_t dl = gblk - (p.row0 + r0);
+                d_lane = (int)(dl > (1 << 30) ? (1 << 30) : (dl < -(1 << 30) ? -(1 << 30) : dl));
+            }
             for (int c0 = 0; c0 < ncb; c0 += kChunk) {
                 T cm[kRows];
 #pragma unroll
@@ -383,14 +414,21 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                             const float up = __shfl_up_sync(0xffffffffu, R.last(), 1);
                             R.step(make_float2(cxy.x, cxy.y), make_float2(cxy.z, cxy.w), up, lane == 0, stop_w[c]);
                         }
-                        R.score_max(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), cm);
+                        if (kSelf && band)
+                            R.score_max_excl(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), cm, d_lane + c,
+                                             p.excl);
+                        else
+                            R.score_max(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), cm);
                     } else {
                         const vec4_t<T> cs = scs[c];
                         if (cb > 0 || c > 0) {
                             const T up = __shfl_up_sync(0xffffffffu, R.last(), 1);
                             R.step(cs.x, cs.y, up, lane == 0, stop_w[c]);
                         }
-                        R.score_max(cs.z, cs.w, cm);
+                        if (kSelf && band)
+                            R.score_max_excl(cs.z, cs.w, cm, d_lane + c, p.excl);
+                        else
+                            R.score_max(cs.z, cs.w, cm);
                     }
                 }
                 const int32_t gch = (int32_t)(gblk + c0);
@@ -438,11 +476,11 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 // Four CTAs (16 warps) per SM for FP32 data: the kernel then fits in 128
 // registers without spilling, and the extra warps hide the shuffle and
 // shared-memory latencies of the recurrence.
-template <typename T, int kRows, bool kSeeds, bool kNear>
+template <typename T, int kRows, bool kSeeds, bool kNear, bool kSelf = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_plain(PlainParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    plain_item<T, kRows, kSeeds, kNear, true>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
+    plain_item<T, kRows, kSeeds, kNear, true, kSelf>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
 }
 
 // Persistent batched form for serving: the CTAs walk a list of work items that
@@ -506,6 +544,8 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     p.seed_ld = seed_ld;
     p.near = near;
     p.ld_part = L.ld_part > 0 ? L.ld_part : L.nq;
+    p.row0 = L.row0;
+    p.excl = L.excl;
     const size_t smem = plain_smem_bytes<T>(L.warps, L.m);
     constexpr int R = plain_rows_per_lane<T>();
     const int64_t grid = (int64_t)L.n_row_blocks * L.n_groups;
@@ -517,9 +557,14 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     };
     if constexpr (sizeof(T) == 8) {
         // FP64 data: seeds from direct dot products, no near-tie records
-        if (seed_top != nullptr || near != nullptr) return cudaErrorInvalidValue;
+        if (seed_top != nullptr || near != nullptr || L.excl > 0) return cudaErrorInvalidValue;
         return launch(k_plain<T, R, false, false>);
     } else {
+        if (L.excl > 0) {
+            // self-join (dictionary learning): tensor-core seeds and near-tie records
+            if (seed_top == nullptr || near == nullptr) return cudaErrorInvalidValue;
+            return launch(k_plain<T, R, true, true, true>);
+        }
         if (seed_top != nullptr)
             return near != nullptr ? launch(k_plain<T, R, true, true>) : launch(k_plain<T, R, true, false>);
         return near != nullptr ? launch(k_plain<T, R, false, true>) : launch(k_plain<T, R, false, false>);

@@ -458,6 +458,8 @@ static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const P
     f.err = nullptr;
     f.near = nullptr;
     f.out_corr = 0;
+    f.excl = 0;
+    f.next_const = nullptr;
     return f;
 }
 
@@ -604,10 +606,15 @@ static size_t join_seed_bytes(const mp_dict *d, int32_t dtype, int64_t nq, int32
 // (the workspace then holds join_seed_bytes(..., true) more bytes). The
 // error word at the front of the workspace is zeroed first; tensor-core
 // kernels set it when a bounded wait runs out.
+// excl > 0 makes it the self-join of one series (the query is the dictionary's
+// only segment): pairs with |g - i| < excl are trivial matches and are left
+// out; next_const is the series' next-constant-window table (launch_next_const).
 static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, int32_t dtype, int64_t n, int32_t m,
                        double *d_dist, int64_t *d_idx, cudaStream_t st, unsigned char *base, int kernel,
-                       bool seeds = true, bool corr = false)
+                       bool seeds = true, bool corr = false, int32_t excl = 0, const int64_t *next_const = nullptr)
 {
+    if (excl > 0 && (dtype != MP_F32 || !seeds || kernel != MP_KERNEL_PLAIN || !next_const))
+        return fail(MP_E_INTERNAL, "the self-join runs the FP32 plain kernel with tensor-core seeds");
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
@@ -701,6 +708,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             Lc.nq = rows;
             Lc.n_row_blocks = (int32_t)((rows + rows_cta - 1) / rows_cta);
             Lc.ld_part = nq;
+            Lc.row0 = r0;
+            Lc.excl = excl;
             CUDA_TRY(launch_plain<float>(Lc, a + r0, rows + m - 1, rs_a + r0, ms_a + r0, (const float *)d->d_samples,
                                          d->nb, (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
                                          gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0,
@@ -713,6 +722,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             f.err = seeds ? err : nullptr;
             f.near = near;
             f.out_corr = corr ? 1 : 0;
+            f.excl = excl;
+            f.next_const = next_const;
             CUDA_TRY(launch_finalize<float>(f, st));
         }
     }
@@ -1478,6 +1489,192 @@ extern "C" int mp_stream_close(mp_stream *st)
 {
     g_err.clear();
     delete st;
+    return MP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Self-join and dictionary learning (Algorithm 1, Sec. 3.1)
+// ---------------------------------------------------------------------------
+namespace {
+// A device allocation freed at scope exit.
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+    int alloc(size_t bytes)
+    {
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(MP_E_NOMEM, "%zu bytes of device memory", bytes);
+        }
+        return MP_OK;
+    }
+};
+}  // namespace
+
+// The self-join profile of the series that dictionary d holds as its only
+// segment, into device outputs (caller holds ctx->mu).
+static int self_join_dev(mp_ctx *ctx, mp_dict *d, int32_t m, int32_t excl, double *dd, int64_t *di)
+{
+    DictStats *s = nullptr;
+    int rc = get_stats(ctx, d, m, &s);
+    if (rc) return rc;
+    const int64_t n = d->nb, nq = n - m + 1;
+    DevBuf nc, scr;
+    if ((rc = nc.alloc((size_t)nq * sizeof(int64_t))) || (rc = scr.alloc(next_const_scratch_elems(nq) * 8)))
+        return rc;
+    CUDA_TRY(launch_next_const(s->cflag, nq, (int64_t *)nc.p, (int64_t *)scr.p, ctx->stream));
+    rc = ensure_ws(ctx, join_ws_bytes(ctx, d, s, MP_F32, n, m));
+    if (rc) return rc;
+    rc = join_device(ctx, d, s, d->d_samples, MP_F32, n, m, dd, di, ctx->stream, (unsigned char *)ctx->ws,
+                     MP_KERNEL_PLAIN, true, false, excl, (const int64_t *)nc.p);
+    if (rc) return rc;
+    int32_t err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, ctx->ws, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (err) return fail(MP_E_TIMEOUT, "a tensor-core wait timed out on the device; results are invalid");
+    return MP_OK;
+}
+
+static int check_series(mp_ctx *ctx, const void *x, int32_t dtype, int64_t n, int32_t m)
+{
+    if (!ctx || !x) return fail(MP_E_ARG, "null argument");
+    if (dtype != MP_F32) return fail(MP_E_ARG, "the self-join and dictionary learning take float32 samples");
+    if (m < 4 || m > 8192) return fail(MP_E_ARG, "m=%d outside [4, 8192]", m);
+    if (n < m) return fail(MP_E_ARG, "series shorter than m");
+    return MP_OK;
+}
+
+extern "C" int mp_self_join(mp_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m, int32_t excl,
+                            double *out_dist, int64_t *out_idx)
+{
+    g_err.clear();
+    int rc = check_series(ctx, series, dtype, n, m);
+    if (rc) return rc;
+    if (excl < 1 || !out_dist || !out_idx) return fail(MP_E_ARG, "bad argument");
+    const int64_t offs[2] = {0, n};
+    mp_dict *d = nullptr;
+    rc = mp_dict_load(ctx, series, dtype, offs, 1, &m, 1, &d);
+    if (rc) return rc;
+    const int64_t nq = n - m + 1;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DevBuf dd, di;
+        if (!(rc = dd.alloc((size_t)nq * 8)) && !(rc = di.alloc((size_t)nq * 8)) &&
+            !(rc = self_join_dev(ctx, d, m, excl, (double *)dd.p, (int64_t *)di.p))) {
+            if (cudaMemcpy(out_dist, dd.p, (size_t)nq * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(out_idx, di.p, (size_t)nq * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = fail(MP_E_CUDA, "copying the self-join back");
+        }
+    }
+    mp_dict_free(ctx, d);
+    return rc;
+}
+
+// Merge overlapping intervals [start, end) (sorted by start); returns the samples they cover.
+static int64_t merge_intervals(std::vector<std::pair<int64_t, int64_t>> iv, std::vector<std::pair<int64_t, int64_t>> *out)
+{
+    std::sort(iv.begin(), iv.end());
+    out->clear();
+    int64_t total = 0;
+    for (const auto &x : iv) {
+        if (!out->empty() && x.first < out->back().second)
+            out->back().second = std::max(out->back().second, x.second);
+        else
+            out->push_back(x);
+    }
+    for (const auto &x : *out) total += x.second - x.first;
+    return total;
+}
+
+extern "C" int mp_learn_dictionary(mp_ctx *ctx, const void *t_b, int32_t dtype, int64_t n_b, int32_t m,
+                                   double k_context, int32_t term_kind, double term_value, int32_t max_elements,
+                                   int64_t *seg_start, int64_t *seg_len, int32_t *n_segments, double *err_bound,
+                                   int64_t *chosen, int32_t *n_chosen)
+{
+    g_err.clear();
+    int rc = check_series(ctx, t_b, dtype, n_b, m);
+    if (rc) return rc;
+    if (!(k_context >= 1.0) || max_elements < 1 || !seg_start || !seg_len || !n_segments ||
+        (term_kind != MP_LEARN_MEMORY && term_kind != MP_LEARN_EMAX))
+        return fail(MP_E_ARG, "bad argument");
+    const int64_t offs[2] = {0, n_b};
+    mp_dict *d = nullptr;
+    rc = mp_dict_load(ctx, t_b, dtype, offs, 1, &m, 1, &d);
+    if (rc) return rc;
+    const int64_t nq = n_b - m + 1;
+    const int32_t half = m / 2;
+    const int64_t pad = (int64_t)std::floor((k_context - 1.0) * m / 2.0);
+    std::vector<std::pair<int64_t, int64_t>> elems, merged;
+    std::vector<int64_t> picks;
+    float smax_v = INFINITY;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaStream_t st = ctx->stream;
+        DevBuf P, I, S, ex, key;
+        DictStats *s = nullptr;
+        if ((rc = P.alloc((size_t)nq * 8)) || (rc = I.alloc((size_t)nq * 8)) || (rc = S.alloc((size_t)nq * 4)) ||
+            (rc = ex.alloc((size_t)nq)) || (rc = key.alloc(16)))
+            goto done;
+        // line 3: the self-join matrix profile P_B, trivial matches |g - i| < ceil(m/2) left out
+        if ((rc = self_join_dev(ctx, d, m, (m + 1) / 2, (double *)P.p, (int64_t *)I.p))) goto done;
+        if ((rc = get_stats(ctx, d, m, &s))) goto done;
+        if (cudaMemsetAsync(S.p, 0, (size_t)nq * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(ex.p, 0, (size_t)nq, st) != cudaSuccess) {
+            rc = fail(MP_E_CUDA, "clearing the learning state");
+            goto done;
+        }
+        for (int32_t it = 0; it < max_elements; ++it) {
+            // lines 7-11: j = argmin (P_B - S) outside the taken elements' zones
+            unsigned long long best = ~0ull;
+            if (launch_learn_argmin((const double *)P.p, (const float *)S.p, (const uint8_t *)ex.p, nq,
+                                    (unsigned long long *)key.p, ctx->sm_count, st) != cudaSuccess ||
+                cudaMemcpyAsync(&best, key.p, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = fail(MP_E_CUDA, "argmin of the processed profile");
+                goto done;
+            }
+            if (best == ~0ull) break;  // every window is taken or excluded
+            const int64_t j = (int64_t)(best & 0xffffffffull);
+            // line 12: add T_B[j : j + m] with its context (k m samples in all)
+            picks.push_back(j);
+            elems.emplace_back(std::max<int64_t>(0, j - pad), std::min<int64_t>(n_b, j + m + pad));
+            // line 10 for the next iterations: the zone [j - m/2, j + m/2)
+            const int64_t z0 = std::max<int64_t>(0, j - half), z1 = std::min<int64_t>(nq, j + half);
+            // lines 15-19: S = S' or ElementwiseMin(S, S'), S' the distance profile of window j
+            uint32_t smax = 0;
+            if ((z1 > z0 && cudaMemsetAsync((uint8_t *)ex.p + z0, 1, (size_t)(z1 - z0), st) != cudaSuccess) ||
+                launch_learn_profile((const float *)d->d_samples, nq, m, (const Split<float> *)s->ms,
+                                     (const float4 *)s->rs, s->cflag, j, (float *)S.p, it == 0,
+                                     (uint32_t *)key.p + 2, ctx->sm_count, st) != cudaSuccess ||
+                cudaMemcpyAsync(&smax, (uint32_t *)key.p + 2, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = fail(MP_E_CUDA, "distance profile of the new element");
+                goto done;
+            }
+            smax_v = learn_key_float(smax);
+            // lines 13-14: the terminal condition
+            const int64_t total = merge_intervals(elems, &merged);
+            if (term_kind == MP_LEARN_MEMORY && (double)total >= term_value) break;
+            if (term_kind == MP_LEARN_EMAX && (double)smax_v <= term_value) break;
+        }
+        merge_intervals(elems, &merged);
+    }
+done:
+    mp_dict_free(ctx, d);
+    if (rc) return rc;
+    *n_segments = (int32_t)merged.size();
+    for (size_t k = 0; k < merged.size(); ++k) {
+        seg_start[k] = merged[k].first;
+        seg_len[k] = merged[k].second - merged[k].first;
+    }
+    if (err_bound) *err_bound = (double)smax_v;
+    if (n_chosen) *n_chosen = (int32_t)picks.size();
+    if (chosen)
+        for (size_t k = 0; k < picks.size(); ++k) chosen[k] = picks[k];
     return MP_OK;
 }
 

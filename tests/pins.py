@@ -251,6 +251,98 @@ def pin_correlation_output(lib, seeds=range(4)):
     assert np.all(np.isneginf(rho)) and np.all(i == -1)
 
 
+def _bf_dist_matrix(x, m):
+    """All-pairs z-normalised distances of one series' windows via numpy.corrcoef (non-constant windows)."""
+    nq = len(x) - m + 1
+    W = np.array([x[i : i + m] for i in range(nq)])
+    R = np.corrcoef(W)
+    return np.sqrt(np.maximum(0.0, 2 * m * (1 - R)))
+
+
+def pin_self_join(lib, seeds=range(4)):
+    for seed in seeds:
+        rng = np.random.default_rng(3000 + seed)
+        m = int(rng.choice([4, 6, 8]))
+        x = rng.standard_normal(int(rng.integers(3 * m, 50))).cumsum()
+        D = _bf_dist_matrix(x, m)
+        nq = len(D)
+        for excl in (1, (m + 1) // 2, m):
+            d, i = oracle.self_join(x, m, excl, lib=lib)
+            g = np.arange(nq)
+            Dm = np.where(np.abs(g[None, :] - g[:, None]) < excl, np.inf, D)
+            bd = Dm.min(axis=1)
+            np.testing.assert_allclose(d, bd, rtol=0, atol=1e-9)
+            srt = np.sort(Dm, axis=1)
+            uniq = np.isfinite(bd) & ((srt[:, 1] - srt[:, 0]) > 1e-9)
+            assert np.array_equal(i[uniq], np.argmin(Dm, axis=1)[uniq])
+            assert np.all(i[~np.isfinite(bd)] == -1)
+
+
+def _bf_learn(x, m, k, budget):
+    """Algorithm 1 restated on brute-force distances (memory terminal condition)."""
+    D = _bf_dist_matrix(x, m)
+    nq = len(D)
+    g = np.arange(nq)
+    P = np.where(np.abs(g[None, :] - g[:, None]) < (m + 1) // 2, np.inf, D).min(axis=1)
+    S = np.zeros(nq)
+    taken = np.zeros(nq, bool)
+    pad = int(np.floor((k - 1) * m / 2))
+    chosen, cover = [], np.zeros(len(x), bool)
+    while True:
+        Pp = np.where(taken, np.inf, P - S)
+        if not np.isfinite(Pp).any():
+            break
+        j = int(np.argmin(Pp))
+        chosen.append(j)
+        cover[max(0, j - pad) : min(len(x), j + m + pad)] = True
+        taken[max(0, j - m // 2) : min(nq, j + m // 2)] = True
+        S = D[j] if len(chosen) == 1 else np.minimum(S, D[j])
+        if cover.sum() >= budget:
+            break
+    return chosen
+
+
+def pin_learn_dictionary(lib):
+    rng = np.random.default_rng(4000)
+    # against an independent restatement on brute-force distances
+    for m, n, budget in ((8, 120, 60), (6, 90, 40)):
+        x = rng.standard_normal(n).cumsum()
+        segs, chosen, smax = oracle.learn_dictionary(x, m, 1.5, "memory", budget, lib=lib)
+        assert chosen == _bf_learn(x, m, 1.5, budget)
+    # invariants on a longer series with a planted motif
+    m = 16
+    x = rng.standard_normal(600).cumsum()
+    motif = np.sin(np.linspace(0, 3 * np.pi, m)) * 5
+    x[100:116] = motif + x[99]
+    x[420:436] = motif * 2 + x[419]
+    P, _ = oracle.self_join(x, m, (m + 1) // 2, lib=lib)
+    segs, chosen, smax = oracle.learn_dictionary(x, m, 1.5, "memory", 150, lib=lib)
+    assert chosen[0] == int(np.argmin(P)) and chosen[0] in (100, 420)
+    for a in range(len(chosen)):
+        for b in range(a):
+            assert not (chosen[b] - m // 2 <= chosen[a] < chosen[b] + m // 2)
+    total = sum(L for _, L in segs)
+    assert total >= 150
+    pad = int(np.floor(0.5 * m / 2))
+    before = oracle._merge([(max(0, j - pad), min(len(x), j + m + pad)) for j in chosen[:-1]])
+    assert sum(b - a for a, b in before) < 150
+    starts = [a for a, _ in segs]
+    assert starts == sorted(starts) and all(a + L <= b for (a, L), (b, _) in zip(segs, segs[1:]))
+    # the learned dictionary's e_max stays within the reported bound max(S)
+    samples = np.concatenate([x[a : a + L] for a, L in segs])
+    offs = np.concatenate(([0], np.cumsum([L for _, L in segs])))
+    d, _, _ = oracle.ab_join(x, samples, offs, m, lib=lib)
+    assert d.max() <= smax + 1e-9
+    # the e_max terminal condition, with a target the memory-limited run reached: the greedy
+    # picks are the same, so the e_max run stops no later and with max(S) <= target
+    segs_m, chosen_m, target = oracle.learn_dictionary(x, m, 1.5, "memory", 400, lib=lib)
+    segs, chosen, smax = oracle.learn_dictionary(x, m, 1.5, "emax", target, lib=lib)
+    assert smax <= target and len(chosen) <= len(chosen_m) and chosen == chosen_m[: len(chosen)]
+    d, _, _ = oracle.ab_join(x, np.concatenate([x[a : a + L] for a, L in segs]),
+                             np.concatenate(([0], np.cumsum([L for _, L in segs]))), m, lib=lib)
+    assert d.max() <= target + 1e-9
+
+
 ALL_PINS = (
     pin_brute_force,
     pin_closed_forms,
@@ -261,4 +353,6 @@ ALL_PINS = (
     pin_empty,
     pin_constant_rows,
     pin_correlation_output,
+    pin_self_join,
+    pin_learn_dictionary,
 )

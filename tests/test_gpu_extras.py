@@ -152,3 +152,54 @@ def test_streaming_join_equals_one_shot_join(mp):
         mp.mp_dict_free(ctx, d)
     finally:
         mp.mp_shutdown(ctx)
+
+
+def test_self_join_matches_oracle(mp):
+    """mp_self_join (Algorithm 1's P_B) against the oracle's self-join, constant windows included."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        m = 64
+        x = synthetic.random_walk(5000, 91).astype(np.float32)
+        x[2000:2200] = x[2000]      # a constant run: windows inside it are constant
+        x[3500:3580] = -4.0         # a second one, farther than the exclusion zone
+        excl = (m + 1) // 2
+        d, i = mp.mp_self_join(ctx, x, m, excl)
+        od, oi = oracle.self_join(x, m, excl)
+        assert np.all(np.abs(d - od) <= 1e-4)
+        g = np.arange(len(d))
+        assert np.all((i < 0) | (np.abs(i - g) >= excl)), "a trivial match was reported"
+        # where the oracle's pick is clearly best, the index must match
+        rows = np.random.default_rng(1).choice(len(d), 300, replace=False)
+        for r in rows:
+            if i[r] != oi[r]:
+                dg = oracle.pair_distance(x[r : r + m], x[i[r] : i[r] + m])
+                assert dg <= od[r] + 1e-4
+        # constant windows: 0 to another constant window outside the zone
+        cst = np.arange(2000, 2200 - m + 1)
+        assert np.all(d[cst] == 0.0) and np.all(np.abs(i[cst] - cst) >= excl)
+    finally:
+        mp.mp_shutdown(ctx)
+
+
+def test_learn_dictionary_matches_oracle(mp):
+    """Algorithm 1 on the GPU picks the same windows as the oracle and keeps its error bound."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        m = 64
+        x = synthetic.ecg_like(12000, 93).astype(np.float32)
+        segs, chosen, bound = mp.mp_learn_dictionary(ctx, x, m, 1.5, mp.MP_LEARN_MEMORY, 2000)
+        osegs, ochosen, obound = oracle.learn_dictionary(x, m, 1.5, "memory", 2000)
+        assert chosen == ochosen and segs == osegs
+        assert abs(bound - obound) <= 1e-3
+        # the learned dictionary's e_max (by the GPU join) is within the bound
+        samples = np.concatenate([x[a : a + L] for a, L in segs])
+        offs = np.concatenate(([0], np.cumsum([L for _, L in segs])))
+        d = mp.mp_dict_load(ctx, samples, offs, [m])
+        e_max, _ = mp.mp_emax(ctx, d, x, m)
+        assert e_max <= bound + 1e-3
+        mp.mp_dict_free(ctx, d)
+        # the e_max terminal condition
+        segs2, chosen2, bound2 = mp.mp_learn_dictionary(ctx, x, m, 1.5, mp.MP_LEARN_EMAX, bound)
+        assert bound2 <= bound + 1e-6 and chosen2 == chosen[: len(chosen2)]
+    finally:
+        mp.mp_shutdown(ctx)
