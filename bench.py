@@ -447,6 +447,58 @@ def study_dict_vs_orig(mp, k_discords=200, with_tf32=False):
     return out
 
 
+def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
+    """Algorithm 1 on the GPU for an ECG-like training series; streaming join throughput against the result."""
+    import oracle
+    import synthetic
+
+    x = synthetic.ecg_like(n_b, seed).astype(np.float32)
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    out = {"study": "dictionary learning (Algorithm 1) and streaming",
+           "workload": f"ECG-like training series of {n_b} samples (seed {seed}, normal beats), m={m}, context k=1.5, "
+                       f"memory budget {budget_frac:.0%} of the series"}
+    try:
+        nq = n_b - m + 1
+        t0 = time.perf_counter()
+        P, _ = mp.mp_self_join(ctx, x, m, (m + 1) // 2)
+        t_sj = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        segs, chosen, bound = mp.mp_learn_dictionary(ctx, x, m, 1.5, mp.MP_LEARN_MEMORY, budget_frac * n_b)
+        t_learn = time.perf_counter() - t0
+        samples = np.concatenate([x[a : a + L] for a, L in segs])
+        offs = np.concatenate(([0], np.cumsum([L for _, L in segs])))
+        d = mp.mp_dict_load(ctx, samples, offs, [m])
+        e_max, _ = mp.mp_emax(ctx, d, x, m)
+        # streaming: a fresh series arriving in appends of 1024 samples
+        q = synthetic.ecg_like(1 << 20, seed + 1, n_malformed=20).astype(np.float32)
+        st = mp.mp_stream_open(ctx, d, mp.MP_F32, m)
+        t0 = time.perf_counter()
+        n_win = 0
+        for a in range(0, len(q), 1024):
+            sd, _, _ = mp.mp_stream_append(st, q[a : a + 1024])
+            n_win += len(sd)
+        t_stream = time.perf_counter() - t0
+        mp.mp_stream_close(st)
+        n_w = mp.mp_dict_windows(d, m)
+        mp.mp_dict_free(ctx, d)
+        # the float64 oracle's Algorithm 1 on a 1/32 sample (the same loop, for context)
+        xs = x[: n_b // 32]
+        t0 = time.perf_counter()
+        oracle.learn_dictionary(xs, m, 1.5, "memory", budget_frac * len(xs))
+        t_or = time.perf_counter() - t0
+        out.update({
+            "self_join_s": t_sj, "self_join_pairs_per_s": nq * (nq - m) / t_sj,
+            "learn_s": t_learn, "iterations": len(chosen), "segments": len(segs),
+            "dictionary_samples": int(offs[-1]), "error_bound_max_S": bound, "e_max_of_learned_dictionary": e_max,
+            "profile_self_join_min_max": [float(np.min(P)), float(np.max(P))],
+            "stream_appends_of_1024": int((len(q) + 1023) // 1024), "stream_windows": n_win,
+            "stream_windows_per_s": n_win / t_stream, "stream_pairs_per_s": n_win * n_w / t_stream,
+            "oracle_learn_s_on_1_32": t_or, "oracle_cores": os.cpu_count()})
+    finally:
+        mp.mp_shutdown(ctx)
+    return out
+
+
 def study_serving(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256, window=64):
     """Continuous-batching serving: capacity, then Poisson load at fractions of it; p50/p99 latency."""
     import synthetic
@@ -545,7 +597,7 @@ def main():
     ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "auto"])
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", choices=["precision", "dict-vs-orig", "serving"], default=None,
+    ap.add_argument("--study", choices=["precision", "dict-vs-orig", "serving", "learn"], default=None,
                     help="run a study instead of the headline benchmark (one JSON line)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the query (profiling captures of a small case); 1.0 = the full workload")
@@ -578,6 +630,8 @@ def main():
             res = study_precision(mp)
         elif args.study == "serving":
             res = study_serving(mp)
+        elif args.study == "learn":
+            res = study_learn(mp)
         else:
             res = study_dict_vs_orig(mp, with_tf32=True)
         if rank == 0:
