@@ -36,6 +36,7 @@ struct Span {
 constexpr int kPlainRowsPerLane = 16;  // query windows owned by one lane
 constexpr int kPlainColBlock = 256;    // dictionary windows staged per block
 constexpr int kChunk = 16;             // windows per chunk of the lazy argmax
+static_assert(kChunk % 2 == 0, "the plain kernel folds the scores of two columns per maximum");
 
 // Per-window statistics of a series for one window length m (kernel K1).
 //   mean[i], invstd[i]   FP64 mean and 1/population-std (0 for a constant window)

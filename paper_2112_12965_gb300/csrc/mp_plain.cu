@@ -138,6 +138,17 @@ template <typename T, int kRows, bool kPacked> struct Rows {
 #pragma unroll
         for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fma(C[j], z, w));
     }
+    // two columns per 3-input maximum, as in the packed form below
+    __device__ __forceinline__ void score(T z, T w, T *q) const
+    {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) q[j] = fma(C[j], z, w);
+    }
+    __device__ __forceinline__ void score_max2(T z, T w, const T *q0, T *cm) const
+    {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) cm[j] = fmax(cm[j], fmax(q0[j], fma(C[j], z, w)));
+    }
     // the same, leaving out rows inside the column's exclusion zone
     // (|d0 - j| < excl, d0 = column window - the lane's first row)
     __device__ __forceinline__ void score_max_excl(T z, T w, T *cm, int d0, int excl) const
@@ -188,6 +199,22 @@ template <int kRows> struct Rows<float, kRows, true> {
             const float2 q = __ffma2_rn(C[k], Z, W);
             cm[k] = fmaxf(cm[k], q.x);
             cm[k + H] = fmaxf(cm[k + H], q.y);
+        }
+    }
+    // Two columns share one 3-input maximum per row: score() keeps the first
+    // column's scores in q, score_max2() folds them with the second's.
+    __device__ __forceinline__ void score(float2 Z, float2 W, float2 *q) const
+    {
+#pragma unroll
+        for (int k = 0; k < H; ++k) q[k] = __ffma2_rn(C[k], Z, W);
+    }
+    __device__ __forceinline__ void score_max2(float2 Z, float2 W, const float2 *q0, float *cm) const
+    {
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float2 q = __ffma2_rn(C[k], Z, W);
+            cm[k] = fmaxf(cm[k], fmaxf(q0[k].x, q.x));
+            cm[k + H] = fmaxf(cm[k + H], fmaxf(q0[k].y, q.y));
         }
     }
     __device__ __forceinline__ void score_max_excl(float2 Z, float2 W, float *cm, int d0, int excl) const
@@ -405,6 +432,39 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                 T cm[kRows];
 #pragma unroll
                 for (int j = 0; j < kRows; ++j) cm[j] = T(-INFINITY);
+                if constexpr (kPack && !kSelf) {
+                    // packed form: columns in pairs, one 3-input maximum per row and pair
+                    float2 q0[kRows / 2];
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u) {
+                        const int c = c0 + u;
+                        const float4 cxy = scs2[2 * c], czw = scs2[2 * c + 1];
+                        if (cb > 0 || c > 0) {
+                            const float up = __shfl_up_sync(0xffffffffu, R.last(), 1);
+                            R.step(make_float2(cxy.x, cxy.y), make_float2(cxy.z, cxy.w), up, lane == 0, stop_w[c]);
+                        }
+                        if ((u & 1) == 0)
+                            R.score(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), q0);
+                        else
+                            R.score_max2(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), q0, cm);
+                    }
+                } else if constexpr (!kPack && !kSelf && sizeof(T) == 4) {
+                    // scalar FP32 form (serving): the same pairing of columns
+                    T q0[kRows];
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u) {
+                        const int c = c0 + u;
+                        const vec4_t<T> cs = scs[c];
+                        if (cb > 0 || c > 0) {
+                            const T up = __shfl_up_sync(0xffffffffu, R.last(), 1);
+                            R.step(cs.x, cs.y, up, lane == 0, stop_w[c]);
+                        }
+                        if ((u & 1) == 0)
+                            R.score(cs.z, cs.w, q0);
+                        else
+                            R.score_max2(cs.z, cs.w, q0, cm);
+                    }
+                } else
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u) {
                     const int c = c0 + u;
