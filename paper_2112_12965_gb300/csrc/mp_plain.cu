@@ -21,18 +21,22 @@
 // increasing g. Moving one column to the right moves every diagonal one row
 // down, so each lane shifts its registers by one row and takes the top one
 // from the lane above with a warp shuffle. The first row of each warp has no
-// row above inside the warp: its value comes from a "top seed", a direct dot
-// product computed per column block. At the first column of each span (a run
-// of columns inside one segment) every row gets a "left seed", also a direct
-// dot product. Dictionary windows never cross a segment (Def. 8) because spans
-// never do. Each lane keeps the running maximum of q and the lowest g that
-// attains it for its rows; the partial result per (row, column group) is
-// reduced by the finalisation kernel.
+// row above inside the warp: its value comes from a "top seed", the centred
+// covariance of that row with the column's window. FP32 joins take the top
+// seeds from the tensor-core kernel K2s (a dense product, computed once per
+// join); the other forms compute them here as direct dot products per column
+// block. At the first column of each span (a run of columns inside one
+// segment) every row gets a "left seed", a direct dot product. Dictionary
+// windows never cross a segment (Def. 8) because spans never do. Each lane
+// keeps, for its rows, the running maximum of q per 16-column chunk and the
+// chunk that raised it (plus near-tie records); the partial result per (row,
+// column group) is reduced by the finalisation kernel, which re-scores the
+// chunk's windows.
 //
-// Seeds are computed on shifted samples (query minus a per-CTA constant,
+// Seeds computed here use shifted samples (query minus a per-CTA constant,
 // dictionary minus a per-block constant), which keeps the FP32 products small
 // for series with large offsets; the exact mean correction m * da * db is
-// applied afterwards from the FP64 means.
+// applied afterwards from the split means.
 #include <math.h>
 
 #include "mp_internal.cuh"

@@ -7,14 +7,22 @@
 //                 m, the cached window statistics (kernel K1), the spans of
 //                 valid windows (windows never cross a segment, Def. 8) and
 //                 the two special windows used by the constant-window rule.
-//   * join     -- K1 on the query, then the join form (plain K2 or tensor K3),
-//                 then K4 (reduction over column groups + exact distance of
-//                 the picked pair), all enqueued on one stream.
+//   * join     -- K1 on the query, then the join form (plain K2, with its top
+//                 seeds from the tensor-core kernel K2s for FP32 data, in row
+//                 chunks when the seed matrix would pass its cap; or the
+//                 tensor-core join K3), then K4 (reduction over column groups,
+//                 re-scoring of the winning and near-tied chunks, exact
+//                 distance of the picked pair), all enqueued on one stream.
 //   * serving  -- mp_submit queues a request; a scheduler thread admits
 //                 requests while slots and the memory budget allow, stages
 //                 them, and runs every admitted request's join work in one
 //                 persistent batched launch; completion is detected with
 //                 events, so batches overlap on the device.
+//   * more     -- the correlation form and the streaming join (on the same
+//                 join path), e_max and discords, the autotuner, the join
+//                 without device allocation, and dictionary learning
+//                 (Algorithm 1: the self-join form of K2/K4 plus the kernels
+//                 of mp_learn.cu).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
