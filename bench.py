@@ -37,6 +37,12 @@ L2_BYTES = 129 * 2**20
 # pair: 2 FMAs of the covariance recurrence, 1 FMA for the score, 1
 # compare-and-keep of the running maximum = 4 FP32-pipe lane instructions.
 PLAIN_OPS_PER_PAIR = 4
+# DRAM bytes of one k_plain launch on the full-size ECG workload (2^20 query
+# samples, 64 x 1024 dictionary, m = 256), from one single-pass ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum: 455.95 MB read (mostly the
+# 403 MB top-seed matrix) and 160.92 MB written (partials and near-tie
+# records). Valid for this kernel build and workload only.
+PLAIN_DRAM_BYTES_FULL = 455.95e6 + 160.92e6
 SMS, LANES_PER_SM = 152, 128
 
 
@@ -189,14 +195,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def roofline(kname, pairs, m, join_ms, peaks, peak_src):
-    """Roofline of the join kernel: ALU-issue bound (plain) or tensor bound (tcgen05)."""
+def roofline(kname, pairs, m, join_ms, peaks, peak_src, full_size=False):
+    """Roofline of the join kernel: ALU-issue bound (plain) or tensor bound (tcgen05).
+
+    `traffic` (DRAM bytes per launch, from ncu) is known for the plain kernel on
+    the full-size workload only; null otherwise."""
     if kname == "plain":
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-instructions/s
         achieved = pairs * PLAIN_OPS_PER_PAIR / (join_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": None, "kernel": "k_plain",
+                "frac": achieved / peak_ops, "traffic": PLAIN_DRAM_BYTES_FULL if full_size else None,
+                "kernel": "k_plain",
                 "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)",
                 "ops_per_pair": PLAIN_OPS_PER_PAIR}
     tflops_peak = peaks.get("bf16_tflops", 1900.0)
@@ -662,7 +672,7 @@ def main():
     peaks, peak_src = load_peaks()
     join_ms = phase_ms[mp.MP_PHASE_JOIN] / max(1, phase_n[mp.MP_PHASE_JOIN])
     clock = clk.summary()
-    roof = roofline(args.kernel, pairs, w.m, join_ms, peaks, peak_src)
+    roof = roofline(args.kernel, pairs, w.m, join_ms, peaks, peak_src, full_size=args.scale == 1.0)
     # the other join forms on the same workload (same timing method)
     kernels = {}
     for kname in ("plain", "bf16x3", "tf32"):

@@ -16,7 +16,9 @@
 //      sqrt(sum_k (z_a[k] - z_b[k])^2), so the reported value carries no
 //      error from the recurrence or the tensor-core products, only from the
 //      choice of the pair.
-// One warp per query window.
+// For m <= 512 (k_finalize_blk) a CTA takes blocks of consecutive query
+// windows: steps 1 and 3 run one thread per window, step 2 one warp per
+// window; for longer windows (k_finalize) one warp takes each window.
 #include <math.h>
 
 #include "mp_internal.cuh"
@@ -292,50 +294,71 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
 }
 
 // ---------------------------------------------------------------------------
-// Single-pass form for m <= kFinMaxM. Per query window the warp stages the
-// window once; per candidate chunk it stages the chunk's samples; the chosen
-// pair's distance is computed from the staged samples. Lane lg of half-warp
-// h sums k in [lg * kpl, (lg + 1) * kpl) for candidates 8h .. 8h + 7, with
-// kpl a multiple of 8 and both buffers zero-filled past their data, so the
+// Block form for m <= kFinMaxM. A CTA takes kFinBlock = 32 * fin_warps<T>()
+// consecutive query windows at a time, in three phases:
+//   1. one thread per window: the reduction of the column groups' partials,
+//      the near-tie candidates, the constant-window cases and the window's
+//      statistics, with loads that are coalesced across the block and no
+//      per-window shuffles; the results go to shared memory;
+//   2. one warp per window (each warp takes 32 of the block's windows): the
+//      re-scoring of the winning chunk and of the candidates, and the chosen
+//      pair's distance from the staged samples;
+//   3. one thread per window again: the constant-window rule and the output.
+// In phase 2 lane lg of half-warp h sums k in [lg * KPL, (lg + 1) * KPL) for
+// candidates 8h .. 8h + 7, with KPL a multiple of 8 (compile-time, so that
+// every loop unrolls) and both buffers zero-filled past their data, so the
 // inner loop runs in unmasked steps of 8. Shared memory is padded by one
 // value per 32 (qidx): a run of 8 starting at a multiple of 8 never crosses a
-// pad, and the lanes' start offsets fall in distinct banks for kpl = 8, 16, 32.
+// pad, and the lanes' start offsets fall in distinct banks for KPL = 8 .. 32.
 // ---------------------------------------------------------------------------
 constexpr int kFinMaxM = 512;
-// warps per CTA: two double buffers per warp stay within 48 KB of static shared memory
+// warps per CTA: the per-warp buffers stay within 48 KB of static shared memory
 template <typename T> constexpr int fin_warps() { return sizeof(T) == 8 ? 2 : 4; }
 __device__ __forceinline__ int qidx(int e) { return e + (e >> 5); }
-constexpr int kFinQVals = kFinMaxM + kFinMaxM / 32 + 1;                           // 16 * kpl <= 512 values
-constexpr int kFinBVals = (kFinMaxM + kChunk) + (kFinMaxM + kChunk) / 32 + 1;  // plus kChunk
+// near-tie candidates kept per window in shared memory; a window with more
+// scans the column groups' records again in phase 2
+constexpr int kFinMaxCand = 4;
 
 __host__ __device__ constexpr int fin_kpl(int m) { return ((m + 15) / 16 + 7) / 8 * 8; }
 
 // Stage chunk g's samples b[g ..] - mean_hi(b_g) into wb (zero past the
 // dictionary), for every value the lanes of rescore_staged read.
-template <typename T>
-__device__ __forceinline__ void stage_chunk(const T *__restrict__ pb, int64_t nb, int nbv,
-                                            const Split<T> *__restrict__ ms_b, int32_t g, int lane, T *wb)
+template <typename T, int KPL>
+__device__ __forceinline__ void stage_chunk(const T *__restrict__ pb, int64_t nb, const Split<T> *__restrict__ ms_b,
+                                            int32_t g, int lane, T *wb)
 {
+    constexpr int NBV = 16 * KPL + kChunk;
     __syncwarp();  // earlier reads of wb are done
     const T sb = ms_b[g].hi;
     const T *bg = pb + g;
-    const int lim = nb - g < nbv ? (int)(nb - g) : nbv;
-    for (int e = lane; e < nbv; e += 32) wb[qidx(e)] = e < lim ? bg[e] - sb : T(0);
+    // value e = lane + 32 u sits at qidx(e) = lane + 33 u
+    if (g + NBV <= nb) {
+#pragma unroll
+        for (int u = 0; u < (NBV + 31) / 32; ++u)
+            if (32 * (u + 1) <= NBV || lane + 32 * u < NBV) wb[lane + 33 * u] = bg[lane + 32 * u] - sb;
+    } else {  // the chunk's samples run past the dictionary: zeros there
+        const int64_t lim = nb - g;
+#pragma unroll
+        for (int u = 0; u < (NBV + 31) / 32; ++u) {
+            const int e = lane + 32 * u;
+            if (e < NBV) wb[lane + 33 * u] = e < lim ? bg[e] - sb : T(0);
+        }
+    }
     __syncwarp();
 }
 
 // Re-score chunk g against the staged query window qa (= a - mean_hi(a)) and
 // the staged chunk wb (= b - mean_hi(b_g)); returns the chunk's best (score,
 // window) in every lane as rescore_chunk.
-template <typename T>
-__device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, const Split<T> *__restrict__ ms_b,
+template <typename T, int KPL>
+__device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const Split<T> *__restrict__ ms_b,
                                                const vec4_t<T> *__restrict__ rs_b, const T *qa, T da, int32_t g,
                                                int lane, const T *wb, T &sc_out, int32_t &g_out, int64_t i,
                                                int excl)
 {
     const T sb = ms_b[g].hi;
     const int half = lane >> 4, lg = lane & 15;
-    const int k0 = lg * kpl;
+    const int k0 = lg * KPL;
     T acc[8], bw[8];
     {
         const T *b0 = wb + qidx(8 * half + k0);
@@ -345,9 +368,10 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, c
             bw[c] = b0[c];
         }
     }
-    for (int kb = k0; kb < k0 + kpl; kb += 8) {
-        const T *qp = qa + qidx(kb);
-        const T *bp = wb + qidx(8 * half + kb + 8);
+#pragma unroll
+    for (int kb = 0; kb < KPL; kb += 8) {
+        const T *qp = qa + qidx(k0 + kb);
+        const T *bp = wb + qidx(8 * half + k0 + kb + 8);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const T av = qp[u];
@@ -367,23 +391,19 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, c
         }
     }
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 8);
+    // lanes l and l ^ 8 now hold the same candidate's total
     const int cand = 8 * half + (lane & 7);
     const int64_t gc = (int64_t)g + cand;
-    bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl));
-    vec4_t<T> rv;
-    if (ok) {
-        rv = rs_b[gc];
-        ok = rv.w == T(0);
-    }
-    T sc = T(-INFINITY);
-    if (ok) {
-        // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
-        const Split<T> mb = ms_b[gc];
-        sc = (acc[0] - T(m) * da * ((mb.hi - sb) + mb.lo)) * rv.z;
-    }
+    const int64_t gcl = gc < npos_b ? gc : npos_b - 1;  // in range, so the loads need no branch
+    const vec4_t<T> rv = rs_b[gcl];
+    const Split<T> mb = ms_b[gcl];
+    const bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl)) && rv.w == T(0);
+    // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
+    T sc = ok ? (acc[0] - T(m) * da * ((mb.hi - sb) + mb.lo)) * rv.z : T(-INFINITY);
     int32_t gw = ok ? (int32_t)gc : -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
+        if (o == 8) continue;  // the same candidate
         const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
         const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
         if (better(s2, g2, sc, gw)) {
@@ -395,53 +415,46 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, int kpl, c
     g_out = gw;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k_finalize_rows(FinalizeParams<T> p)
+template <typename T, int KPL>
+__global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k_finalize_blk(FinalizeParams<T> p)
 {
-    constexpr int kFinWarps = fin_warps<T>();
-    __shared__ T fr_smem[kFinWarps][kFinQVals + kFinBVals];
-    const int lane = threadIdx.x & 31;
-    T *const qa = fr_smem[threadIdx.x >> 5];
-    T *const wb = qa + kFinQVals;
-    const int64_t warp_global = (int64_t)blockIdx.x * kFinWarps + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * kFinWarps;
+    constexpr int kW = fin_warps<T>();
+    constexpr int kNB = 32 * kW;                                   // query windows per block
+    constexpr int kQV = 16 * KPL + (16 * KPL) / 32 + 1;             // staged query window
+    constexpr int kBV = (16 * KPL + kChunk) + (16 * KPL + kChunk) / 32 + 1;  // staged chunk
+    __shared__ T f_buf[kW][kQV + kBV];
+    __shared__ int32_t s_g[kNB];                 // winning chunk to re-score, -1: none
+    __shared__ int32_t s_nc[kNB];                // near-tie candidates found
+    __shared__ int32_t s_cand[kFinMaxCand][kNB];
+    __shared__ int32_t s_gi[kNB];                // phase 2's window (-1: none)
+    __shared__ T s_mhi[kNB], s_mlo[kNB], s_isa[kNB], s_lim[kNB], s_d[kNB];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T *const qa = f_buf[warp];
+    T *const wb = qa + kQV;
     const int m = p.m;
-    const int kpl = fin_kpl(m);
-    const int nbv = 16 * kpl + kChunk;
     const double sqrt_m = sqrt((double)m);
     if (p.err != nullptr && *p.err != 0) {
         // a bounded wait of a tensor-core kernel ran out: the partials are incomplete
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nq; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < p.nq; i += (int64_t)gridDim.x * blockDim.x) {
             p.out_dist[i] = NAN;
             p.out_idx[i] = -1;
         }
         return;
     }
-    for (int64_t i = warp_global; i < p.nq; i += nwarps) {
-        // 1. reduce the column groups: largest q, then lowest chunk start
-        T q = T(-INFINITY);
-        int32_t g = -1;
-        for (int k = lane; k < p.n_groups; k += 32) {
-            const Partial<T> v = p.part[(int64_t)k * p.nq + i];
-            if (better(v.q, v.g, q, g)) {
-                q = v.q;
-                g = v.g;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const T q2 = __shfl_xor_sync(0xffffffffu, q, o);
-            const int32_t g2 = __shfl_xor_sync(0xffffffffu, g, o);
-            if (better(q2, g2, q, g)) {
-                q = q2;
-                g = g2;
-            }
-        }
+    const int64_t nblk = (p.nq + kNB - 1) / kNB;
+    for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const int64_t i0 = blk * kNB;
+        const int64_t i = i0 + tid;
+        // ---- phase 1: this thread's window ----
         double d = INFINITY;
-        int64_t gi = -1;
-        if (p.g_first >= 0) {
+        int64_t gi = -1, gcst = -1;
+        int32_t g = -1;
+        int nc = 0;
+        bool resc = false;  // phase 2 re-scores this window
+        if (i < p.nq && p.g_first >= 0) {
             if (p.cflag_a[i]) {
-                // 3. a constant query window is 0 from a constant window, sqrt(m) from the rest
+                // a constant query window is 0 from a constant window, sqrt(m) from the rest
                 const int64_t gc = const_outside(p, i), gf = first_outside(p, i);
                 if (gc >= 0) {
                     d = 0.0;
@@ -451,88 +464,182 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
                     gi = gf;
                 }
             } else {
+                // the column groups: largest q, then lowest chunk start
+                T q = T(-INFINITY);
+#pragma unroll 4
+                for (int k = 0; k < p.n_groups; ++k) {
+                    const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+                    if (better(v.q, v.g, q, g)) {
+                        q = v.q;
+                        g = v.g;
+                    }
+                }
+                gcst = const_outside(p, i);
                 if (g >= 0) {
-                    // 2. stage the query window, re-score the winning chunk and the near-tied ones
+                    resc = true;
                     const Split<T> ma = p.ms_a[i];
-                    const T *ai = p.a + i;
-                    for (int e = lane; e < 16 * kpl; e += 32) qa[qidx(e)] = e < m ? ai[e] - ma.hi : T(0);
-                    stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, g, lane, wb);
-                    T sc;
-                    int32_t gw;
-                    rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, g, lane, wb, sc, gw, i, p.excl);
-                    int32_t staged = g;  // the chunk whose samples wb holds
-                    int32_t win = g;     // the chunk of the best window so far
+                    const T isa = p.rs_a[i].z;  // the row is not constant: isa > 0
+                    s_mhi[tid] = ma.hi;
+                    s_mlo[tid] = ma.lo;
+                    s_isa[tid] = isa;
                     if (p.near != nullptr) {
-                        const T lim = q - T(kNearTieRho) * T(m) / p.rs_a[i].z;  // the row is not constant
-                        for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
-                            const int k = k0 + lane;
-                            int32_t c0 = -1, c1 = -1, c2 = -1;
-                            if (k < p.n_groups) {
-                                const Partial<T> v = p.part[(int64_t)k * p.nq + i];
-                                if (v.g >= 0 && v.g != g && v.q >= lim) c0 = v.g;
-                                const NearTies nt = p.near[(int64_t)k * p.nq + i];
-                                if (nt.g0 >= 0 && nt.g0 != g && T(nt.q0) >= lim) c1 = nt.g0;
-                                if (nt.g1 >= 0 && nt.g1 != g && T(nt.q1) >= lim) c2 = nt.g1;
-                            }
-                            unsigned pend = __ballot_sync(0xffffffffu, c0 >= 0 || c1 >= 0 || c2 >= 0);
-                            while (pend) {
-                                const int src = __ffs(pend) - 1;
-                                pend &= pend - 1;
-                                const int32_t s0 = __shfl_sync(0xffffffffu, c0, src);
-                                const int32_t s1 = __shfl_sync(0xffffffffu, c1, src);
-                                const int32_t s2c = __shfl_sync(0xffffffffu, c2, src);
-#pragma unroll 1
-                                for (int u = 0; u < 3; ++u) {
-                                    const int32_t cu = u == 0 ? s0 : (u == 1 ? s1 : s2c);
-                                    if (cu < 0) continue;
-                                    T s2;
-                                    int32_t g2;
-                                    stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, cu, lane, wb);
-                                    rescore_staged<T>(p.npos_b, m, kpl, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2,
-                                                      g2, i, p.excl);
-                                    staged = cu;
-                                    if (better(s2, g2, sc, gw)) {
-                                        sc = s2;
-                                        gw = g2;
-                                        win = cu;
-                                    }
+                        // every other chunk whose approximate score came within the
+                        // near-tie width of the best (other groups' winners and the
+                        // plain kernel's near-tie records) is re-scored too, so that
+                        // the recurrence's rounding cannot decide between near ties
+                        const T lim = q - T(kNearTieRho) * T(m) / isa;
+                        s_lim[tid] = lim;
+#pragma unroll 2
+                        for (int k = 0; k < p.n_groups; ++k) {
+                            const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+                            const NearTies nt = p.near[(int64_t)k * p.nq + i];
+                            const int32_t c3[3] = {v.g >= 0 && v.g != g && v.q >= lim ? v.g : -1,
+                                                   nt.g0 >= 0 && nt.g0 != g && T(nt.q0) >= lim ? nt.g0 : -1,
+                                                   nt.g1 >= 0 && nt.g1 != g && T(nt.q1) >= lim ? nt.g1 : -1};
+#pragma unroll
+                            for (int u = 0; u < 3; ++u) {
+                                if (c3[u] >= 0) {
+                                    if (nc < kFinMaxCand) s_cand[nc][tid] = c3[u];
+                                    ++nc;
                                 }
                             }
                         }
                     }
-                    if (gw >= 0) {
-                        // 4. the chosen pair's distance from its definition, on the staged samples
-                        if (staged != win) stage_chunk<T>(p.b, p.nb, nbv, p.ms_b, win, lane, wb);
-                        const Split<T> mb = p.ms_b[gw];
-                        const T db = (mb.hi - p.ms_b[win].hi) + mb.lo;  // wb holds b - mean_hi(win)
-                        const T is_a = p.rs_a[i].z, is_b = p.rs_b[gw].z;
-                        const int o = gw - win;
-                        T acc = T(0);
-                        for (int k = lane; k < m; k += 32) {
-                            const T za = (qa[qidx(k)] - ma.lo) * is_a;
-                            const T zb = (wb[qidx(o + k)] - db) * is_b;
-                            const T dd = za - zb;
-                            acc = fma(dd, dd, acc);
-                        }
-#pragma unroll
-                        for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
-                        d = (double)sqrt(acc);
-                        gi = gw;
-                    }
-                    __syncwarp();  // the next row rewrites qa and wb
-                }
-                const int64_t gcst = const_outside(p, i);
-                if (gcst >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && gcst < gi))) {
-                    d = sqrt_m;
-                    gi = gcst;
                 }
             }
         }
-        if (lane == 0) {
+        s_g[tid] = resc ? g : -1;
+        s_nc[tid] = nc;
+        __syncthreads();
+
+        // ---- phase 2: this warp's 32 windows, one at a time ----
+        for (int w = 0; w < 32; ++w) {
+            const int t = warp * 32 + w;
+            const int32_t g0 = s_g[t];
+            if (g0 < 0) continue;
+            const int64_t iw = i0 + t;
+            const Split<T> ma{s_mhi[t], s_mlo[t]};
+            const T *ai = p.a + iw;
+#pragma unroll
+            for (int u = 0; u < KPL / 2; ++u) {  // 16 * KPL values over 32 lanes; qidx(lane + 32 u) = lane + 33 u
+                const int e = lane + 32 * u;
+                qa[lane + 33 * u] = e < m ? ai[e] - ma.hi : T(0);
+            }
+            stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, g0, lane, wb);
+            T sc;
+            int32_t gw;
+            rescore_staged<T, KPL>(p.npos_b, m, p.ms_b, p.rs_b, qa, ma.lo, g0, lane, wb, sc, gw, iw, p.excl);
+            int32_t staged = g0;  // the chunk whose samples wb holds
+            int32_t win = g0;     // the chunk of the best window so far
+            const int ncw = s_nc[t];
+            if (ncw > 0 && ncw <= kFinMaxCand) {
+                for (int c = 0; c < ncw; ++c) {
+                    const int32_t cu = s_cand[c][t];
+                    T s2;
+                    int32_t g2;
+                    stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
+                    rescore_staged<T, KPL>(p.npos_b, m, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
+                    staged = cu;
+                    if (better(s2, g2, sc, gw)) {
+                        sc = s2;
+                        gw = g2;
+                        win = cu;
+                    }
+                }
+            } else if (ncw > kFinMaxCand) {
+                // more candidates than the shared list holds: scan the records again
+                const T lim = s_lim[t];
+                for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
+                    const int k = k0 + lane;
+                    int32_t c0 = -1, c1 = -1, c2 = -1;
+                    if (k < p.n_groups) {
+                        const Partial<T> v = p.part[(int64_t)k * p.nq + iw];
+                        if (v.g >= 0 && v.g != g0 && v.q >= lim) c0 = v.g;
+                        const NearTies nt = p.near[(int64_t)k * p.nq + iw];
+                        if (nt.g0 >= 0 && nt.g0 != g0 && T(nt.q0) >= lim) c1 = nt.g0;
+                        if (nt.g1 >= 0 && nt.g1 != g0 && T(nt.q1) >= lim) c2 = nt.g1;
+                    }
+                    unsigned pend = __ballot_sync(0xffffffffu, c0 >= 0 || c1 >= 0 || c2 >= 0);
+                    while (pend) {
+                        const int src = __ffs(pend) - 1;
+                        pend &= pend - 1;
+                        const int32_t s0 = __shfl_sync(0xffffffffu, c0, src);
+                        const int32_t s1 = __shfl_sync(0xffffffffu, c1, src);
+                        const int32_t s2c = __shfl_sync(0xffffffffu, c2, src);
+#pragma unroll 1
+                        for (int u = 0; u < 3; ++u) {
+                            const int32_t cu = u == 0 ? s0 : (u == 1 ? s1 : s2c);
+                            if (cu < 0) continue;
+                            T s2;
+                            int32_t g2;
+                            stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
+                            rescore_staged<T, KPL>(p.npos_b, m, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2, g2, iw,
+                                                   p.excl);
+                            staged = cu;
+                            if (better(s2, g2, sc, gw)) {
+                                sc = s2;
+                                gw = g2;
+                                win = cu;
+                            }
+                        }
+                    }
+                }
+            }
+            T dw = T(INFINITY);
+            if (gw >= 0) {
+                // the chosen pair's distance from its definition, on the staged samples
+                if (staged != win) stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, win, lane, wb);
+                const Split<T> mb = p.ms_b[gw];
+                const T db = (mb.hi - p.ms_b[win].hi) + mb.lo;  // wb holds b - mean_hi(win)
+                const T is_a = s_isa[t], is_b = p.rs_b[gw].z;
+                // z_a - z_b = (qa - lo_a) is_a - (wb - db) is_b: each difference is
+                // taken before its scaling, so no large term is rounded (db, the
+                // mean difference within the chunk, can be far above the spread)
+                const T *wo = wb + qidx(gw - win + lane);  // value gw - win + lane + 32 u sits at wo[33 u]
+                T acc = T(0);
+#pragma unroll
+                for (int u = 0; u < KPL / 2; ++u) {
+                    if (lane + 32 * u < m) {
+                        const T dd = fma(qa[lane + 33 * u] - ma.lo, is_a, -((wo[33 * u] - db) * is_b));
+                        acc = fma(dd, dd, acc);
+                    }
+                }
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+                dw = sqrt(acc);
+            }
+            if (lane == 0) {
+                s_d[t] = dw;
+                s_gi[t] = gw;
+            }
+            __syncwarp();  // the next window rewrites qa and wb
+        }
+        __syncthreads();
+
+        // ---- phase 3: this thread's window ----
+        if (i < p.nq) {
+            if (resc) {
+                d = (double)s_d[tid];
+                gi = s_gi[tid];
+            }
+            if (gcst >= 0 && (gi < 0 || sqrt_m < d || (sqrt_m == d && gcst < gi))) {
+                d = sqrt_m;
+                gi = gcst;
+            }
             p.out_dist[i] = p.out_corr ? (gi >= 0 ? 1.0 - d * d / (2.0 * m) : -INFINITY) : d;
             p.out_idx[i] = gi;
         }
+        __syncthreads();  // the next block rewrites the per-window arrays
     }
+}
+
+template <typename T, int KPL> cudaError_t launch_blk(const FinalizeParams<T> &p, cudaStream_t st)
+{
+    constexpr int kNB = 32 * fin_warps<T>();
+    int64_t grid = (p.nq + kNB - 1) / kNB;  // one block of query windows per CTA and pass
+    if (grid > 152 * 64) grid = 152 * 64;
+    k_finalize_blk<T, KPL><<<(unsigned)grid, kNB, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -542,11 +649,12 @@ cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st)
 {
     if (p.nq <= 0) return cudaSuccess;
     if (p.m <= kFinMaxM) {
-        constexpr int W = fin_warps<T>();
-        int64_t grid = (p.nq + W - 1) / W;  // one query window per warp and pass
-        if (grid > 152 * 32) grid = 152 * 32;
-        k_finalize_rows<T><<<(unsigned)grid, 32 * W, 0, st>>>(p);
-        return cudaGetLastError();
+        switch (fin_kpl(p.m)) {
+        case 8: return launch_blk<T, 8>(p, st);
+        case 16: return launch_blk<T, 16>(p, st);
+        case 24: return launch_blk<T, 24>(p, st);
+        default: return launch_blk<T, 32>(p, st);
+        }
     }
     int64_t grid = (p.nq + 7) / 8;  // 8 warps (rows) per CTA
     if (grid > 152 * 64) grid = 152 * 64;

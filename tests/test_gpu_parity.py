@@ -238,6 +238,24 @@ def test_near_ties_all_rows(mp, ctx, k):
     parity.check(dist, idx, q, b, offs, m, atol=1e-4, oracle_out=(od, oi, od2))
 
 
+def test_repeated_segments_rescore_every_tied_chunk(mp, ctx):
+    """A dictionary of 16 exact copies of one segment: each row's best window
+    ties in every copy, so the column groups hand the finalisation many
+    near-tie candidates per row (more than it keeps per window in shared
+    memory, which sends it back to the records). Every row's distance must
+    still match the oracle's, and the chosen window must be at that distance.
+    """
+    m = 64
+    seg = synthetic.ecg_like(301, 91).astype(np.float32)
+    b = np.tile(seg, 16)
+    offs = (np.arange(17) * 301).astype(np.int64)
+    q = synthetic.ecg_like(3000, 92).astype(np.float32)
+    dist, idx = join(mp, ctx, q, b, offs, m)
+    od, oi, od2 = oracle.ab_join(q, b, offs, m)
+    assert np.all(od2 - od < 1e-9), "every best window must tie with its copies"
+    parity.check(dist, idx, q, b, offs, m, atol=1e-4, oracle_out=(od, oi, od2))
+
+
 def test_drifting_offset_series_all_rows(mp, ctx):
     """Large offsets and drift: the seeds' centring must keep FP32 products small.
 
