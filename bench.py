@@ -146,12 +146,13 @@ def cpu_baseline(w, target_s: float = 15.0):
 
     oracle.build()
     nq = w.n_rows
-    # calibrate on a few rows, then size the sample for ~target_s seconds
-    rows = np.arange(0, nq, nq // 16)[:16]
+    # calibrate on 256 rows (about 0.3 s, enough to amortise the oracle's start-up),
+    # then size the sample for ~target_s seconds
+    rows = np.arange(0, nq, max(1, nq // 256))[:256]
     t0 = time.perf_counter()
     oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)
     dt = time.perf_counter() - t0
-    n_rows = int(max(16, min(nq, len(rows) * target_s / max(dt, 1e-6))))
+    n_rows = int(max(256, min(nq, len(rows) * target_s / max(dt, 1e-6))))
     rows = np.linspace(0, nq - 1, n_rows).astype(np.int64)
     t0 = time.perf_counter()
     oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)

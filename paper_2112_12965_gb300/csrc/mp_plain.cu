@@ -538,8 +538,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 }
 
 // Four CTAs (16 warps) per SM for FP32 data: the kernel then fits in 128
-// registers without spilling, and the extra warps hide the shuffle and
-// shared-memory latencies of the recurrence.
+// registers (with a few tens of bytes spilled), and the extra warps hide the
+// shuffle and shared-memory latencies of the recurrence.
 template <typename T, int kRows, bool kSeeds, bool kNear, bool kSelf = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_plain(PlainParams<T> p)
 {

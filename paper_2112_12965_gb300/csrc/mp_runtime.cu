@@ -252,18 +252,31 @@ struct PhaseTimer {
 // ---------------------------------------------------------------------------
 static int dtype_size(int32_t dtype) { return dtype == MP_F64 ? 8 : 4; }
 
-static bool host_all_finite(const void *x, int32_t dtype, int64_t n)
+// No NaN or Inf among n samples: a value is non-finite exactly when its
+// exponent bits are all ones. Branch-free within blocks of 4096 values so
+// that the compiler vectorises the test; one exit test per block.
+template <typename U>
+static bool all_exponents_finite(const unsigned char *x, int64_t n, U exp_mask)
 {
-    if (dtype == MP_F64) {
-        const double *p = (const double *)x;
-        for (int64_t i = 0; i < n; ++i)
-            if (!isfinite(p[i])) return false;
-    } else {
-        const float *p = (const float *)x;
-        for (int64_t i = 0; i < n; ++i)
-            if (!isfinite(p[i])) return false;
+    constexpr int64_t kBlock = 4096;
+    for (int64_t i0 = 0; i0 < n; i0 += kBlock) {
+        const int64_t i1 = std::min(n, i0 + kBlock);
+        U bad = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            U u;
+            memcpy(&u, x + i * sizeof(U), sizeof(U));
+            bad |= (U)((u & exp_mask) == exp_mask);
+        }
+        if (bad) return false;
     }
     return true;
+}
+
+static bool host_all_finite(const void *x, int32_t dtype, int64_t n)
+{
+    const unsigned char *p = (const unsigned char *)x;
+    if (dtype == MP_F64) return all_exponents_finite<uint64_t>(p, n, 0x7ff0000000000000ull);
+    return all_exponents_finite<uint32_t>(p, n, 0x7f800000u);
 }
 
 static int check_join_args(mp_ctx *ctx, const mp_dict *dict, const void *q, int32_t dtype, int64_t n, int32_t m)
@@ -1248,7 +1261,6 @@ static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int
     int rc = check_join_args(ctx, dict, query, dtype, n, m);
     if (rc) return rc;
     if (!out_dist || !out_idx) return fail(MP_E_ARG, "null output");
-    if (!host_all_finite(query, dtype, n)) return fail(MP_E_ARG, "query has NaN or Inf samples");
     CUDA_TRY(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lk(ctx->mu);
     mp_dict *d = const_cast<mp_dict *>(dict);
@@ -1257,6 +1269,7 @@ static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int
     if (rc) return rc;
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) {
+        if (!host_all_finite(query, dtype, n)) return fail(MP_E_ARG, "query has NaN or Inf samples");
         for (int64_t i = 0; i < nq; ++i) {
             out_dist[i] = corr ? -INFINITY : INFINITY;
             out_idx[i] = -1;
@@ -1277,6 +1290,14 @@ static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int
     rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes,
                      resolve_kernel(ctx, dtype, m, s, nq), true, corr);
     if (rc) return rc;
+    // The query is checked for NaN and Inf here, while the device joins it.
+    // A join of such samples is wasted but harmless: the kernels take every
+    // index from the launch geometry or from valid chunks, never from sample
+    // values. Nothing is copied out unless the check passes.
+    if (!host_all_finite(query, dtype, n)) {
+        cudaStreamSynchronize(st);
+        return fail(MP_E_ARG, "query has NaN or Inf samples");
+    }
     CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
     // the error word of the tensor-core kernels (zeroed by join_device)

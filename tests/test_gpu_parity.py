@@ -184,6 +184,13 @@ def test_argument_errors(mp, ctx):
         with pytest.raises(mp.MPError) as e:
             mp.mp_ab_join(ctx, d, qn, 32)
         assert e.value.code == mp.MP_E_ARG
+        # through the C call: the caller's outputs stay untouched, the context stays usable
+        nq = len(qn) - 32 + 1
+        od, oi = np.full(nq, 7.0), np.full(nq, 7, dtype=np.int64)
+        rc = mp.lib.mp_ab_join(ctx, d, qn.ctypes.data, mp.MP_F32, len(qn), 32, od.ctypes.data, oi.ctypes.data)
+        assert rc == mp.MP_E_ARG and np.all(od == 7.0) and np.all(oi == 7)
+        dist, idx = mp.mp_ab_join(ctx, d, q, 32)
+        assert np.all(idx >= 0) and np.all(np.isfinite(dist))
         with pytest.raises(mp.MPError) as e:
             mp.mp_ab_join(ctx, d, q.astype(np.float64), 32)
         assert e.value.code == mp.MP_E_ARG
