@@ -76,11 +76,50 @@ def test_fp32_ecg_full_size_sampled_rows(mp, ctx):
     assert np.all((idx >= 0) & (idx < len(w.dict_samples)))
 
 
-def test_transport_m512_sampled_rows(mp, ctx):
-    w = synthetic.workload("transport_4m_m512", scale=0.25)
+def _sampled_rows(dist, n_random, seed, n_top=0, n_ends=16):
+    """Random rows, the first and last rows, and the rows of the n_top largest distances."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.choice(len(dist), n_random, replace=False), np.arange(0, n_ends),
+             np.arange(len(dist) - n_ends, len(dist))]
+    if n_top:
+        parts.append(np.argsort(dist)[-n_top:])
+    return np.unique(np.concatenate(parts))
+
+
+def test_transport_m512_full_size_sampled_rows(mp, ctx):
+    """Transportation-like query of 2^22 samples against 256 x 2048 segments, m = 512, at full size."""
+    w = synthetic.workload("transport_4m_m512")
     dist, idx = join(mp, ctx, w.query, w.dict_samples, w.offsets, w.m)
-    rows = np.random.default_rng(1).choice(len(dist), 192, replace=False)
+    assert len(dist) == (1 << 22) - 512 + 1
+    rows = _sampled_rows(dist, 160, 1, n_top=8)
     parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, rows=rows, atol=1e-4)
+    assert np.all((dist >= 0) & (dist <= 2 * math.sqrt(w.m) + 1e-9))
+
+
+def test_ecg_m1024_dictionary_full_size_sampled_rows(mp, ctx):
+    """ECG-like query of 2^24 samples (200 planted malformed beats) against 128 x 2048 segments cut from a
+    normal-beat training series, m = 1024, at full size. Windows longer than 512 take the per-pass
+    finalisation, and the top-seed matrix (17 GB at once) is built in row chunks. The rows of the 20 largest
+    distances are planted beats."""
+    w = synthetic.workload("ecg_16m_m1024_dict")
+    dist, idx = join(mp, ctx, w.query, w.dict_samples, w.offsets, w.m)
+    assert len(dist) == (1 << 24) - 1024 + 1
+    rows = _sampled_rows(dist, 96, 2, n_top=20, n_ends=8)
+    parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, rows=rows, atol=1e-4)
+    assert np.all((dist >= 0) & (dist <= 2 * math.sqrt(w.m) + 1e-9))
+
+
+def test_ecg_m1024_original_series_and_lemma_1(mp, ctx):
+    """A quarter-size query (2^22 samples) against the whole training series as one segment (2^20 samples,
+    m = 1024): sampled rows against the oracle, and Lemma 1 (the join against the dictionary cut from that
+    series never undercuts the join against the series) on every row."""
+    wo = synthetic.workload("ecg_16m_m1024_orig", scale=0.25)
+    wd = synthetic.workload("ecg_16m_m1024_dict", scale=0.25)
+    p_orig, i_orig = join(mp, ctx, wo.query, wo.dict_samples, wo.offsets, wo.m)
+    p_dict, _ = join(mp, ctx, wd.query, wd.dict_samples, wd.offsets, wd.m)
+    rows = _sampled_rows(p_orig, 16, 3, n_top=4, n_ends=2)
+    parity.check(p_orig, i_orig, wo.query, wo.dict_samples, wo.offsets, wo.m, rows=rows, atol=1e-4)
+    assert np.all(p_dict >= p_orig - 1e-4)
 
 
 EDGE_CASES = {
