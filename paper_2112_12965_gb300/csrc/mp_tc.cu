@@ -580,8 +580,9 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
 // FP32's error, not the 2^-16 of a BF16 split; the recurrence adds its own
 // rounding to that seed for up to 32 * 16 rows. The epilogue removes the
 // shifts and stores S in FP32, transposed through shared memory so that the
-// stores are row-contiguous. A CTA builds and multiplies in turn; two CTAs
-// share an SM, so one CTA's operand build overlaps the other's MMAs.
+// stores are row-contiguous. A CTA (8 warps) builds and multiplies in turn;
+// two CTAs share an SM, so one CTA's operand build overlaps the other's MMAs,
+// and 16 warps per SM hide the latency of the builds' conversion chains.
 struct SeedArgs {
     const float *a;
     int64_t nq;
@@ -601,9 +602,16 @@ struct SeedArgs {
 };
 
 constexpr int kSeedVariant = 2;  // TF32 hi/lo
-constexpr int kSeedThreads = 128;
+constexpr int kSeedThreads = 256;
 constexpr int kSeedRows = 128;
+constexpr int kSeedRowStep = kSeedThreads / 8;          // query rows one pass of the threads fills
+constexpr int kSeedRowsPer = kSeedRows / kSeedRowStep;  // query rows per thread
 constexpr int kSeedEpr = 32;  // TF32 values of K per 128-byte operand row
+constexpr int kSeedRawPer = (kTcMaxN + kSeedEpr + kSeedThreads - 1) / kSeedThreads;  // staged samples per thread
+constexpr int kSeedColPer = (kTcMaxN + kSeedThreads - 1) / kSeedThreads;             // column terms per thread
+constexpr int kHalves = kSeedThreads / kSeedRows;  // groups of 4 warps sharing the TMEM lanes in the epilogue
+static_assert(kSeedThreads % kSeedRows == 0 && kSeedRows == 128, "the epilogue splits columns over groups of 4 warps");
+static_assert(kSeedRows % kSeedRowStep == 0, "query rows per thread");
 constexpr int kSeedKstep = 8;  // K per MMA
 constexpr long long kSeedWaitCycles = 4000000000LL;  // about 2 s
 
@@ -626,7 +634,7 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
     float *colp = raw + kTcMaxN + kSeedEpr + 8;                     // m * (mean_b - s_b) per column
     uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
-    float *ost = reinterpret_cast<float *>(base);  // epilogue staging (operands are idle then): 128 x 33
+    float *ost = reinterpret_cast<float *>(base);  // epilogue staging (operands are idle then): kHalves x 128 x 33
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t rb = blockIdx.x / p.n_groups;
@@ -642,14 +650,14 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
     tc_fence_after();
     const uint32_t taddr = *tmem_slot;
 
-    // Query operand: this thread fills 16-byte chunk c of rows rho_i = tid / 8 + 16 i
+    // Query operand: this thread fills 16-byte chunk c of rows rho_i = tid / 8 + kSeedRowStep i
     // (4 values of k each); the rows are centred on their own mean's hi part.
     const int c = tid & 7;
-    int64_t r_i[8];
-    float sa_i[8];
+    int64_t r_i[kSeedRowsPer];
+    float sa_i[kSeedRowsPer];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t sr = rb * kSeedRows + (tid >> 3) + 16 * i;
+    for (int i = 0; i < kSeedRowsPer; ++i) {
+        const int64_t sr = rb * kSeedRows + (tid >> 3) + kSeedRowStep * i;
         r_i[i] = sr < p.n_srows ? sr * p.stride : -1;
         sa_i[i] = r_i[i] >= 0 ? p.ms_a[r_i[i]].hi : 0.f;
     }
@@ -658,8 +666,8 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
     // stage, its column terms, loaded into registers one stage ahead. Nothing
     // consumes them until the next stage, so their latency overlaps the MMAs.
     // Positions past m or past the series hold the shift itself (x - shift = 0).
-    float xa[8][4], xb[3];
-    Split<float> mbv[2];
+    float xa[kSeedRowsPer][4], xb[kSeedRawPer];
+    Split<float> mbv[kSeedColPer];
     TcTile tl_next;
     float sb_next = 0.f;
     const int n_st = (t_hi - t_lo) * nkb;
@@ -667,7 +675,7 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
         tl_next = p.tiles[t_lo + j / nkb];
         const int k0 = (j % nkb) * kSeedEpr;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < kSeedRowsPer; ++i) {
             const int k = k0 + 4 * c;
             if (r_i[i] >= 0 && a16 && k + 3 < m) {
                 const float4 v = *reinterpret_cast<const float4 *>(p.a + r_i[i] + k);
@@ -682,14 +690,14 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
         }
         sb_next = p.ms_b[tl_next.g0].hi;
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
+        for (int u = 0; u < kSeedRawPer; ++u) {
             const int e = tid + u * kSeedThreads;
             const int64_t jj = tl_next.g0 + k0 + e;
             xb[u] = (e < tl_next.nmma + kSeedEpr && jj < p.nb) ? p.b[jj] : sb_next;
         }
         if (j % nkb == 0) {
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < kSeedColPer; ++u) {
                 const int n = tid + u * kSeedThreads;
                 mbv[u] = n < tl_next.nvalid ? p.ms_b[tl_next.g0 + n] : Split<float>{sb_next, 0.f};
             }
@@ -697,8 +705,10 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
     };
     if (n_st > 0) load_stage(0);
 
-    // the accumulator row this thread reads back (TMEM lane tid)
-    const int64_t srow = rb * kSeedRows + tid;
+    // the accumulator row this thread reads back: TMEM lane tid % 128 (a warp reads
+    // the lane quarter warp % 4); the two groups of 4 warps take alternate column groups
+    const int lrow = tid & (kSeedRows - 1), half = tid / kSeedRows;
+    const int64_t srow = rb * kSeedRows + lrow;
     const float da = srow < p.n_srows ? p.ms_a[srow * p.stride].lo : 0.f;  // mean - hi = lo
 
     uint32_t phase = 0;
@@ -708,21 +718,23 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
         const TcTile tile = tl_next;  // loaded with the tile's first stage
         const float s_b = sb_next;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) colp[tid + u * kSeedThreads] = (float)m * ((mbv[u].hi - s_b) + mbv[u].lo);
+        for (int u = 0; u < kSeedColPer; ++u)
+            if (tid + u * kSeedThreads < kTcMaxN)
+                colp[tid + u * kSeedThreads] = (float)m * ((mbv[u].hi - s_b) + mbv[u].lo);
         const uint32_t idesc = instr_desc<kSeedVariant>(tile.nmma);
         for (int q = 0; q < nkb; ++q, ++j) {
             const int k0 = q * kSeedEpr;
             // write this stage's operands from the registers
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int rho = (tid >> 3) + 16 * i;
+            for (int i = 0; i < kSeedRowsPer; ++i) {
+                const int rho = (tid >> 3) + kSeedRowStep * i;
                 float x[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) x[e] = xa[i][e] - sa_i[i];
                 put_chunk<kSeedVariant>(x, a_hi, a_lo, (uint32_t)rho * 128u + (uint32_t)((c ^ (rho & 7)) << 4));
             }
 #pragma unroll
-            for (int u = 0; u < 3; ++u) {
+            for (int u = 0; u < kSeedRawPer; ++u) {
                 const int e = tid + u * kSeedThreads;
                 if (e < kTcMaxN + kSeedEpr) raw[e] = xb[u] - s_b;
             }
@@ -753,20 +765,30 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
             if (!ok) break;
         }
         if (!ok) break;
-        // epilogue: accumulator row tid, 32 columns per TMEM load, staged in
-        // shared memory so that each warp stores contiguous runs of a row
-        const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
+        // epilogue: accumulator row lrow, 32 columns per TMEM load, staged in
+        // shared memory (one buffer per group of 4 warps) so that each warp
+        // stores contiguous runs of a row; group `half` takes the column
+        // groups c32 = 32 (kHalves j + half), and both groups pass the same
+        // barriers
+        const uint32_t t_lane = taddr + ((uint32_t)((warp & 3) * 32) << 16);
         const int ncols = (tile.nmma + 31) & ~31;
-        for (int c32 = 0; c32 < ncols; c32 += 32) {
-            uint32_t v[32];
-            tmem_ld32(t_lane + (uint32_t)c32, v);
+        float *const osth = ost + half * kSeedRows * 33;
+        for (int cg = 0; cg < ncols; cg += 32 * kHalves) {
+            const int c32 = cg + 32 * half;
+            const bool act = c32 < ncols;  // the same for the whole group of warps
+            if (act) {
+                uint32_t v[32];
+                tmem_ld32(t_lane + (uint32_t)c32, v);
 #pragma unroll
-            for (int u = 0; u < 32; ++u) ost[tid * 33 + u] = fmaf(-da, colp[c32 + u], __uint_as_float(v[u]));
+                for (int u = 0; u < 32; ++u) osth[lrow * 33 + u] = fmaf(-da, colp[c32 + u], __uint_as_float(v[u]));
+            }
             __syncthreads();
-            const int n = c32 + lane;
-            for (int rr = warp; rr < kSeedRows; rr += kSeedThreads / 32) {
-                const int64_t sr = rb * kSeedRows + rr;
-                if (sr < p.n_srows && n < tile.nvalid) p.seeds[sr * p.ld + tile.g0 + n] = ost[rr * 33 + lane];
+            if (act) {
+                const int n = c32 + lane;
+                for (int rr = warp & 3; rr < kSeedRows; rr += 4) {
+                    const int64_t sr = rb * kSeedRows + rr;
+                    if (sr < p.n_srows && n < tile.nvalid) p.seeds[sr * p.ld + tile.g0 + n] = osth[rr * 33 + lane];
+                }
             }
             __syncthreads();  // ost is rewritten by the next group (or the next tile's operands)
         }
