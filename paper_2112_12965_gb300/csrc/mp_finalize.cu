@@ -324,8 +324,8 @@ __host__ __device__ constexpr int fin_kpl(int m) { return ((m + 15) / 16 + 7) / 
 // Stage chunk g's samples b[g ..] - mean_hi(b_g) into wb (zero past the
 // dictionary), for every value the lanes of rescore_staged read.
 template <typename T, int KPL>
-__device__ __forceinline__ void stage_chunk(const T *__restrict__ pb, int64_t nb, const Split<T> *__restrict__ ms_b,
-                                            int32_t g, int lane, T *wb)
+__device__ __forceinline__ T stage_chunk(const T *__restrict__ pb, int64_t nb, const Split<T> *__restrict__ ms_b,
+                                         int32_t g, int lane, T *wb)
 {
     constexpr int NBV = 16 * KPL + kChunk;
     __syncwarp();  // earlier reads of wb are done
@@ -345,18 +345,36 @@ __device__ __forceinline__ void stage_chunk(const T *__restrict__ pb, int64_t nb
         }
     }
     __syncwarp();
+    return sb;
+}
+
+// The terms of the chunk window this lane scores in rescore_staged (window
+// g + 8 (lane / 16) + lane % 8, clamped into range): 1/std, penalty (0 or
+// -inf) and split mean. Loaded before the chunk is staged, so that their
+// latency overlaps the staging.
+template <typename T> struct CandTerms {
+    T z, w, mhi, mlo;
+};
+template <typename T>
+__device__ __forceinline__ CandTerms<T> load_cand(const vec4_t<T> *__restrict__ rs_b,
+                                                  const Split<T> *__restrict__ ms_b, int64_t npos_b, int32_t g,
+                                                  int lane)
+{
+    const int64_t gc = (int64_t)g + 8 * (lane >> 4) + (lane & 7);
+    const int64_t gcl = gc < npos_b ? gc : npos_b - 1;
+    const vec4_t<T> rv = rs_b[gcl];
+    const Split<T> mb = ms_b[gcl];
+    return CandTerms<T>{rv.z, rv.w, mb.hi, mb.lo};
 }
 
 // Re-score chunk g against the staged query window qa (= a - mean_hi(a)) and
 // the staged chunk wb (= b - mean_hi(b_g)); returns the chunk's best (score,
 // window) in every lane as rescore_chunk.
 template <typename T, int KPL>
-__device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const Split<T> *__restrict__ ms_b,
-                                               const vec4_t<T> *__restrict__ rs_b, const T *qa, T da, int32_t g,
-                                               int lane, const T *wb, T &sc_out, int32_t &g_out, int64_t i,
-                                               int excl)
+__device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const CandTerms<T> &ct, T sb, const T *qa,
+                                               T da, int32_t g, int lane, const T *wb, T &sc_out, int32_t &g_out,
+                                               int64_t i, int excl)
 {
-    const T sb = ms_b[g].hi;
     const int half = lane >> 4, lg = lane & 15;
     const int k0 = lg * KPL;
     T acc[8], bw[8];
@@ -394,12 +412,9 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const Spli
     // lanes l and l ^ 8 now hold the same candidate's total
     const int cand = 8 * half + (lane & 7);
     const int64_t gc = (int64_t)g + cand;
-    const int64_t gcl = gc < npos_b ? gc : npos_b - 1;  // in range, so the loads need no branch
-    const vec4_t<T> rv = rs_b[gcl];
-    const Split<T> mb = ms_b[gcl];
-    const bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl)) && rv.w == T(0);
+    const bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl)) && ct.w == T(0);
     // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
-    T sc = ok ? (acc[0] - T(m) * da * ((mb.hi - sb) + mb.lo)) * rv.z : T(-INFINITY);
+    T sc = ok ? (acc[0] - T(m) * da * ((ct.mhi - sb) + ct.mlo)) * ct.z : T(-INFINITY);
     int32_t gw = ok ? (int32_t)gc : -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -519,17 +534,18 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
             if (g0 < 0) continue;
             const int64_t iw = i0 + t;
             const Split<T> ma{s_mhi[t], s_mlo[t]};
+            CandTerms<T> ct = load_cand(p.rs_b, p.ms_b, p.npos_b, g0, lane);
             const T *ai = p.a + iw;
 #pragma unroll
             for (int u = 0; u < KPL / 2; ++u) {  // 16 * KPL values over 32 lanes; qidx(lane + 32 u) = lane + 33 u
                 const int e = lane + 32 * u;
                 qa[lane + 33 * u] = e < m ? ai[e] - ma.hi : T(0);
             }
-            stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, g0, lane, wb);
+            T sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, g0, lane, wb);
             T sc;
             int32_t gw;
-            rescore_staged<T, KPL>(p.npos_b, m, p.ms_b, p.rs_b, qa, ma.lo, g0, lane, wb, sc, gw, iw, p.excl);
-            int32_t staged = g0;  // the chunk whose samples wb holds
+            rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, g0, lane, wb, sc, gw, iw, p.excl);
+            int32_t staged = g0;  // the chunk whose samples wb holds (and whose terms ct and sb are)
             int32_t win = g0;     // the chunk of the best window so far
             const int ncw = s_nc[t];
             if (ncw > 0 && ncw <= kFinMaxCand) {
@@ -537,8 +553,9 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
                     const int32_t cu = s_cand[c][t];
                     T s2;
                     int32_t g2;
-                    stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
-                    rescore_staged<T, KPL>(p.npos_b, m, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
+                    ct = load_cand(p.rs_b, p.ms_b, p.npos_b, cu, lane);
+                    sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
+                    rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
                     staged = cu;
                     if (better(s2, g2, sc, gw)) {
                         sc = s2;
@@ -572,9 +589,9 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
                             if (cu < 0) continue;
                             T s2;
                             int32_t g2;
-                            stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
-                            rescore_staged<T, KPL>(p.npos_b, m, p.ms_b, p.rs_b, qa, ma.lo, cu, lane, wb, s2, g2, iw,
-                                                   p.excl);
+                            ct = load_cand(p.rs_b, p.ms_b, p.npos_b, cu, lane);
+                            sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
+                            rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
                             staged = cu;
                             if (better(s2, g2, sc, gw)) {
                                 sc = s2;
@@ -588,10 +605,15 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
             T dw = T(INFINITY);
             if (gw >= 0) {
                 // the chosen pair's distance from its definition, on the staged samples
-                if (staged != win) stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, win, lane, wb);
-                const Split<T> mb = p.ms_b[gw];
-                const T db = (mb.hi - p.ms_b[win].hi) + mb.lo;  // wb holds b - mean_hi(win)
-                const T is_a = s_isa[t], is_b = p.rs_b[gw].z;
+                if (staged != win) {
+                    ct = load_cand(p.rs_b, p.ms_b, p.npos_b, win, lane);
+                    sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, win, lane, wb);
+                }
+                // the winner's terms from the lane that scored it (lanes 16 (o / 8) + o % 8)
+                const int ow = gw - win, src = 16 * (ow >> 3) + (ow & 7);
+                const T is_b = __shfl_sync(0xffffffffu, ct.z, src);
+                const T db = (__shfl_sync(0xffffffffu, ct.mhi, src) - sb) + __shfl_sync(0xffffffffu, ct.mlo, src);
+                const T is_a = s_isa[t];
                 // z_a - z_b = (qa - lo_a) is_a - (wb - db) is_b: each difference is
                 // taken before its scaling, so no large term is rounded (db, the
                 // mean difference within the chunk, can be far above the spread)
