@@ -39,11 +39,13 @@ L2_BYTES = 129 * 2**20
 PLAIN_OPS_PER_PAIR = 4
 # DRAM bytes of one k_plain launch on the full-size ECG workload (2^20 query
 # samples, 64 x 1024 dictionary, m = 256), from one single-pass ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum: 455.95 MB read (mostly the
-# 403 MB top-seed matrix) and 160.92 MB written (partials and near-tie
-# records). Valid for this kernel build and workload only.
-PLAIN_DRAM_BYTES_FULL = 455.95e6 + 160.92e6
+# dram__bytes_read.sum + dram__bytes_write.sum: 369.35 MB read (mostly the
+# 322 MB top-seed matrix) and 220.94 MB written (partials and near-tie
+# records). Valid for this kernel build (20 rows per lane) and workload only.
+PLAIN_DRAM_BYTES_FULL = 369.35e6 + 220.94e6
 SMS, LANES_PER_SM = 152, 128
+# query windows per top seed of the FP32 plain kernel: one per warp, 32 lanes x 20 rows
+SEED_STRIDE = 32 * 20
 
 
 def shard_rows(n: int, m: int, world: int, rank: int):
@@ -206,7 +208,7 @@ def roofline(kname, pairs, m, join_ms, peaks, peak_src, full_size=False):
         peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-instructions/s
         achieved = pairs * PLAIN_OPS_PER_PAIR / (join_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": PLAIN_DRAM_BYTES_FULL if full_size else None,
+                "frac": achieved / peak_ops, "traffic": PLAIN_DRAM_BYTES_FULL if full_size and PLAIN_DRAM_BYTES_FULL else None,
                 "kernel": "k_plain",
                 "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)",
                 "ops_per_pair": PLAIN_OPS_PER_PAIR}
@@ -223,11 +225,11 @@ def roofline(kname, pairs, m, join_ms, peaks, peak_src, full_size=False):
 
 
 def seed_roofline(w, seeds_ms, peaks, peak_src):
-    """Tensor roofline of the plain join's seed kernel (K2s): one seed row per 512 query
-    windows against every dictionary window, K = m, three TF32 products per term."""
+    """Tensor roofline of the plain join's seed kernel (K2s): one seed row per SEED_STRIDE
+    query windows against every dictionary window, K = m, three TF32 products per term."""
     if seeds_ms <= 0:
         return None
-    n_srows = -(-w.n_rows // 512)
+    n_srows = -(-w.n_rows // SEED_STRIDE)
     flops = n_srows * w.n_dict_windows * 2 * w.m * 3
     peak = peaks.get("bf16_tflops", 1900.0) / 2.0
     achieved = flops / (seeds_ms / 1e3) / 1e12
@@ -326,8 +328,9 @@ def serving_run(mp, n_requests, seed=7):
             pairs += nq * mp.mp_dict_windows(handles[r.dict_id], r.m)
         mp.mp_drain(ctx, 600.0)
         cap_s = time.perf_counter() - t0
-        for t in tickets:
-            mp.mp_poll(ctx, t)
+        failed = sum(mp.mp_poll(ctx, t)[0] != mp.MP_DONE for t in tickets)
+        if failed:
+            raise RuntimeError(f"serving: {failed} of {len(tickets)} requests failed")
         capacity_rps = len(reqs) / cap_s
         # 2) offered load at 0.5x capacity, Poisson arrivals
         rate = 0.5 * capacity_rps
@@ -348,6 +351,8 @@ def serving_run(mp, n_requests, seed=7):
             for t in list(pending):
                 st, lat = mp.mp_poll(ctx, t)
                 if st != mp.MP_PENDING:
+                    if st != mp.MP_DONE:
+                        raise RuntimeError(f"serving: request {t} failed")
                     lats.append(lat)
                     pending.discard(t)
             time.sleep(0.0002)

@@ -33,7 +33,8 @@ struct Span {
 };
 
 // Launch geometry of the plain diagonal kernel.
-constexpr int kPlainRowsPerLane = 16;  // query windows owned by one lane
+constexpr int kPlainRowsPerLane = 20;  // query windows owned by one lane (k_plain, FP32)
+constexpr int kServeRowsPerLane = 16;  // the same in the batched serving kernel (two CTAs per SM)
 constexpr int kPlainColBlock = 256;    // dictionary windows staged per block
 constexpr int kChunk = 16;             // windows per chunk of the lazy argmax
 static_assert(kChunk % 2 == 0, "the plain kernel folds the scores of two columns per maximum");
@@ -118,7 +119,8 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
                          NearTies *near, cudaStream_t st);
-template <typename T> size_t plain_smem_bytes(int warps, int m);
+template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
+template <typename T> size_t plain_smem_bytes(int warps, int m, int rows_per_lane = plain_rows_per_lane<T>());
 // Resident CTAs per SM of the plain kernel for this shape (occupancy API).
 template <typename T> int plain_ctas_per_sm(int warps, int m);
 
@@ -156,7 +158,6 @@ struct BatchItem {
 // `warps` warps per row block.
 cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *items, int32_t n_items,
                                  int32_t *counter, int warps, int max_m, int grid, cudaStream_t st);
-template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
 
 // Finalisation (kernel K4): reduce the column groups, re-score the winning
 // chunk, apply the constant-window convention, recompute the chosen pair's

@@ -116,9 +116,9 @@ template <int P> __device__ __forceinline__ int pad(int e) { return e + e / P; }
 // that one packed FMA (fma.rn.f32x2: each half rounded once, exactly as
 // fmaf) advances two rows: moving one column right shifts every row down by
 // one, which maps pair k-1 onto pair k, and only pair 0 takes new inputs
-// (the row above the lane, and row kRows/2 - 1). The packed form pays off with
-// 16 warps per SM (k_plain); the batched serving kernel, at 8 warps per SM,
-// cannot hide the packed FMA's longer pipe occupancy and stays scalar.
+// (the row above the lane, and row kRows/2 - 1). The packed form pays off in
+// k_plain; the batched serving kernel, at 8 warps per SM, cannot hide the
+// packed FMA's longer pipe occupancy and stays scalar.
 template <typename T, int kRows, bool kPacked> struct Rows {
     T C[kRows], df[kRows], dg[kRows];
     __device__ __forceinline__ void set_terms(int j, T f, T g)
@@ -391,19 +391,25 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 
             // ---- left seeds at the first column of the span ----
             if (cb == 0) {
-                T aw[16], acc[kRows];
+                T acc[kRows];
 #pragma unroll
                 for (int j = 0; j < kRows; ++j) acc[j] = T(0);
+                // rows in passes of up to 16, each with a sliding window of 16 query samples
 #pragma unroll
-                for (int t = 0; t < 16; ++t) aw[t] = sa[pad<16>(sa_l + t)];
-                for (int k0 = 0; k0 < m_up16; k0 += 16) {
+                for (int j0 = 0; j0 < kRows; j0 += 16) {
+                    T aw[16];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int k = k0 + u;
-                        const T bk = (k < m) ? sb[pad<8>(k)] : T(0);
+                    for (int t = 0; t < 16; ++t) aw[t] = sa[pad<16>(sa_l + j0 + t)];
+                    for (int k0 = 0; k0 < m_up16; k0 += 16) {
 #pragma unroll
-                        for (int j = 0; j < kRows; ++j) acc[j] = fma(aw[(j + u) & 15], bk, acc[j]);
-                        aw[u] = sa[pad<16>(sa_l + 16 + k)];
+                        for (int u = 0; u < 16; ++u) {
+                            const int k = k0 + u;
+                            const T bk = (k < m) ? sb[pad<8>(k)] : T(0);
+#pragma unroll
+                            for (int j = j0; j < kRows && j < j0 + 16; ++j)
+                                acc[j] = fma(aw[(j - j0 + u) & 15], bk, acc[j]);
+                            aw[u] = sa[pad<16>(sa_l + j0 + 16 + k)];
+                        }
                     }
                 }
                 const T db0 = p.ms_b[gblk].lo;  // shift_b is this window's mean rounded
@@ -537,11 +543,13 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     }
 }
 
-// Four CTAs (16 warps) per SM for FP32 data: the kernel then fits in 128
-// registers (with a few tens of bytes spilled), and the extra warps hide the
-// shuffle and shared-memory latencies of the recurrence.
+// Three CTAs (12 warps) per SM for FP32 data, with 20 rows per lane in 168
+// registers (a few tens of bytes spilled). More rows per lane spread the
+// per-column work (shuffle, column terms, seed select) and the per-chunk
+// argmax over more pairs, and mean fewer top seeds; that gained more than the
+// 16 warps of 16 rows per lane at 128 registers hid.
 template <typename T, int kRows, bool kSeeds, bool kNear, bool kSelf = false>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_plain(PlainParams<T> p)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_plain(PlainParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     plain_item<T, kRows, kSeeds, kNear, true, kSelf>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
@@ -572,9 +580,9 @@ __global__ void __launch_bounds__(128, 2) k_plain_batched(const PlainParams<T> *
 }  // namespace
 
 template <typename T>
-size_t plain_smem_bytes(int warps, int m)
+size_t plain_smem_bytes(int warps, int m, int rows_per_lane)
 {
-    const int rows_cta = warps * 32 * plain_rows_per_lane<T>();
+    const int rows_cta = warps * 32 * rows_per_lane;
     const int m_up8 = (m + 7) & ~7, m_up16 = (m + 15) & ~15;
     const int NA = rows_cta + m_up16 + 32;
     const int NB = kPlainColBlock + m_up8 + 16;
@@ -639,8 +647,8 @@ cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *
                                  int32_t *counter, int warps, int max_m, int grid, cudaStream_t st)
 {
     static_assert(sizeof(PlainRequest) == sizeof(PlainParams<float>), "request layout");
-    const size_t smem = plain_smem_bytes<float>(warps, max_m);
-    auto kern = k_plain_batched<float, kPlainRowsPerLane, true>;  // every request carries near-tie slots
+    const size_t smem = plain_smem_bytes<float>(warps, max_m, kServeRowsPerLane);
+    auto kern = k_plain_batched<float, kServeRowsPerLane, true>;  // every request carries near-tie slots
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 32 * warps, smem, st>>>(reinterpret_cast<const PlainParams<float> *>(reqs_dev), items, n_items,
@@ -668,8 +676,8 @@ int plain_ctas_per_sm(int warps, int m)
 
 template int plain_ctas_per_sm<float>(int, int);
 template int plain_ctas_per_sm<double>(int, int);
-template size_t plain_smem_bytes<float>(int, int);
-template size_t plain_smem_bytes<double>(int, int);
+template size_t plain_smem_bytes<float>(int, int, int);
+template size_t plain_smem_bytes<double>(int, int, int);
 template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,
                                          const Split<float> *, const float *, int64_t, const float4 *,
                                          const Split<float> *, const Span *, const int32_t *, Partial<float> *,

@@ -542,8 +542,9 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
 // Top seeds of the plain FP32 kernel computed on the tensor cores: one row
 // per warp of query windows (every 32 * kPlainRowsPerLane-th window), one
 // column per dictionary window position. A join whose seed matrix would
-// exceed kSeedCapBytes runs in row chunks (multiples of 2048 query windows),
-// each with its own seeds in the same buffer.
+// exceed kSeedCapBytes runs in row chunks (whole CTAs: multiples of
+// 4 * 32 * kPlainRowsPerLane query windows), each with its own seeds in the
+// same buffer.
 constexpr size_t kSeedCapBytes = (size_t)2 << 30;
 
 struct SeedGeo {
@@ -783,11 +784,35 @@ static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const Dic
 // ---------------------------------------------------------------------------
 // serving scheduler
 // ---------------------------------------------------------------------------
+// Geometry of one request in the batched serving kernel: kServeRowsPerLane
+// rows per lane, 4 warps per CTA. The request's memory is sized and laid out
+// with this one function, so the two always agree.
+static Geometry serve_geometry(const mp_ctx *ctx, int64_t nq, const DictStats *s, int32_t dtype, int32_t m)
+{
+    Geometry geo =
+        plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), kServeRowsPerLane, dtype, m,
+                       (int64_t)s->seg_spans.size());
+    geo.warps = 4;
+    geo.n_row_blocks = (int)((nq + 4 * 32 * kServeRowsPerLane - 1) / (4 * 32 * kServeRowsPerLane));
+    return geo;
+}
+
+// Device bytes of a request: its query, its outputs (dist, idx) and a
+// workspace for either way it may run (alone through join_device, or in the
+// batched kernel).
+static size_t request_ws_bytes(const mp_ctx *ctx, const Request &r, const DictStats *s)
+{
+    const int64_t nq = r.n - r.m + 1;
+    size_t ws = join_ws_bytes(ctx, r.dict, s, r.dtype, r.n, r.m, false);
+    if (s->n_windows > 0 && r.dtype == MP_F32)
+        ws = std::max(ws, join_ws_layout(nq, r.dtype, serve_geometry(ctx, nq, s, r.dtype, r.m).n_groups, 0).total);
+    return ws;
+}
+
 static size_t request_bytes(const mp_ctx *ctx, const Request &r, const DictStats *s)
 {
     const int64_t nq = r.n - r.m + 1;
-    return align_up((size_t)r.n * dtype_size(r.dtype), 256) + align_up(nq * 16, 256) +
-           join_ws_bytes(ctx, r.dict, s, r.dtype, r.n, r.m, false);
+    return align_up((size_t)r.n * dtype_size(r.dtype), 256) + align_up(nq * 16, 256) + request_ws_bytes(ctx, r, s);
 }
 
 // Pinned host buffer of at least `bytes` (caller holds ctx->smu or is the
@@ -891,15 +916,14 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
             CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
             continue;
         }
-        const Geometry geo0 =
-            plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, r.dtype, r.m, (int64_t)s->seg_spans.size());
-        Geometry geo = geo0;
-        geo.warps = 4;
-        geo.n_row_blocks = (int)((nq + 4 * 32 * kPlainRowsPerLane - 1) / (4 * 32 * kPlainRowsPerLane));
+        const Geometry geo = serve_geometry(ctx, nq, s, r.dtype, r.m);
         DictStats::Grouping *gr = nullptr;
         rc = get_grouping(ctx, s, geo.n_groups, &gr);
         if (rc) return rc;
         JoinWs w = join_ws_layout(nq, r.dtype, geo.n_groups, 0);
+        // the layout must lie inside the request's memory (sized by request_bytes)
+        if ((size_t)(p - (unsigned char *)r.dmem) + w.total > r.bytes)
+            return fail(MP_E_INTERNAL, "serving workspace of %zu bytes exceeds the request's %zu", w.total, r.bytes);
         const float *a = (const float *)q;
         double *mean_a = (double *)(p + w.off_mean);
         double *inv_a = (double *)(p + w.off_inv);

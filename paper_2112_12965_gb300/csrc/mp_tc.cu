@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
 // are TF32 with a hi/lo split of both operands (hi*hi + hi*lo + lo*hi): each
 // value is split with a residual below 2^-22 of it, so a seed carries about
 // FP32's error, not the 2^-16 of a BF16 split; the recurrence adds its own
-// rounding to that seed for up to 32 * 16 rows. The epilogue removes the
+// rounding to that seed for up to 32 * 20 rows. The epilogue removes the
 // shifts and stores S in FP32, transposed through shared memory so that the
 // stores are row-contiguous. A CTA (8 warps) builds and multiplies in turn;
 // two CTAs share an SM, so one CTA's operand build overlaps the other's MMAs,

@@ -131,7 +131,7 @@ EDGE_CASES = {
     "one_window_segments": (2500, [96] * 40, 96, "rw"),
     "many_tiny_segments": (5000, [20 + (k % 7) for k in range(300)], 16, "ecg"),
     "long_single_segment": (3000, [9000], 200, "ecg"),
-    "rows_span_cta_tail": (2048 + 511 + 300, [2000, 1000], 300, "rw"),
+    "rows_span_cta_tail": (2560 + 639 + 300, [2000, 1000], 300, "rw"),
 }
 
 
@@ -306,7 +306,7 @@ def test_drifting_offset_series_all_rows(mp, ctx):
     """Large offsets and drift: the seeds' centring must keep FP32 products small.
 
     m = 100 is no multiple of the tensor-core K step, the query has a ragged
-    number of rows (not a multiple of the 512 rows a warp seeds), and the
+    number of rows (not a multiple of the 640 rows a warp seeds), and the
     dictionary's segments have uneven lengths.
     """
     rng = np.random.default_rng(21)
@@ -323,16 +323,16 @@ def test_large_join_runs_in_row_chunks(mp, ctx):
     """A join whose top-seed matrix would pass its 2 GiB cap runs in row chunks.
 
     A dictionary of 2^20 samples makes each seed row about 4 MB, so a chunk is
-    512 seed rows = 262,144 query windows, and a query of 600,000 windows runs
-    in three chunks. Rows at every chunk boundary are checked against the
-    oracle.
+    512 seed rows of 640 query windows = 327,680 query windows, and a query of
+    700,000 windows runs in three chunks. Rows at every chunk boundary and at
+    a seed-row boundary are checked against the oracle.
     """
     m = 64
     b = synthetic.random_walk(1 << 20, 81).astype(np.float32)
     offs = np.array([0, 300_000, 300_100, 1 << 20])
-    q = synthetic.random_walk(600_000 + m - 1, 82).astype(np.float32)
+    q = synthetic.random_walk(700_000 + m - 1, 82).astype(np.float32)
     dist, idx = join(mp, ctx, q, b, offs, m)
-    edges = np.array([0, 1, 511, 512, 262_143, 262_144, 262_145, 524_287, 524_288, 524_289, 599_999])
-    rows = np.unique(np.concatenate([edges, np.random.default_rng(4).choice(600_000, 40, replace=False)]))
+    edges = np.array([0, 1, 639, 640, 327_679, 327_680, 327_681, 655_359, 655_360, 655_361, 699_999])
+    rows = np.unique(np.concatenate([edges, np.random.default_rng(4).choice(700_000, 40, replace=False)]))
     parity.check(dist, idx, q, b, offs, m, rows=rows, atol=1e-4)
     assert np.all((dist >= 0) & (dist <= 2 * math.sqrt(m) + 1e-9))

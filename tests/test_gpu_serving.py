@@ -85,6 +85,40 @@ def test_serving_matches_sync_join_and_is_mix_invariant(mp):
         mp.mp_shutdown(ctx)
 
 
+def test_serving_large_requests_match_sync_join(mp):
+    """Requests of the serving benchmark's largest sizes (queries and dictionaries of up to 2^18 samples),
+    submitted together: each result matches the synchronous join and, on sampled rows, the oracle. The
+    batched kernel's geometry (its own rows per lane and column groups) must fit the memory the request was
+    given at submission."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=8, max_batch=16)
+    try:
+        dicts = synthetic.serving_dictionaries(n_dicts=3, seed=140, min_log2=16, max_log2=18)
+        handles = [mp.mp_dict_load(ctx, b, offs, [64, 128, 256]) for b, offs in dicts]
+        rng = np.random.default_rng(5)
+        reqs, outs, tickets = [], [], []
+        for k in range(8):
+            n = int(2 ** rng.uniform(15, 18))
+            m = int(rng.choice([64, 128, 256]))
+            q = (synthetic.random_walk(n, 3000 + k) if k % 2 else synthetic.ecg_like(n, 3000 + k)).astype(np.float32)
+            di = int(rng.integers(0, len(dicts)))
+            od, oi = np.empty(n - m + 1), np.empty(n - m + 1, dtype=np.int64)
+            reqs.append((di, q, m))
+            outs.append((od, oi))
+            tickets.append(mp.mp_submit(ctx, handles[di], q, m, od, oi))
+        wait(mp, ctx, tickets, timeout=300.0)
+        for (od, oi), (di, q, m) in zip(outs, reqs):
+            sd, _ = mp.mp_ab_join(ctx, handles[di], q, m)
+            np.testing.assert_allclose(od, sd, atol=1e-4, rtol=0)
+            b, offs = dicts[di]
+            rows = np.unique(np.concatenate([np.arange(0, len(od), max(1, len(od) // 12)), [len(od) - 1]]))
+            parity.check(od, oi, q, b, offs, m, rows=rows, atol=1e-4)
+        mp.mp_drain(ctx, 60.0)
+        for h in handles:
+            mp.mp_dict_free(ctx, h)
+    finally:
+        mp.mp_shutdown(ctx)
+
+
 def test_drain_returns_only_after_every_result_is_written(mp):
     """mp_drain must not return while a batch is being launched (its outputs unwritten)."""
     ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=4, max_batch=4)
