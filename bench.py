@@ -39,10 +39,11 @@ L2_BYTES = 129 * 2**20
 PLAIN_OPS_PER_PAIR = 4
 # DRAM bytes of one k_plain launch on the full-size ECG workload (2^20 query
 # samples, 64 x 1024 dictionary, m = 256), from one single-pass ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum: 369.35 MB read (mostly the
-# 322 MB top-seed matrix) and 220.94 MB written (partials and near-tie
-# records). Valid for this kernel build (20 rows per lane) and workload only.
-PLAIN_DRAM_BYTES_FULL = 369.35e6 + 220.94e6
+# dram__bytes_read.sum + dram__bytes_write.sum: 367.49 MB read (mostly the
+# 323 MB top-seed matrix) and 219.89 MB written (partials and near-tie
+# records). Valid for this kernel build (20 rows per lane, one 16-byte column
+# term per column) and workload only.
+PLAIN_DRAM_BYTES_FULL = 367.49e6 + 219.89e6
 SMS, LANES_PER_SM = 152, 128
 # query windows per top seed of the FP32 plain kernel: one per warp, 32 lanes x 20 rows
 SEED_STRIDE = 32 * 20

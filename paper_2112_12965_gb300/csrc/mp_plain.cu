@@ -261,11 +261,12 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     // stop: top seeds, one per (warp, column of the block)
     T *stop = sb + NB_pad;
     // scs: recurrence terms of the block's columns (padded to whole chunks),
-    // 32 bytes per column, 32-byte aligned: (df, dg, 1/std, penalty) for FP64
-    // data; for FP32 the pairs (df, df, dg, dg) and (1/std, 1/std, penalty,
-    // penalty), so that 128-bit loads yield the packed FMA operands directly.
-    // Offset arithmetic on smem_raw keeps the shared address space visible to
-    // the compiler (shared, not generic, loads).
+    // (df, dg, 1/std, penalty), one vec4 per column (32 bytes for FP64 data,
+    // 16 for FP32), 32-byte aligned. The packed form builds its operand pairs
+    // (x, x) from one 128-bit load per column: storing the pairs themselves
+    // (two loads per column) cost 14 % of the kernel's time, and two columns'
+    // worth of spilled registers. Offset arithmetic on smem_raw keeps the
+    // shared address space visible to the compiler (shared, not generic, loads).
     const size_t scs_off = ((size_t)(reinterpret_cast<unsigned char *>(stop + nwarps * CB) - smem_raw) + 31) &
                            ~static_cast<size_t>(31);
     vec4_t<T> *scs = reinterpret_cast<vec4_t<T> *>(smem_raw + scs_off);
@@ -347,8 +348,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     v.w = T(-INFINITY);
                 }
                 if constexpr (kPack) {
-                    scs2[2 * c] = make_float4(v.x, v.x, v.y, v.y);
-                    scs2[2 * c + 1] = make_float4(v.z, v.z, v.w, v.w);
+                    scs2[c] = make_float4(v.x, v.y, v.z, v.w);
                 } else {
                     scs[c] = v;
                 }
@@ -448,15 +448,15 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 #pragma unroll
                     for (int u = 0; u < kChunk; ++u) {
                         const int c = c0 + u;
-                        const float4 cxy = scs2[2 * c], czw = scs2[2 * c + 1];
+                        const float4 cv = scs2[c];
                         if (cb > 0 || c > 0) {
                             const float up = __shfl_up_sync(0xffffffffu, R.last(), 1);
-                            R.step(make_float2(cxy.x, cxy.y), make_float2(cxy.z, cxy.w), up, lane == 0, stop_w[c]);
+                            R.step(make_float2(cv.x, cv.x), make_float2(cv.y, cv.y), up, lane == 0, stop_w[c]);
                         }
                         if ((u & 1) == 0)
-                            R.score(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), q0);
+                            R.score(make_float2(cv.z, cv.z), make_float2(cv.w, cv.w), q0);
                         else
-                            R.score_max2(make_float2(czw.x, czw.y), make_float2(czw.z, czw.w), q0, cm);
+                            R.score_max2(make_float2(cv.z, cv.z), make_float2(cv.w, cv.w), q0, cm);
                     }
                 } else if constexpr (!kPack && !kSelf && sizeof(T) == 4) {
                     // scalar FP32 form (serving): the same pairing of columns
@@ -479,7 +479,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                 for (int u = 0; u < kChunk; ++u) {
                     const int c = c0 + u;
                     if constexpr (kPack) {
-                        const float4 cxy = scs2[2 * c], czw = scs2[2 * c + 1];
+                        const float4 cv = scs2[c];
+                        const float4 cxy = make_float4(cv.x, cv.x, cv.y, cv.y);
+                        const float4 czw = make_float4(cv.z, cv.z, cv.w, cv.w);
                         if (cb > 0 || c > 0) {
                             const float up = __shfl_up_sync(0xffffffffu, R.last(), 1);
                             R.step(make_float2(cxy.x, cxy.y), make_float2(cxy.z, cxy.w), up, lane == 0, stop_w[c]);
@@ -587,7 +589,7 @@ size_t plain_smem_bytes(int warps, int m, int rows_per_lane)
     const int NA = rows_cta + m_up16 + 32;
     const int NB = kPlainColBlock + m_up8 + 16;
     const size_t scalars = (size_t)(NA + NA / 16 + 1) + (size_t)(NB + NB / 8 + 1) + (size_t)warps * kPlainColBlock;
-    // + 32: the column-term array (32 bytes per column) is aligned up to 32 bytes
+    // + 32: the column-term array (up to 32 bytes per column) is aligned up to 32 bytes
     return sizeof(T) * scalars + 32 + 32 * (size_t)kPlainColBlock;
 }
 
