@@ -157,13 +157,22 @@ def cpu_baseline(w, target_s: float = 15.0):
     dt = time.perf_counter() - t0
     n_rows = int(max(256, min(nq, len(rows) * target_s / max(dt, 1e-6))))
     rows = np.linspace(0, nq - 1, n_rows).astype(np.int64)
+    cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)
+    oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows, nthreads=cores)
     dt = time.perf_counter() - t0
     pairs = n_rows * w.n_dict_windows
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+    # the same oracle on one thread, on a sample sized for about 3 s
+    n1 = int(max(16, min(nq, n_rows * 3.0 / max(dt, 1e-6) / cores)))
+    rows1 = np.linspace(0, nq - 1, n1).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows1, nthreads=1)
+    dt1 = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_rows} evenly spaced of {nq} query windows, all {w.n_dict_windows} dictionary windows, "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s",
+            "single_thread_value": n1 * w.n_dict_windows / dt1,
+            "single_thread_sample": f"{n1} evenly spaced query windows, {dt1:.1f} s on 1 thread"}
 
 
 def run_reference(args, rank, world):
