@@ -546,10 +546,10 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 }
 
 // Three CTAs (12 warps) per SM for FP32 data, with 20 rows per lane in 168
-// registers (a few tens of bytes spilled). More rows per lane spread the
-// per-column work (shuffle, column terms, seed select) and the per-chunk
-// argmax over more pairs, and mean fewer top seeds; that gained more than the
-// 16 warps of 16 rows per lane at 128 registers hid.
+// registers and no spills. More rows per lane spread the per-column work
+// (shuffle, column terms, seed select) and the per-chunk argmax over more
+// pairs, and mean fewer top seeds; that gained more than the 16 warps of 16
+// rows per lane at 128 registers hid.
 template <typename T, int kRows, bool kSeeds, bool kNear, bool kSelf = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_plain(PlainParams<T> p)
 {
