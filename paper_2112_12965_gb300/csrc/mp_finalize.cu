@@ -431,10 +431,11 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const Cand
 }
 
 template <typename T, int KPL>
-__global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k_finalize_blk(FinalizeParams<T> p)
+__global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
+    k_finalize_blk(FinalizeParams<T> p, int wpw)
 {
     constexpr int kW = fin_warps<T>();
-    constexpr int kNB = 32 * kW;                                   // query windows per block
+    constexpr int kNB = 32 * kW;                                   // threads, and the most windows per block
     constexpr int kQV = 16 * KPL + (16 * KPL) / 32 + 1;             // staged query window
     constexpr int kBV = (16 * KPL + kChunk) + (16 * KPL + kChunk) / 32 + 1;  // staged chunk
     __shared__ T f_buf[kW][kQV + kBV];
@@ -457,9 +458,13 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
         }
         return;
     }
-    const int64_t nblk = (p.nq + kNB - 1) / kNB;
+    // wpw (1..32) query windows per warp: a block is kW * wpw windows, so that
+    // short joins still spread over many CTAs
+    const int nb = kW * wpw;
+    const int64_t nblk = (p.nq + nb - 1) / nb;
     for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        const int64_t i0 = blk * kNB;
+        const int64_t i0 = blk * nb;
+        const bool mine = tid < nb;  // this thread has a window of the block
         const int64_t i = i0 + tid;
         // ---- phase 1: this thread's window ----
         double d = INFINITY;
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
         int32_t g = -1;
         int nc = 0;
         bool resc = false;  // phase 2 re-scores this window
-        if (i < p.nq && p.g_first >= 0) {
+        if (mine && i < p.nq && p.g_first >= 0) {
             if (p.cflag_a[i]) {
                 // a constant query window is 0 from a constant window, sqrt(m) from the rest
                 const int64_t gc = const_outside(p, i), gf = first_outside(p, i);
@@ -528,8 +533,8 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
         __syncthreads();
 
         // ---- phase 2: this warp's 32 windows, one at a time ----
-        for (int w = 0; w < 32; ++w) {
-            const int t = warp * 32 + w;
+        for (int w = 0; w < wpw; ++w) {
+            const int t = warp * wpw + w;
             const int32_t g0 = s_g[t];
             if (g0 < 0) continue;
             const int64_t iw = i0 + t;
@@ -639,7 +644,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
         __syncthreads();
 
         // ---- phase 3: this thread's window ----
-        if (i < p.nq) {
+        if (mine && i < p.nq) {
             if (resc) {
                 d = (double)s_d[tid];
                 gi = s_gi[tid];
@@ -658,9 +663,14 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8) k
 template <typename T, int KPL> cudaError_t launch_blk(const FinalizeParams<T> &p, cudaStream_t st)
 {
     constexpr int kNB = 32 * fin_warps<T>();
-    int64_t grid = (p.nq + kNB - 1) / kNB;  // one block of query windows per CTA and pass
+    // windows per warp: 32, unless that leaves fewer than about eight CTAs per
+    // SM (152 SMs), as for the short requests of the serving path
+    const int64_t per = (p.nq + 152 * 8 * fin_warps<T>() - 1) / (152 * 8 * fin_warps<T>());
+    const int wpw = (int)(per < 1 ? 1 : (per > 32 ? 32 : per));
+    const int nb = fin_warps<T>() * wpw;
+    int64_t grid = (p.nq + nb - 1) / nb;  // one block of query windows per CTA and pass
     if (grid > 152 * 64) grid = 152 * 64;
-    k_finalize_blk<T, KPL><<<(unsigned)grid, kNB, 0, st>>>(p);
+    k_finalize_blk<T, KPL><<<(unsigned)grid, kNB, 0, st>>>(p, wpw);
     return cudaGetLastError();
 }
 
