@@ -294,13 +294,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
 }
 
 // ---------------------------------------------------------------------------
-// Block form for m <= kFinMaxM. A CTA takes kFinBlock = 32 * fin_warps<T>()
-// consecutive query windows at a time, in three phases:
+// Block form for m <= kFinMaxM. A CTA takes a block of fin_warps<T>() * wpw
+// consecutive query windows at a time (wpw = 1 .. 32 windows per warp, 32 for
+// large joins, fewer for short ones so that they still fill the GPU), in three
+// phases:
 //   1. one thread per window: the reduction of the column groups' partials,
 //      the near-tie candidates, the constant-window cases and the window's
 //      statistics, with loads that are coalesced across the block and no
 //      per-window shuffles; the results go to shared memory;
-//   2. one warp per window (each warp takes 32 of the block's windows): the
+//   2. one warp per window (each warp takes wpw of the block's windows): the
 //      re-scoring of the winning chunk and of the candidates, and the chosen
 //      pair's distance from the staged samples;
 //   3. one thread per window again: the constant-window rule and the output.
