@@ -353,6 +353,26 @@ int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t n, double t
 int mp_profile(mp_ctx *ctx, int32_t enable);
 int mp_profile_read(mp_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
 
+/* Counters of the finalisation step of Algorithm 2's element-wise minimum (Sec. 3.2), for mp_counters. */
+#define MP_COUNTER_NEAR_ROWS 0      /* query windows that re-scored near-tied chunks besides the winner */
+#define MP_COUNTER_NEAR_CHUNKS 1    /* near-tied chunks (16 dictionary windows each) re-scored */
+#define MP_COUNTER_OVERFLOW_ROWS 2  /* query windows whose near-tie records of a column group overflowed */
+#define MP_COUNTER_OVERFLOW_CHUNKS 3 /* chunks re-scored because of those overflows (whole column groups) */
+#define MP_COUNTER_COUNT 4
+
+/*
+ * Counters summed over every join of this context (synchronous, device,
+ * no-allocation and serving) since the last reset. The join kernels keep an
+ * approximate score per 16-window chunk; the finalisation re-scores exactly
+ * the winning chunk and every chunk whose approximate score came within the
+ * form's near-tie width of the best (the kernels record up to a fixed number
+ * of such chunks per column group and query window; when a record that might
+ * matter has to be dropped, the finalisation re-scores that whole column
+ * group for that window instead). values: MP_COUNTER_COUNT int64 (host).
+ * Waits for all work on the context's device; reset = 1 zeroes them.
+ */
+int mp_counters(mp_ctx *ctx, int64_t *values, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

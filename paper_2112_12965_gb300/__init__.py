@@ -43,6 +43,12 @@ MP_PHASE_FINALIZE = 2
 MP_PHASE_SEEDS = 3
 MP_PHASE_COUNT = 4
 
+MP_COUNTER_NEAR_ROWS = 0
+MP_COUNTER_NEAR_CHUNKS = 1
+MP_COUNTER_OVERFLOW_ROWS = 2
+MP_COUNTER_OVERFLOW_CHUNKS = 3
+MP_COUNTER_COUNT = 4
+
 MP_LEARN_MEMORY = 0
 MP_LEARN_EMAX = 1
 
@@ -118,6 +124,7 @@ def _load():
         "mp_autotune": ([P, P, i32, i64, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32),
                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mp_profile_read": ([P, P, P, i32], ctypes.c_int),
+        "mp_counters": ([P, P, i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -319,6 +326,13 @@ def mp_profile_read(ctx, reset: bool = False) -> Tuple[np.ndarray, np.ndarray]:
     n = np.zeros(MP_PHASE_COUNT, dtype=np.int64)
     _check(lib.mp_profile_read(ctx, _ptr(ms), _ptr(n), 1 if reset else 0))
     return ms, n
+
+
+def mp_counters(ctx, reset: bool = False) -> np.ndarray:
+    """Finalisation counters (MP_COUNTER_*) summed over the context's joins since the last reset."""
+    v = np.zeros(MP_COUNTER_COUNT, dtype=np.int64)
+    _check(lib.mp_counters(ctx, _ptr(v), 1 if reset else 0))
+    return v
 
 
 def mp_autotune(ctx, d, m: int, n: int, tolerance: float = 1e-4) -> Tuple[int, int, float]:

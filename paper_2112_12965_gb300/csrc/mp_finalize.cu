@@ -173,10 +173,58 @@ __device__ __forceinline__ void rescore_chunk(const T *__restrict__ pa, const T 
     g_out = gw;
 }
 
+// Entry e of query window i's near-tie candidates, with per = S + 1 entries per
+// column group k = e / per: entry 0 is the group's winning chunk, entry u > 0
+// its record u - 1. Returns the chunk if it differs from the overall winner g
+// and its approximate score reaches lim, else -1; sets ovf if group k's
+// records overflowed (tested at entry 1).
+template <typename T>
+__device__ __forceinline__ int32_t near_entry(const FinalizeParams<T> &p, int64_t i, int64_t e, int per, int64_t tot,
+                                              int32_t g, T lim, bool &ovf)
+{
+    if (e >= tot) return -1;
+    const int64_t k = e / per;
+    const int u = (int)(e - k * per);
+    if (u == 0) {
+        const Partial<T> v = p.part[k * p.nq + i];
+        return (v.g >= 0 && v.g != g && v.q >= lim) ? v.g : -1;
+    }
+    const unsigned f = p.near.flag[k * p.near.ld + i];
+    if (u == 1 && (f & kNearOverflow)) ovf = true;
+    if (u - 1 >= (int)(f & kNearCountMask)) return -1;
+    const NearSlot sl = p.near.slot[(k * p.near.S + u - 1) * p.near.ld + i];
+    return (sl.g != g && T(sl.q) >= lim) ? sl.g : -1;
+}
+
+// Near-tie width of query window i in units of its score q, the width the
+// join used (NearRec): the plain form's rho m std_a, or the tensor-core
+// forms' bound 2 u m sqrt(std_a^2 + da^2) F_b, da = mean_a - s_a with s_a the
+// shift of the window's CTA of kTcRows windows.
+template <typename T>
+__device__ __forceinline__ T near_width(const FinalizeParams<T> &p, int64_t i, T isa, const Split<T> &ma)
+{
+    if (p.near.fb == nullptr) return T(p.near.rho) * T(p.m) / isa;
+    const T s_a = p.ms_a[(i / kTcRows) * kTcRows].hi;
+    const T da = (ma.hi - s_a) + ma.lo;
+    const T sd = T(1) / isa;
+    return T(2) * T(p.near.u) * T(p.m) * sqrt(fma(sd, sd, da * da)) * T(*p.near.fb);
+}
+
+// Add a CTA's counters (shared) to the global ones; every thread calls it.
+__device__ __forceinline__ void flush_counters(unsigned long long *ctr, unsigned long long *s_ctr)
+{
+    __syncthreads();
+    if (ctr != nullptr && threadIdx.x < kFinCounters && s_ctr[threadIdx.x] != 0)
+        atomicAdd(&ctr[threadIdx.x], s_ctr[threadIdx.x]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(FinalizeParams<T> p)
 {
     __shared__ T fin_smem[8][2 * kFinWarpVals];
+    __shared__ unsigned long long s_ctr[kFinCounters];
+    if (threadIdx.x < kFinCounters) s_ctr[threadIdx.x] = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     T *wa = fin_smem[threadIdx.x >> 5];
     T *wb = wa + kFinWarpVals;
@@ -238,39 +286,55 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                     int32_t gw;
                     rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, g, ma, lane, wa, wb, sc,
                                      gw, p.excl);
-                    if (p.near != nullptr) {
-                        const T lim = q - T(kNearTieRho) * T(m) / p.rs_a[i].z;  // the row is not constant: z > 0
-                        for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
-                            const int k = k0 + lane;
-                            int32_t c0 = -1, c1 = -1, c2 = -1;
-                            if (k < p.n_groups) {
-                                const Partial<T> v = p.part[(int64_t)k * p.nq + i];
-                                if (v.g >= 0 && v.g != g && v.q >= lim) c0 = v.g;
-                                const NearTies nt = p.near[(int64_t)k * p.nq + i];
-                                if (nt.g0 >= 0 && nt.g0 != g && T(nt.q0) >= lim) c1 = nt.g0;
-                                if (nt.g1 >= 0 && nt.g1 != g && T(nt.q1) >= lim) c2 = nt.g1;
+                    if (p.near.slot != nullptr) {
+                        const T lim = q - near_width(p, i, p.rs_a[i].z, ma);  // the row is not constant: z > 0
+                        auto consider = [&](int32_t cu) {
+                            T s2;
+                            int32_t g2;
+                            rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, cu, ma, lane, wa, wb,
+                                             s2, g2, p.excl);
+                            if (better(s2, g2, sc, gw)) {
+                                sc = s2;
+                                gw = g2;
                             }
-                            unsigned pend = __ballot_sync(0xffffffffu, c0 >= 0 || c1 >= 0 || c2 >= 0);
+                        };
+                        // other groups' winners and the records, one (group, entry) per lane
+                        const int per = p.near.S + 1;
+                        const int64_t tot = (int64_t)p.n_groups * per;
+                        bool ovf = false;
+                        unsigned extra = 0;
+                        for (int64_t e0 = 0; e0 < tot; e0 += 32) {
+                            const int32_t c = near_entry(p, i, e0 + lane, per, tot, g, lim, ovf);
+                            unsigned pend = __ballot_sync(0xffffffffu, c >= 0);
                             while (pend) {
                                 const int src = __ffs(pend) - 1;
                                 pend &= pend - 1;
-                                const int32_t s0 = __shfl_sync(0xffffffffu, c0, src);
-                                const int32_t s1 = __shfl_sync(0xffffffffu, c1, src);
-                                const int32_t s2c = __shfl_sync(0xffffffffu, c2, src);
-#pragma unroll 1
-                                for (int u = 0; u < 3; ++u) {
-                                    const int32_t cu = u == 0 ? s0 : (u == 1 ? s1 : s2c);
-                                    if (cu < 0) continue;
-                                    T s2;
-                                    int32_t g2;
-                                    rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, cu, ma, lane,
-                                                     wa, wb, s2, g2, p.excl);
-                                    if (better(s2, g2, sc, gw)) {
-                                        sc = s2;
-                                        gw = g2;
+                                consider(__shfl_sync(0xffffffffu, c, src));
+                                ++extra;
+                            }
+                        }
+                        unsigned ochunks = 0;
+                        const bool any_ovf = __any_sync(0xffffffffu, ovf);
+                        if (any_ovf) {
+                            // a record within the width was dropped: every chunk of that group
+                            for (int k = 0; k < p.n_groups; ++k) {
+                                if (!(p.near.flag[(int64_t)k * p.near.ld + i] & kNearOverflow)) continue;
+                                for (int sp = p.cgroup_start[k]; sp < p.cgroup_start[k + 1]; ++sp) {
+                                    const Span span = p.cspans[sp];
+                                    for (int c0 = 0; c0 < span.ncols; c0 += kChunk) {
+                                        const int32_t cu = (int32_t)(span.g0 + c0);
+                                        if (cu == g) continue;
+                                        consider(cu);
+                                        ++ochunks;
                                     }
                                 }
                             }
+                        }
+                        if (lane == 0 && (extra > 0 || any_ovf)) {
+                            atomicAdd(&s_ctr[0], extra > 0 ? 1ull : 0ull);
+                            atomicAdd(&s_ctr[1], (unsigned long long)extra);
+                            atomicAdd(&s_ctr[2], any_ovf ? 1ull : 0ull);
+                            atomicAdd(&s_ctr[3], (unsigned long long)ochunks);
                         }
                     }
                     if (gw >= 0) {
@@ -291,6 +355,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
             p.out_idx[i] = gi;
         }
     }
+    flush_counters(p.ctr, s_ctr);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,7 +384,7 @@ template <typename T> constexpr int fin_warps() { return sizeof(T) == 8 ? 2 : 4;
 __device__ __forceinline__ int qidx(int e) { return e + (e >> 5); }
 // near-tie candidates kept per window in shared memory; a window with more
 // scans the column groups' records again in phase 2
-constexpr int kFinMaxCand = 4;
+constexpr int kFinMaxCand = 8;
 
 __host__ __device__ constexpr int fin_kpl(int m) { return ((m + 15) / 16 + 7) / 8 * 8; }
 
@@ -446,8 +511,10 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
     __shared__ int32_t s_cand[kFinMaxCand][kNB];
     __shared__ int32_t s_gi[kNB];                // phase 2's window (-1: none)
     __shared__ T s_mhi[kNB], s_mlo[kNB], s_isa[kNB], s_lim[kNB], s_d[kNB];
+    __shared__ unsigned long long s_ctr[kFinCounters];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kFinCounters) s_ctr[tid] = 0;  // published by the first block's barrier
     T *const qa = f_buf[warp];
     T *const wb = qa + kQV;
     const int m = p.m;
@@ -473,6 +540,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
         int64_t gi = -1, gcst = -1;
         int32_t g = -1;
         int nc = 0;
+        bool ovf = false;   // a column group's records overflowed for this window
         bool resc = false;  // phase 2 re-scores this window
         if (mine && i < p.nq && p.g_first >= 0) {
             if (p.cflag_a[i]) {
@@ -504,24 +572,27 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                     s_mhi[tid] = ma.hi;
                     s_mlo[tid] = ma.lo;
                     s_isa[tid] = isa;
-                    if (p.near != nullptr) {
+                    if (p.near.slot != nullptr) {
                         // every other chunk whose approximate score came within the
                         // near-tie width of the best (other groups' winners and the
-                        // plain kernel's near-tie records) is re-scored too, so that
-                        // the recurrence's rounding cannot decide between near ties
-                        const T lim = q - T(kNearTieRho) * T(m) / isa;
+                        // join's near-tie records) is re-scored too, so that the
+                        // join's rounding cannot decide between near ties
+                        const T lim = q - near_width(p, i, isa, ma);
                         s_lim[tid] = lim;
-#pragma unroll 2
+                        const int S = p.near.S;
                         for (int k = 0; k < p.n_groups; ++k) {
                             const Partial<T> v = p.part[(int64_t)k * p.nq + i];
-                            const NearTies nt = p.near[(int64_t)k * p.nq + i];
-                            const int32_t c3[3] = {v.g >= 0 && v.g != g && v.q >= lim ? v.g : -1,
-                                                   nt.g0 >= 0 && nt.g0 != g && T(nt.q0) >= lim ? nt.g0 : -1,
-                                                   nt.g1 >= 0 && nt.g1 != g && T(nt.q1) >= lim ? nt.g1 : -1};
-#pragma unroll
-                            for (int u = 0; u < 3; ++u) {
-                                if (c3[u] >= 0) {
-                                    if (nc < kFinMaxCand) s_cand[nc][tid] = c3[u];
+                            if (v.g >= 0 && v.g != g && v.q >= lim) {
+                                if (nc < kFinMaxCand) s_cand[nc][tid] = v.g;
+                                ++nc;
+                            }
+                            const unsigned f = p.near.flag[(int64_t)k * p.near.ld + i];
+                            ovf |= (f & kNearOverflow) != 0;
+                            const int n = (int)(f & kNearCountMask);
+                            for (int u = 0; u < n && u < S; ++u) {
+                                const NearSlot sl = p.near.slot[((int64_t)k * S + u) * p.near.ld + i];
+                                if (sl.g != g && T(sl.q) >= lim) {
+                                    if (nc < kFinMaxCand) s_cand[nc][tid] = sl.g;
                                     ++nc;
                                 }
                             }
@@ -531,7 +602,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
             }
         }
         s_g[tid] = resc ? g : -1;
-        s_nc[tid] = nc;
+        s_nc[tid] = ovf ? -1 : nc;  // -1: scan the records again and re-score the overflowed groups
         __syncthreads();
 
         // ---- phase 2: this warp's 32 windows, one at a time ----
@@ -554,60 +625,62 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
             rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, g0, lane, wb, sc, gw, iw, p.excl);
             int32_t staged = g0;  // the chunk whose samples wb holds (and whose terms ct and sb are)
             int32_t win = g0;     // the chunk of the best window so far
+            unsigned extra = 0, ochunks = 0;
+            auto consider = [&](int32_t cu) {
+                T s2;
+                int32_t g2;
+                ct = load_cand(p.rs_b, p.ms_b, p.npos_b, cu, lane);
+                sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
+                rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
+                staged = cu;
+                if (better(s2, g2, sc, gw)) {
+                    sc = s2;
+                    gw = g2;
+                    win = cu;
+                }
+            };
             const int ncw = s_nc[t];
             if (ncw > 0 && ncw <= kFinMaxCand) {
-                for (int c = 0; c < ncw; ++c) {
-                    const int32_t cu = s_cand[c][t];
-                    T s2;
-                    int32_t g2;
-                    ct = load_cand(p.rs_b, p.ms_b, p.npos_b, cu, lane);
-                    sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
-                    rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
-                    staged = cu;
-                    if (better(s2, g2, sc, gw)) {
-                        sc = s2;
-                        gw = g2;
-                        win = cu;
-                    }
-                }
-            } else if (ncw > kFinMaxCand) {
-                // more candidates than the shared list holds: scan the records again
+                for (int c = 0; c < ncw; ++c) consider(s_cand[c][t]);
+                extra = ncw;
+            } else if (ncw != 0) {
+                // more candidates than the shared list holds, or overflowed
+                // records: scan the entries again, one (group, entry) per lane
                 const T lim = s_lim[t];
-                for (int k0 = 0; k0 < p.n_groups; k0 += 32) {
-                    const int k = k0 + lane;
-                    int32_t c0 = -1, c1 = -1, c2 = -1;
-                    if (k < p.n_groups) {
-                        const Partial<T> v = p.part[(int64_t)k * p.nq + iw];
-                        if (v.g >= 0 && v.g != g0 && v.q >= lim) c0 = v.g;
-                        const NearTies nt = p.near[(int64_t)k * p.nq + iw];
-                        if (nt.g0 >= 0 && nt.g0 != g0 && T(nt.q0) >= lim) c1 = nt.g0;
-                        if (nt.g1 >= 0 && nt.g1 != g0 && T(nt.q1) >= lim) c2 = nt.g1;
-                    }
-                    unsigned pend = __ballot_sync(0xffffffffu, c0 >= 0 || c1 >= 0 || c2 >= 0);
+                const int per = p.near.S + 1;
+                const int64_t tot = (int64_t)p.n_groups * per;
+                bool o = false;
+                for (int64_t e0 = 0; e0 < tot; e0 += 32) {
+                    const int32_t c = near_entry(p, iw, e0 + lane, per, tot, g0, lim, o);
+                    unsigned pend = __ballot_sync(0xffffffffu, c >= 0);
                     while (pend) {
                         const int src = __ffs(pend) - 1;
                         pend &= pend - 1;
-                        const int32_t s0 = __shfl_sync(0xffffffffu, c0, src);
-                        const int32_t s1 = __shfl_sync(0xffffffffu, c1, src);
-                        const int32_t s2c = __shfl_sync(0xffffffffu, c2, src);
-#pragma unroll 1
-                        for (int u = 0; u < 3; ++u) {
-                            const int32_t cu = u == 0 ? s0 : (u == 1 ? s1 : s2c);
-                            if (cu < 0) continue;
-                            T s2;
-                            int32_t g2;
-                            ct = load_cand(p.rs_b, p.ms_b, p.npos_b, cu, lane);
-                            sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, cu, lane, wb);
-                            rescore_staged<T, KPL>(p.npos_b, m, ct, sb, qa, ma.lo, cu, lane, wb, s2, g2, iw, p.excl);
-                            staged = cu;
-                            if (better(s2, g2, sc, gw)) {
-                                sc = s2;
-                                gw = g2;
-                                win = cu;
+                        consider(__shfl_sync(0xffffffffu, c, src));
+                        ++extra;
+                    }
+                }
+                if (ncw < 0) {
+                    // a record within the width was dropped: every chunk of that group
+                    for (int k = 0; k < p.n_groups; ++k) {
+                        if (!(p.near.flag[(int64_t)k * p.near.ld + iw] & kNearOverflow)) continue;
+                        for (int sp = p.cgroup_start[k]; sp < p.cgroup_start[k + 1]; ++sp) {
+                            const Span span = p.cspans[sp];
+                            for (int c0 = 0; c0 < span.ncols; c0 += kChunk) {
+                                const int32_t cu = (int32_t)(span.g0 + c0);
+                                if (cu == g0) continue;
+                                consider(cu);
+                                ++ochunks;
                             }
                         }
                     }
                 }
+            }
+            if (lane == 0 && (extra > 0 || ncw < 0)) {
+                atomicAdd(&s_ctr[0], extra > 0 ? 1ull : 0ull);
+                atomicAdd(&s_ctr[1], (unsigned long long)extra);
+                atomicAdd(&s_ctr[2], ncw < 0 ? 1ull : 0ull);
+                atomicAdd(&s_ctr[3], (unsigned long long)ochunks);
             }
             T dw = T(INFINITY);
             if (gw >= 0) {
@@ -660,6 +733,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
         }
         __syncthreads();  // the next block rewrites the per-window arrays
     }
+    flush_counters(p.ctr, s_ctr);
 }
 
 template <typename T, int KPL> cudaError_t launch_blk(const FinalizeParams<T> &p, cudaStream_t st)

@@ -78,22 +78,91 @@ template <typename T> struct Partial {
     int32_t g;
 };
 
-// Near-tie records of the FP32 plain kernel for one (column group, query
-// window): up to two chunks (first window g, -1 if unused) whose approximate
-// score q came within kNearTieRho (in Pearson correlation) below the running
-// best, or that were the best until overtaken by less than that. The
-// recurrence's rounding can misorder such chunks; the finalisation re-scores
-// each of them exactly, so the pick does not depend on that rounding.
-struct __align__(16) NearTies {
-    int32_t g0;
-    float q0;
-    int32_t g1;
-    float q1;
+// Near-tie records of a join for one (column group, query window): up to S
+// chunks (first window g and approximate score q) whose score came within the
+// near-tie width below the running best, or that were the best until
+// overtaken by less than the width. The join's rounding (the FP32 recurrence,
+// or the tensor cores' operand rounding) can misorder such chunks; the
+// finalisation re-scores each of them exactly, so the pick does not depend on
+// that rounding. A record is dropped only when all S slots are in use; if the
+// dropped score may still lie within the width of the final best, the
+// overflow bit is set and the finalisation re-scores every chunk of that
+// column group for that window.
+struct NearSlot {
+    int32_t g;
+    float q;
 };
-// Near-tie width in correlation, many times the FP32 recurrence's error
-// (about 1e-6 to 5e-6 in rho measured over 512-step diagonals; the diagonals
-// of 32 lanes x 20 rows run up to 640 steps between seeds).
-constexpr float kNearTieRho = 4e-5f;
+constexpr unsigned kNearCountMask = 0x3fu;  // flag bits 0-5: slots in use
+constexpr unsigned kNearOverflow = 0x80u;   // flag bit 7: a record within the width was dropped
+constexpr int kNearMaxSlots = 32;
+struct NearRec {
+    NearSlot *slot;   // [n_groups][S][ld]: slot u of (group k, row r) at (k * S + u) * ld + r; null: no records
+    uint8_t *flag;    // [n_groups][ld]: slots in use | kNearOverflow; the join zeroes the flags of its rows
+    int64_t ld;       // row stride of slot and flag
+    int32_t S;        // slots per (group, row), 1 .. kNearMaxSlots
+    float rho;        // plain form: width in Pearson correlation
+    const float *fb;  // tensor-core forms (rho unused): the dictionary's column factor F_b, below
+    float u;          // tensor-core forms: bound on the relative error of the products and their sum
+};
+// Width of the plain FP32 recurrence, in correlation: 8x the largest drift
+// measured by a float32 model of the recurrence on the benchmark data (about
+// 1e-6 to 5e-6 over the up to 640-step diagonals between seeds, 32 lanes x 20
+// rows).
+constexpr float kNearRhoFP32 = 4e-5f;
+// Tensor-core forms: a bound, not a measurement. The product sum S of the
+// shifted operands a' = a - s_a, b' = b - s_b (per-CTA and per-tile shifts)
+// errs by at most u * sum_k |a'_k b'_k| <= u ||a'|| ||b'|| (Cauchy-Schwarz),
+// with u the relative error of one product plus that of the FP32 sum. In
+// units of the score q = C / std_b this is u m sqrt(std_a^2 + da^2) F_b, where
+// da = mean_a - s_a and F_b = max over the dictionary's windows of
+// sqrt(1 + ((mean_b - s_b) / std_b)^2). The width is twice that (two chunks
+// err in opposite directions), so a chunk left out is surely not the best.
+//   single TF32 product: operands rounded to 11 significant bits (2^-11 each)
+//   split BF16 (hi*hi + hi*lo + lo*hi): hi + lo within 2^-18 of each operand,
+//     lo*lo left out: 3 * 2^-18
+//   FP32 sum of the m (TF32) or 3m (split BF16) products: 2^-23 per product
+constexpr float kTcUnitTF32 = 9.7752e-4f;    // 2^-10 + 2^-21
+constexpr float kTcUnitBF16X3 = 1.1445e-5f;  // 3 * 2^-18
+constexpr int kNearSlotsPlain = 4;
+constexpr int kNearSlotsTC = 32;
+constexpr int kTcRows = 128;  // query windows per CTA of the tensor-core join (one per TMEM lane)
+
+#ifdef __CUDACC__
+// Record chunk g with approximate score q for (group k, row r). floor_q is
+// the running best minus the width: a record below it can never come within
+// the width of the final best, so dropping it needs no overflow mark. The
+// caller owns (k, r) exclusively for the whole join.
+__device__ __forceinline__ void near_add(const NearRec &nr, int64_t k, int64_t r, int32_t g, float q, float floor_q)
+{
+    uint8_t *fp = nr.flag + k * nr.ld + r;
+    const unsigned f = *fp;
+    const int n = (int)(f & kNearCountMask);
+    NearSlot *base = nr.slot + k * (int64_t)nr.S * nr.ld + r;
+    if (n < nr.S) {
+        base[(int64_t)n * nr.ld] = NearSlot{g, q};
+        *fp = (uint8_t)((f & kNearOverflow) | (unsigned)(n + 1));
+        return;
+    }
+    // all S slots in use: replace the lowest-scoring one if q is higher; the
+    // record dropped (that one, or q itself) sets the overflow bit if it may
+    // still lie within the width of the final best
+    int lo = 0;
+    float qlo = base[0].q;
+    for (int u = 1; u < nr.S; ++u) {
+        const float qu = base[(int64_t)u * nr.ld].q;
+        if (qu < qlo) {
+            qlo = qu;
+            lo = u;
+        }
+    }
+    float dropped = q;
+    if (q > qlo) {
+        dropped = qlo;
+        base[(int64_t)lo * nr.ld] = NearSlot{g, q};
+    }
+    if (dropped >= floor_q) *fp = (uint8_t)(f | kNearOverflow);
+}
+#endif
 
 struct PlainLaunch {
     int64_t nq;            // query windows
@@ -113,13 +182,13 @@ struct PlainLaunch {
 // seed_top (may be null): the centred covariances of each warp's first query
 // window, row r / (32 * rows per lane) at column g, row stride seed_ld (as
 // written by tc_seeds); null makes the kernel compute them itself.
-// near (may be null; FP32 only): [n_groups][nq] near-tie records, written
-// for every query window.
+// near (near.slot may be null; FP32 only): near-tie records of every query
+// window; near.ld must equal the partial results' row stride.
 template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
-                         NearTies *near, cudaStream_t st);
+                         const NearRec &near, cudaStream_t st);
 template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
 template <typename T> size_t plain_smem_bytes(int warps, int m, int rows_per_lane = plain_rows_per_lane<T>());
 // Resident CTAs per SM of the plain kernel for this shape (occupancy API).
@@ -144,7 +213,7 @@ struct PlainRequest {
     Partial<float> *part;
     const float *seed_top;  // always null: batched work computes its own seeds
     int64_t seed_ld;
-    NearTies *near;         // [n_groups][nq] near-tie records (required)
+    NearRec near;           // near-tie records (required), ld = nq
     int64_t ld_part;        // nq
     int64_t row0;           // 0
     int32_t excl;           // 0: serving joins are AB-joins
@@ -182,7 +251,12 @@ template <typename T> struct FinalizeParams {
     double *out_dist;
     int64_t *out_idx;
     const int32_t *err;       // may be null; if *err != 0 a tensor-core wait ran out: NaN / -1 everywhere
-    const NearTies *near;     // may be null; [n_groups][nq] near-tie records of the plain kernel
+    NearRec near;             // near-tie records of the join (near.slot null: none), ld = nq
+    // chunk layout of the column groups, for windows whose records overflowed:
+    // chunks g0 + 16 j of cspans[cgroup_start[k] .. cgroup_start[k+1]) are group k's
+    const Span *cspans;
+    const int32_t *cgroup_start;
+    unsigned long long *ctr;  // may be null; kFinCounters counters, added to (see below)
     int32_t out_corr;         // 1: write rho = 1 - d^2 / (2m) (Pearson's r for non-constant windows), -inf if none
     // Self-join of one series (dictionary learning): windows g with |g - i| < excl are
     // trivial matches of query window i and are left out; next_const[x] is the lowest
@@ -190,6 +264,10 @@ template <typename T> struct FinalizeParams {
     int32_t excl;
     const int64_t *next_const;
 };
+// Finalisation counters (FinalizeParams::ctr): query windows with near-tie
+// candidates re-scored, near-tie chunks re-scored, windows whose records
+// overflowed, chunks re-scored for them.
+constexpr int kFinCounters = 4;
 template <typename T> cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st);
 
 // Dictionary learning (Algorithm 1) kernels, mp_learn.cu.

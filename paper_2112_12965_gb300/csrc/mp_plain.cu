@@ -61,34 +61,11 @@ template <typename T> struct PlainParams {
     Partial<T> *part;
     const T *seed_top;  // top seeds from the tensor cores, or null
     int64_t seed_ld;
-    NearTies *near;     // near-tie records, or null
+    NearRec near;       // near-tie records (near.ld = ld_part), or near.slot null
     int64_t ld_part;    // row stride of part and near (>= nq)
     int64_t row0;       // self-join: position in the series of query window 0
     int32_t excl;       // self-join: pairs with |g - (row0 + r)| < excl are left out (0: none)
 };
-
-// Add a near-tie record (chunk g, approximate score q) to a slot; with both
-// entries in use, the lower-scoring one is replaced if q is higher.
-__device__ __forceinline__ void near_record(NearTies *slot, int32_t g, float q)
-{
-    NearTies v = *slot;
-    if (v.g0 < 0) {
-        v.g0 = g;
-        v.q0 = q;
-    } else if (v.g1 < 0) {
-        v.g1 = g;
-        v.q1 = q;
-    } else if (q > fminf(v.q0, v.q1)) {
-        if (v.q0 <= v.q1) {
-            v.g0 = g;
-            v.q0 = q;
-        } else {
-            v.g1 = g;
-            v.q1 = q;
-        }
-    }
-    *slot = v;
-}
 
 // Asynchronous copy of one element from global to shared memory; zero-fills
 // the destination when !valid (src is then not read).
@@ -293,7 +270,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             R.set_terms(j, v.x, v.y);
             if (kNear) {
                 if (v.z > T(0)) sig_max = fmax(sig_max, T(1) / v.z);
-                p.near[(int64_t)grp * p.ld_part + r] = NearTies{-1, 0.f, -1, 0.f};
+                p.near.flag[(int64_t)grp * p.ld_part + r] = 0;  // no records yet
             }
         } else {
             R.set_terms(j, T(0), T(0));
@@ -304,7 +281,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
     }
     // near-tie width in units of the score q = C * invstd_b (q = rho * m * std_a),
     // taken with the lane's largest std so that it covers every row of the lane
-    const T tq = T(kNearTieRho) * T(m) * sig_max;
+    const T tq = T(p.near.rho) * T(m) * sig_max;
     const Split<T> mw = p.ms_a[r_w < p.nq ? r_w : p.nq - 1];
     const T da_w = (mw.hi - shift_a) + mw.lo;
     const int sa_w = warp * 32 * kRows;      // sa index of this warp's first row
@@ -517,8 +494,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                         for (int j = 0; j < kRows; ++j) {
                             if (fabs(cm[j] - best[j]) <= tq && r0 + j < p.nq) {
                                 const bool upd = cm[j] > best[j];
-                                near_record(p.near + (int64_t)grp * p.ld_part + r0 + j, upd ? bchunk[j] : gch,
-                                            (float)(upd ? best[j] : cm[j]));
+                                near_add(p.near, grp, r0 + j, upd ? bchunk[j] : gch, (float)(upd ? best[j] : cm[j]),
+                                         (float)(fmax(cm[j], best[j]) - tq));
                             }
                         }
                     }
@@ -597,7 +574,7 @@ template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
-                         NearTies *near, cudaStream_t st)
+                         const NearRec &near, cudaStream_t st)
 {
     PlainParams<T> p{};
     p.a = a;
@@ -631,17 +608,19 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     };
     if constexpr (sizeof(T) == 8) {
         // FP64 data: seeds from direct dot products, no near-tie records
-        if (seed_top != nullptr || near != nullptr || L.excl > 0) return cudaErrorInvalidValue;
+        if (seed_top != nullptr || near.slot != nullptr || L.excl > 0) return cudaErrorInvalidValue;
         return launch(k_plain<T, R, false, false>);
     } else {
+        if (near.slot != nullptr && (near.ld != p.ld_part || near.S < 1 || near.S > kNearMaxSlots))
+            return cudaErrorInvalidValue;
         if (L.excl > 0) {
             // self-join (dictionary learning): tensor-core seeds and near-tie records
-            if (seed_top == nullptr || near == nullptr) return cudaErrorInvalidValue;
+            if (seed_top == nullptr || near.slot == nullptr) return cudaErrorInvalidValue;
             return launch(k_plain<T, R, true, true, true>);
         }
         if (seed_top != nullptr)
-            return near != nullptr ? launch(k_plain<T, R, true, true>) : launch(k_plain<T, R, true, false>);
-        return near != nullptr ? launch(k_plain<T, R, false, true>) : launch(k_plain<T, R, false, false>);
+            return near.slot != nullptr ? launch(k_plain<T, R, true, true>) : launch(k_plain<T, R, true, false>);
+        return near.slot != nullptr ? launch(k_plain<T, R, false, true>) : launch(k_plain<T, R, false, false>);
     }
 }
 
@@ -683,10 +662,10 @@ template size_t plain_smem_bytes<double>(int, int, int);
 template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,
                                          const Split<float> *, const float *, int64_t, const float4 *,
                                          const Split<float> *, const Span *, const int32_t *, Partial<float> *,
-                                         const float *, int64_t, NearTies *, cudaStream_t);
+                                         const float *, int64_t, const NearRec &, cudaStream_t);
 template cudaError_t launch_plain<double>(const PlainLaunch &, const double *, int64_t, const dvec4 *,
                                           const Split<double> *, const double *, int64_t, const dvec4 *,
                                           const Split<double> *, const Span *, const int32_t *, Partial<double> *,
-                                          const double *, int64_t, NearTies *, cudaStream_t);
+                                          const double *, int64_t, const NearRec &, cudaStream_t);
 
 }  // namespace mpd

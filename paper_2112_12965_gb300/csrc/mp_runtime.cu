@@ -91,6 +91,7 @@ struct DictStats {
     void *rs = nullptr;         // float4 / dvec4 recurrence terms
     void *ms = nullptr;         // Split<float> / Split<double> window means
     std::vector<Span> seg_spans;  // one span per segment with at least one window
+    Span *d_seg_spans = nullptr;  // the same on the device
     int64_t n_windows = 0;        // W
     int64_t g_const = -1, g_first = -1;
     // column grouping cache: n_groups -> (device spans, device group_start)
@@ -209,6 +210,9 @@ struct mp_ctx {
     std::map<TuneKey, TuneVal> tune;
     std::string tune_path;
     int force_groups = 0;  // set while the autotuner times a candidate
+
+    // finalisation counters (kFinCounters, summed on the device by every join)
+    unsigned long long *d_counters = nullptr;
 };
 
 static void tune_load(mp_ctx *ctx, const char *path);
@@ -373,6 +377,7 @@ static int get_stats(mp_ctx *ctx, mp_dict *d, int32_t m, DictStats **out)
             Span *dsp = nullptr;
             int64_t *dsv = nullptr;
             CUDA_TRY(cudaMalloc(&dsp, s->seg_spans.size() * sizeof(Span)));
+            s->d_seg_spans = dsp;  // kept: the join without allocation cuts its column groups from it
             CUDA_TRY(cudaMalloc(&dsv, 2 * sizeof(int64_t)));
             CUDA_TRY(cudaMemcpyAsync(dsp, s->seg_spans.data(), s->seg_spans.size() * sizeof(Span),
                                      cudaMemcpyHostToDevice, ctx->stream));
@@ -381,7 +386,6 @@ static int get_stats(mp_ctx *ctx, mp_dict *d, int32_t m, DictStats **out)
             int64_t hv[2];
             CUDA_TRY(cudaMemcpyAsync(hv, dsv, sizeof hv, cudaMemcpyDeviceToHost, ctx->stream));
             CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-            cudaFree(dsp);
             cudaFree(dsv);
             s->g_const = hv[0];
             s->g_first = hv[1];
@@ -441,6 +445,7 @@ static int get_grouping(mp_ctx *ctx, DictStats *s, int n_groups, DictStats::Grou
 
 static void free_stats(DictStats *s)
 {
+    cudaFree(s->d_seg_spans);
     cudaFree(s->mean);
     cudaFree(s->invstd);
     cudaFree(s->cflag);
@@ -454,7 +459,7 @@ static void free_stats(DictStats *s)
 }
 
 template <typename T>
-static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const Partial<T> *part, const T *a,
+static FinalizeParams<T> fin_params(mp_ctx *ctx, int64_t nq, int32_t m, int n_groups, const Partial<T> *part, const T *a,
                                     const vec4_t<T> *rs_a, const Split<T> *ms_a, const uint8_t *cf_a,
                                     const mp_dict *d, const DictStats *s, double *dist, int64_t *idx)
 {
@@ -477,7 +482,10 @@ static FinalizeParams<T> fin_params(int64_t nq, int32_t m, int n_groups, const P
     f.out_dist = dist;
     f.out_idx = idx;
     f.err = nullptr;
-    f.near = nullptr;
+    f.near = NearRec{};
+    f.cspans = nullptr;
+    f.cgroup_start = nullptr;
+    f.ctr = ctx->d_counters;
     f.out_corr = 0;
     f.excl = 0;
     f.next_const = nullptr;
@@ -582,10 +590,17 @@ static int64_t plain_chunk_rows(const mp_dict *d, int32_t dtype, int64_t nq, int
 
 // Workspace layout of one join.
 struct JoinWs {
-    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_seed, total;
+    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_nflag, off_seed, total;
+    int near_slots;
 };
 
-static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front, size_t seed_bytes = 0)
+// Near-tie record slots per (column group, query window) a join form uses.
+static bool is_tc(int kernel) { return kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32; }
+static int near_slots_for(int kernel) { return is_tc(kernel) ? kNearSlotsTC : kNearSlotsPlain; }
+
+// near_slots: record slots per (column group, query window) of FP32 joins.
+static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front, size_t seed_bytes = 0,
+                             int near_slots = kNearSlotsPlain)
 {
     JoinWs w;
     // error word of the tensor-core kernels at the front
@@ -605,13 +620,30 @@ static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t ext
     o = align_up(o + nq * 2 * e, 256);
     w.off_part = o;
     o = align_up(o + (size_t)n_groups * nq * (e == 8 ? sizeof(Partial<double>) : sizeof(Partial<float>)), 256);
-    // near-tie records of the FP32 plain kernel, one per (column group, query window)
+    // near-tie records of FP32 joins: near_slots slots and one flag byte per
+    // (column group, query window)
+    w.near_slots = dtype == MP_F32 ? near_slots : 0;
     w.off_near = o;
-    if (dtype == MP_F32) o = align_up(o + (size_t)n_groups * nq * sizeof(NearTies), 256);
+    o = align_up(o + (size_t)n_groups * w.near_slots * nq * sizeof(NearSlot), 256);
+    w.off_nflag = o;
+    if (dtype == MP_F32) o = align_up(o + (size_t)n_groups * nq, 256);
     w.off_seed = o;
     o = align_up(o + seed_bytes, 256);
     w.total = o;
     return w;
+}
+
+// The near-tie records of a join laid out by w, for query windows of stride
+// ld (the tensor-core join adds its width's terms, fb and u).
+static NearRec near_rec(unsigned char *base, const JoinWs &w, int64_t ld)
+{
+    NearRec r{};
+    r.slot = (NearSlot *)(base + w.off_near);
+    r.flag = base + w.off_nflag;
+    r.ld = ld;
+    r.S = w.near_slots;
+    r.rho = kNearRhoFP32;
+    return r;
 }
 
 // Seed bytes a join of this shape reserves (FP32 joins that may take the
@@ -642,9 +674,9 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     const int64_t crow = plain_chunk_rows(d, dtype, nq, m, seeds);  // query windows per plain launch
     const Geometry geo = plain_geometry(ctx, crow, s->n_windows, rpl, dtype, m, (int64_t)s->seg_spans.size());
-    const bool tc = (kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32);
+    const bool tc = is_tc(kernel);
     JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0,
-                              join_seed_bytes(d, dtype, nq, m, seeds));
+                              join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel));
     int32_t *err = (int32_t *)(base + w.off_err);
     CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
     double *mean_a = (double *)(base + w.off_mean);
@@ -672,12 +704,12 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
             CUDA_TRY(launch_plain<double>(L, a, n, rs_a, ms_a, (const double *)d->d_samples, d->nb,
                                           (const dvec4 *)s->rs, (const Split<double> *)s->ms, gr->spans,
-                                          gr->group_start, part, nullptr, 0, nullptr, st));
+                                          gr->group_start, part, nullptr, 0, NearRec{}, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
             FinalizeParams<double> f =
-                fin_params<double>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
+                fin_params<double>(ctx, nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
             f.out_corr = corr ? 1 : 0;
             CUDA_TRY(launch_finalize<double>(f, st));
         }
@@ -691,26 +723,33 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         }
         if (tc) {
             Partial<float> *part = (Partial<float> *)(base + w.off_part);
+            NearRec near = near_rec(base, w, nq);
             int ng = 1;
+            const Span *cspans = nullptr;
+            const int32_t *cgs = nullptr;
             {
                 PhaseTimer t(ctx, MP_PHASE_JOIN, st);
                 int rc = tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
                                  (const float *)d->d_samples, d->nb, s->seg_spans.data(),
-                                 (int32_t)s->seg_spans.size(), s->ms, s->rs, a, n, m, ms_a, part, err, &ng, st,
-                                 fail);
+                                 (int32_t)s->seg_spans.size(), s->ms, s->rs, a, n, m, ms_a, rs_a, part, &near, err,
+                                 &ng, &cspans, &cgs, st, fail);
                 if (rc) return rc;
             }
             {
                 PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
-                FinalizeParams<float> f = fin_params<float>(nq, m, ng, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
+                FinalizeParams<float> f =
+                    fin_params<float>(ctx, nq, m, ng, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
                 f.err = err;
+                f.near = near;
+                f.cspans = cspans;
+                f.cgroup_start = cgs;
                 f.out_corr = corr ? 1 : 0;
                 CUDA_TRY(launch_finalize<float>(f, st));
             }
             return MP_OK;
         }
         Partial<float> *part = (Partial<float> *)(base + w.off_part);
-        NearTies *near = (NearTies *)(base + w.off_near);
+        const NearRec near = near_rec(base, w, nq);
         float *seed_top = nullptr;
         const SeedGeo sg = seed_geometry(nq, d->nb - m + 1);
         if (seeds) seed_top = (float *)(base + w.off_seed);
@@ -732,17 +771,21 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             Lc.ld_part = nq;
             Lc.row0 = r0;
             Lc.excl = excl;
+            NearRec nc = near;  // this chunk's rows
+            nc.slot += r0;
+            nc.flag += r0;
             CUDA_TRY(launch_plain<float>(Lc, a + r0, rows + m - 1, rs_a + r0, ms_a + r0, (const float *)d->d_samples,
                                          d->nb, (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
-                                         gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0,
-                                         near + r0, st));
+                                         gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0, nc, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
             FinalizeParams<float> f =
-                fin_params<float>(nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
+                fin_params<float>(ctx, nq, m, geo.n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_dist, d_idx);
             f.err = seeds ? err : nullptr;
             f.near = near;
+            f.cspans = gr->spans;
+            f.cgroup_start = gr->group_start;
             f.out_corr = corr ? 1 : 0;
             f.excl = excl;
             f.next_const = next_const;
@@ -760,9 +803,13 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const mp_dict *d, const DictStats
     const Geometry geo = plain_geometry(ctx, plain_chunk_rows(d, dtype, nq, m, seeds),
                                         std::max<int64_t>(1, s->n_windows), rpl, dtype, m,
                                         (int64_t)s->seg_spans.size());
-    return join_ws_layout(nq, dtype, std::max(geo.n_groups, tc_groups_bound(ctx->sm_count, nq)), 0,
-                          join_seed_bytes(d, dtype, nq, m, seeds))
-        .total;
+    // the plain form's groups or the tensor-core forms' (the wider TF32 records)
+    return std::max(join_ws_layout(nq, dtype, geo.n_groups, 0, join_seed_bytes(d, dtype, nq, m, seeds),
+                                   kNearSlotsPlain)
+                        .total,
+                    join_ws_layout(nq, dtype, tc_groups_bound(ctx->sm_count, nq), 0,
+                                   join_seed_bytes(d, dtype, nq, m, seeds), kNearSlotsTC)
+                        .total);
 }
 
 static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s, int64_t nq)
@@ -884,6 +931,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
     struct Post {
         Request *r;
         DictStats *s;
+        const DictStats::Grouping *gr;
         int n_groups;
         unsigned char *base;
         float *a;
@@ -931,7 +979,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         float4 *rs_a = (float4 *)(p + w.off_rs);
         Split<float> *ms_a = (Split<float> *)(p + w.off_ms);
         Partial<float> *part = (Partial<float> *)(p + w.off_part);
-        NearTies *near = (NearTies *)(p + w.off_near);
+        const NearRec near = near_rec(p, w, nq);
         CUDA_TRY(launch_window_stats<float>(a, r.n, r.m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
         PlainRequest pr{};  // seed_top null: the batched kernel computes its seeds
         pr.a = a;
@@ -955,7 +1003,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         for (int64_t rb = 0; rb < geo.n_row_blocks; ++rb)
             for (int g = 0; g < geo.n_groups; ++g) items.push_back(BatchItem{ridx, g, rb});
         max_m = std::max(max_m, (int)r.m);
-        post.push_back(Post{&r, s, geo.n_groups, p, (float *)a, dist, idx});
+        post.push_back(Post{&r, s, gr, geo.n_groups, p, (float *)a, dist, idx});
     }
     if (!preqs.empty()) {
         const size_t sz_req = align_up(preqs.size() * sizeof(PlainRequest), 256);
@@ -978,10 +1026,12 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
             const int64_t nq = r.n - r.m + 1;
             JoinWs w = join_ws_layout(nq, r.dtype, ps.n_groups, 0);
             FinalizeParams<float> f =
-                fin_params<float>(nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part), ps.a,
+                fin_params<float>(ctx, nq, r.m, ps.n_groups, (const Partial<float> *)(ps.base + w.off_part), ps.a,
                                   (const float4 *)(ps.base + w.off_rs), (const Split<float> *)(ps.base + w.off_ms),
                                   (const uint8_t *)(ps.base + w.off_cflag), r.dict, ps.s, ps.dist, ps.idx);
-            f.near = (const NearTies *)(ps.base + w.off_near);
+            f.near = near_rec(ps.base, w, nq);
+            f.cspans = ps.gr->spans;
+            f.cgroup_start = ps.gr->group_start;
             CUDA_TRY(launch_finalize<float>(f, st));
             CUDA_TRY(cudaMemcpyAsync(r.h_stage, ps.dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
         }
@@ -1104,6 +1154,8 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
     CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[0], cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[1], cudaStreamNonBlocking));
+    CUDA_TRY(cudaMalloc(&c->d_counters, kFinCounters * sizeof(unsigned long long)));
+    CUDA_TRY(cudaMemset(c->d_counters, 0, kFinCounters * sizeof(unsigned long long)));
     size_t fr = 0, tot = 0;
     CUDA_TRY(cudaMemGetInfo(&fr, &tot));
     c->mem_budget = cfg.mem_budget ? cfg.mem_budget : fr / 2;
@@ -1133,6 +1185,7 @@ int mp_shutdown(mp_ctx *ctx)
         delete d;
     }
     if (ctx->ws) cudaFree(ctx->ws);
+    cudaFree(ctx->d_counters);
     for (auto &mk : ctx->marks) {
         cudaEventDestroy(mk.t0);
         cudaEventDestroy(mk.t1);
@@ -1458,6 +1511,21 @@ int mp_profile_read(mp_ctx *ctx, double *ms, int64_t *launches, int32_t reset)
             ctx->prof_n[k] = 0;
         }
     }
+    return MP_OK;
+}
+
+int mp_counters(mp_ctx *ctx, int64_t *values, int32_t reset)
+{
+    g_err.clear();
+    if (!ctx || !values) return fail(MP_E_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    static_assert(MP_COUNTER_COUNT == kFinCounters, "counter layout");
+    unsigned long long h[kFinCounters];
+    CUDA_TRY(cudaDeviceSynchronize());  // every stream's joins, serving batches included
+    CUDA_TRY(cudaMemcpy(h, ctx->d_counters, sizeof h, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < kFinCounters; ++k) values[k] = (int64_t)h[k];
+    if (reset) CUDA_TRY(cudaMemset(ctx->d_counters, 0, sizeof h));
     return MP_OK;
 }
 
@@ -1924,16 +1992,19 @@ constexpr size_t kNoAllocFlagOff = kNoAllocInvOff + kNoAllocMaxWindows * sizeof(
 constexpr size_t kNoAllocRsOff = kNoAllocFlagOff + kNoAllocMaxWindows;
 constexpr size_t kNoAllocMsOff = kNoAllocRsOff + kNoAllocMaxWindows * sizeof(float4);
 constexpr size_t kNoAllocPartOff = kNoAllocMsOff + kNoAllocMaxWindows * sizeof(Split<float>);
+constexpr int kNoAllocNearSlots = 2;                        // near-tie record slots per (group, window)
 constexpr size_t kNoAllocNearOff = kNoAllocPartOff + kNoAllocMaxPartials * sizeof(Partial<float>);
-constexpr size_t kNoAllocSpanOff = kNoAllocNearOff + kNoAllocMaxPartials * sizeof(NearTies);
+constexpr size_t kNoAllocNFlagOff = kNoAllocNearOff + kNoAllocMaxPartials * kNoAllocNearSlots * sizeof(NearSlot);
+constexpr size_t kNoAllocSpanOff = kNoAllocNFlagOff + kNoAllocMaxPartials;
 constexpr size_t kNoAllocGroupOff = kNoAllocSpanOff + kNoAllocMaxSpans * sizeof(Span);
 constexpr size_t kNoAllocBytes = kNoAllocGroupOff + (kNoAllocMaxSpans + 1) * sizeof(int32_t);
 constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
-// About 46 MB: statistics of 2^19 query windows, 2^20 partial results with
-// their near-tie records, and 2^16 spans. Host code must not use this name as an address: it is a
-// host-side stand-in; the device address comes from cudaGetSymbolAddress.
+// About 47 MB: statistics of 2^19 query windows, 2^20 partial results with
+// their near-tie records, and 2^16 spans. Host code must not use this name as
+// an address: it is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 static unsigned char *g_noalloc_dev[kNoAllocMaxDevices];
 static std::mutex g_noalloc_mu;
@@ -1953,6 +2024,72 @@ static int noalloc_scratch(int device, unsigned char **out)
     }
     *out = g_noalloc_dev[device];
     return MP_OK;
+}
+
+// The dictionary's valid windows cut into column groups on the device, as
+// get_grouping cuts them on the host: in the order of the segments, windows
+// [k T, (k + 1) T) of that order form group k, and a span never crosses a
+// segment or a group. One CTA of 1024 threads, each taking a run of
+// segments: block scans give each segment's first window in that order and its
+// first span. Writes spans[0 .. total) and gstart[0 .. n_groups].
+__device__ int64_t block_excl_scan(int64_t v, int64_t *tmp, int64_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < nw ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) tmp[lane] = w;  // inclusive sums per warp
+    }
+    __syncthreads();
+    const int64_t before = (warp > 0 ? tmp[warp - 1] : 0) + x - v;
+    *total = tmp[nw - 1];
+    __syncthreads();  // tmp is reused by the next scan
+    return before;
+}
+
+__global__ void __launch_bounds__(1024) k_noalloc_groups(const Span *seg, int32_t n_seg, int64_t T, int32_t n_groups,
+                                                         int32_t n_spans_total, Span *spans, int32_t *gstart)
+{
+    __shared__ int64_t tmp[32];
+    const int per = (n_seg + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int s0 = min(n_seg, (int)threadIdx.x * per), s1 = min(n_seg, s0 + per);
+    for (int k = threadIdx.x; k <= n_groups; k += blockDim.x) gstart[k] = n_spans_total;
+    int64_t cols = 0;
+    for (int s = s0; s < s1; ++s) cols += seg[s].ncols;
+    int64_t tot;
+    const int64_t cum0 = block_excl_scan(cols, tmp, &tot);
+    // spans of each segment: one per group it meets
+    int64_t pieces = 0, cum = cum0;
+    for (int s = s0; s < s1; ++s) {
+        const int64_t n = seg[s].ncols;
+        pieces += (cum + n - 1) / T - cum / T + 1;
+        cum += n;
+    }
+    int64_t idx = block_excl_scan(pieces, tmp, &tot);  // also orders the gstart initialisation before the writes
+    cum = cum0;
+    for (int s = s0; s < s1; ++s) {
+        const Span sg = seg[s];
+        const int64_t end = cum + sg.ncols;
+        for (int64_t k = cum / T; k * T < end; ++k) {
+            const int64_t a = max(cum, k * T), b = min(end, (k + 1) * T);
+            spans[idx] = Span{sg.g0 + (a - cum), (int32_t)(b - a), 0};
+            if (a == k * T) gstart[k] = (int32_t)idx;  // group k starts here
+            ++idx;
+        }
+        cum = end;
+    }
 }
 
 extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int32_t dtype, int64_t n,
@@ -1986,54 +2123,50 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
     float4 *rs_a = (float4 *)(base + kNoAllocRsOff);
     Split<float> *ms_a = (Split<float> *)(base + kNoAllocMsOff);
     Partial<float> *part = (Partial<float> *)(base + kNoAllocPartOff);
-    NearTies *near = (NearTies *)(base + kNoAllocNearOff);
     CUDA_TRY(launch_window_stats<float>(a, n, m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
     int n_groups = 0;
+    NearRec near{};
+    Span *d_spans = (Span *)(base + kNoAllocSpanOff);
+    int32_t *d_gstart = (int32_t *)(base + kNoAllocGroupOff);
     if (s->n_windows > 0) {
         Geometry geo = plain_geometry(ctx, nq, s->n_windows, kPlainRowsPerLane, MP_F32, m,
                                       (int64_t)s->seg_spans.size());
         geo.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(geo.n_groups, kNoAllocMaxPartials / nq));
-        // the same cut into column groups as get_grouping, staged through the scratch
-        std::vector<Span> spans;
-        std::vector<int32_t> gstart(1, 0);
+        // the cut into column groups of get_grouping, built on the device from
+        // the dictionary's resident segment table (no host copy per call)
         const int64_t target = (s->n_windows + geo.n_groups - 1) / geo.n_groups;
-        int64_t fill = 0;
+        int64_t n_spans = 0, cum = 0;
         for (const Span &seg : s->seg_spans) {
-            for (int64_t off = 0; off < seg.ncols;) {
-                const int64_t take = std::min<int64_t>(seg.ncols - off, target - fill);
-                spans.push_back(Span{seg.g0 + off, (int32_t)take, 0});
-                off += take;
-                fill += take;
-                if (fill == target) {
-                    gstart.push_back((int32_t)spans.size());
-                    fill = 0;
-                }
-            }
+            n_spans += (cum + seg.ncols - 1) / target - cum / target + 1;
+            cum += seg.ncols;
         }
-        if (fill > 0) gstart.push_back((int32_t)spans.size());
-        while ((int)gstart.size() < geo.n_groups + 1) gstart.push_back((int32_t)spans.size());
-        if ((int64_t)spans.size() > kNoAllocMaxSpans)
-            return fail(MP_E_ARG, "dictionary needs %zu spans, above the no-allocation limit of %lld", spans.size(),
-                        (long long)kNoAllocMaxSpans);
-        Span *d_spans = (Span *)(base + kNoAllocSpanOff);
-        int32_t *d_gstart = (int32_t *)(base + kNoAllocGroupOff);
-        // pageable sources: the copies are staged before these calls return
-        CUDA_TRY(cudaMemcpyAsync(d_spans, spans.data(), spans.size() * sizeof(Span), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaMemcpyAsync(d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        if (n_spans > kNoAllocMaxSpans)
+            return fail(MP_E_ARG, "dictionary needs %lld spans, above the no-allocation limit of %lld",
+                        (long long)n_spans, (long long)kNoAllocMaxSpans);
+        k_noalloc_groups<<<1, 1024, 0, st>>>(s->d_seg_spans, (int32_t)s->seg_spans.size(), target, geo.n_groups,
+                                             (int32_t)n_spans, d_spans, d_gstart);
+        CUDA_TRY(cudaGetLastError());
         PlainLaunch L;
         L.nq = nq;
         L.m = m;
         L.n_row_blocks = geo.n_row_blocks;
         L.n_groups = geo.n_groups;
         L.warps = geo.warps;
+        near.slot = (NearSlot *)(base + kNoAllocNearOff);
+        near.flag = base + kNoAllocNFlagOff;
+        near.ld = nq;
+        near.S = kNoAllocNearSlots;
+        near.rho = kNearRhoFP32;
         CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb, (const float4 *)s->rs,
                                      (const Split<float> *)s->ms, d_spans, d_gstart, part, nullptr, 0, near, st));
         n_groups = geo.n_groups;
     }
     // with no dictionary window (n_groups = 0, g_first = -1) this writes +inf / -1
     FinalizeParams<float> f =
-        fin_params<float>(nq, m, n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_out_dist, d_out_idx);
-    f.near = n_groups > 0 ? near : nullptr;
+        fin_params<float>(ctx, nq, m, n_groups, part, a, rs_a, ms_a, cf_a, d, s, d_out_dist, d_out_idx);
+    f.near = near;
+    f.cspans = d_spans;
+    f.cgroup_start = d_gstart;
     CUDA_TRY(launch_finalize<float>(f, st));
     return MP_OK;
 }

@@ -23,12 +23,15 @@
 // memory). After the last K-group the epilogue reads the accumulators with
 // tcgen05.ld (one query window per thread), removes the shifts, scales by the
 // dictionary windows' 1/std, masks invalid and constant windows and keeps the
-// running maximum per 16-window chunk, as the plain kernel does.
+// running maximum per 16-window chunk, as the plain kernel does, with the same
+// near-tie records (their width covers the products' rounding: the TF32 form's
+// 11-bit operands need a wider one than the split-BF16 form).
 //
 // Every wait on the tensor core is bounded: on timeout the CTA records an
 // error, waits (bounded) for its MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 
 #include <algorithm>
@@ -62,6 +65,8 @@ struct TcArgs {
     const TcTile *tiles;
     const int32_t *group_start;
     Partial<float> *part;
+    const float4 *rs_a;  // query terms (z = 1/std, 0 for a constant window)
+    NearRec near;        // near-tie records (ld = nq), or near.slot null
     int32_t *err;
     int32_t ra_rows;   // rows of the query Hankel buffer
     int32_t nmax;      // widest tile
@@ -499,6 +504,18 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
         }
         float best = -INFINITY;
         int32_t bchunk = -1;
+        // near-tie width of this row in units of the score q = rho * m * std_a
+        // (negative: no records, for rows past the end and constant rows)
+        float tq = -1.f;
+        if (row < p.nq && p.near.slot != nullptr) {
+            p.near.flag[(int64_t)grp * p.near.ld + row] = 0;
+            const float za = p.rs_a[row].z;
+            if (za > 0.f) {
+                // twice the products' error bound: u m sqrt(std_a^2 + da^2) F_b
+                const float sd = 1.f / za;
+                tq = 2.f * p.near.u * (float)m * sqrtf(fmaf(sd, sd, da * da)) * *p.near.fb;
+            }
+        }
         bool ok = true;
         for (int t = t_lo; ok && t < t_hi; ++t) {
             const TcTile tile = p.tiles[t];
@@ -536,9 +553,16 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
                         const float cov = fmaf(-da, cp.x, __uint_as_float(v[16 * h + u]));
                         cm = fmaxf(cm, fmaf(cov, cp.y, cp.z));
                     }
+                    const int32_t gch = (int32_t)(tile.g0 + c32 + 16 * h);
+                    // near ties: a chunk within tq below the running best, or a best
+                    // overtaken by less than tq (-inf on either side: no record)
+                    if (fabsf(cm - best) <= tq) {
+                        const bool upd = cm > best;
+                        near_add(p.near, grp, row, upd ? bchunk : gch, upd ? best : cm, fmaxf(cm, best) - tq);
+                    }
                     if (cm > best) {
                         best = cm;
-                        bchunk = (int32_t)(tile.g0 + c32 + 16 * h);
+                        bchunk = gch;
                     }
                 }
             }
@@ -887,7 +911,31 @@ struct TcPack {
     TcTile *tiles = nullptr;
     int32_t *group_start = nullptr;
     int32_t n_tiles = 0;
+    float *fb = nullptr;  // the dictionary's column factor F_b for these tiles' shifts
 };
+
+// F_b = max over the tiles' valid windows g of sqrt(1 + ((mean_b[g] - s_b) /
+// std_b[g])^2), s_b the tile's shift (its first window's mean, hi part), as
+// the tensor-core join's epilogue forms them; *fb must start at 1. One CTA
+// per tile.
+__global__ void __launch_bounds__(256) k_tile_colfactor(const TcTile *tiles, int32_t n_tiles,
+                                                        const Split<float> *ms_b, const float4 *rs_b, float *fb)
+{
+    if ((int)blockIdx.x >= n_tiles) return;
+    const TcTile tile = tiles[blockIdx.x];
+    const float s_b = ms_b[tile.g0].hi;
+    float f = 1.f;
+    for (int n = threadIdx.x; n < tile.nvalid; n += blockDim.x) {
+        const int64_t g = tile.g0 + n;
+        const Split<float> mb = ms_b[g];
+        const float dz = ((mb.hi - s_b) + mb.lo) * rs_b[g].z;
+        f = fmaxf(f, sqrtf(fmaf(dz, dz, 1.f)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, o));
+    // f >= 1: the order of positive floats is that of their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(fb), __float_as_int(f));
+}
 
 struct TcPacks {
     std::vector<TcPack> packs;
@@ -909,8 +957,9 @@ std::vector<TcTile> make_tiles(const Span *seg_spans, int32_t n_seg, int nmax)
 }
 
 // The device tile table of this tile width split into ng column groups
-// (cached per dictionary and m); nullptr if device memory runs out.
-TcPack *get_pack(TcPacks *pk, const std::vector<TcTile> &tiles, int nmax, int ng)
+// (cached per dictionary and m); nullptr if device memory runs out or a CUDA
+// call fails. Synchronises `st` once, when it is built.
+TcPack *get_pack(TcPacks *pk, const std::vector<TcTile> &tiles, int nmax, int ng, cudaStream_t st)
 {
     for (auto &p : pk->packs)
         if (p.nmax == nmax && p.n_groups == ng) return &p;
@@ -927,10 +976,46 @@ TcPack *get_pack(TcPacks *pk, const std::vector<TcTile> &tiles, int nmax, int ng
         cudaFree(np.tiles);
         return nullptr;
     }
-    if (n_tiles) cudaMemcpy(np.tiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice);
-    cudaMemcpy(np.group_start, gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    const bool ok = (n_tiles == 0 || cudaMemcpyAsync(np.tiles, tiles.data(), tiles.size() * sizeof(TcTile),
+                                                     cudaMemcpyHostToDevice, st) == cudaSuccess) &&
+                    cudaMemcpyAsync(np.group_start, gs.data(), gs.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;  // the sources are host vectors
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(np.tiles);
+        cudaFree(np.group_start);
+        return nullptr;
+    }
     pk->packs.push_back(np);
     return &pk->packs.back();
+}
+
+// The column factor F_b of a pack's tiles, computed at its first use by the
+// join (synchronising `st` once); false if a CUDA call fails.
+bool pack_colfactor(TcPack *pk, const void *ms_b, const void *rs_b, cudaStream_t st)
+{
+    if (pk->fb) return true;
+    float *fb = nullptr;
+    if (cudaMalloc(&fb, sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const float one = 1.f;
+    bool ok = cudaMemcpyAsync(fb, &one, sizeof one, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (ok && pk->n_tiles > 0) {
+        k_tile_colfactor<<<pk->n_tiles, 256, 0, st>>>(pk->tiles, pk->n_tiles, (const Split<float> *)ms_b,
+                                                      (const float4 *)rs_b, fb);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;  // ready for every later join, on any stream
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(fb);
+        return false;
+    }
+    pk->fb = fb;
+    return true;
 }
 
 }  // namespace
@@ -954,15 +1039,19 @@ void tc_free_pack(void *pack)
     for (auto &p : pk->packs) {
         cudaFree(p.tiles);
         cudaFree(p.group_start);
+        cudaFree(p.fb);
     }
     delete pk;
 }
 
 int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
             const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
-            Partial<float> *part,
-            int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail)
+            const void *rs_a, Partial<float> *part, NearRec *near, int32_t *err, int *n_groups_out,
+            const Span **cspans_out, const int32_t **cgroup_start_out, cudaStream_t st, fail_fn fail)
 {
+    static_assert(sizeof(TcTile) == sizeof(Span) && offsetof(TcTile, g0) == offsetof(Span, g0) &&
+                      offsetof(TcTile, nvalid) == offsetof(Span, ncols),
+                  "a tile reads as the span of its valid windows");
     TcPlan P;
     if (!make_plan(variant, m, &P)) return fail(MP_E_ARG, "tensor-core join does not support m=%d", m);
     const int64_t nq = n - m + 1;
@@ -972,8 +1061,14 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     const std::vector<TcTile> tiles = make_tiles(seg_spans, n_seg, P.nmax);
     const int n_tiles = (int)tiles.size();
     int ng = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (2 * sm_count + n_row_blocks - 1) / n_row_blocks));
-    TcPack *use = get_pack(pk, tiles, P.nmax, ng);
+    TcPack *use = get_pack(pk, tiles, P.nmax, ng, st);
     if (!use) return fail(MP_E_NOMEM, "tensor-core tile table");
+    if (near->slot != nullptr) {
+        if (!pack_colfactor(use, ms_b, rs_b, st)) return fail(MP_E_CUDA, "tensor-core column factor");
+        // the products' error bound: one product's rounding plus the FP32 sum's
+        near->fb = use->fb;
+        near->u = variant == 1 ? kTcUnitTF32 + (float)m * 0x1p-23f : kTcUnitBF16X3 + 3.f * (float)m * 0x1p-23f;
+    }
     TcArgs A;
     A.a = a;
     A.na = n;
@@ -988,6 +1083,10 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     A.tiles = use->tiles;
     A.group_start = use->group_start;
     A.part = part;
+    A.rs_a = (const float4 *)rs_a;
+    A.near = *near;
+    if (near->slot != nullptr && (near->ld != nq || near->S < 1 || near->S > kNearMaxSlots))
+        return fail(MP_E_INTERNAL, "tensor-core join: near-tie record layout");
     A.err = err;
     A.ra_rows = P.ra_rows;
     A.nmax = P.nmax;
@@ -1009,6 +1108,9 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
         launch(k_tc<1>);
     if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core kernel launch: %s", cudaGetErrorString(e));
     *n_groups_out = ng;
+    // the column groups' chunks, for the finalisation of overflowed records
+    *cspans_out = reinterpret_cast<const Span *>(use->tiles);
+    *cgroup_start_out = use->group_start;
     return MP_OK;
 }
 
@@ -1027,7 +1129,7 @@ int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *
     if (n_tiles == 0 || n_srows <= 0) return MP_OK;
     // about eight CTAs per SM over the launch (four waves of two per SM)
     const int ng = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (8 * sm_count + n_rb - 1) / n_rb));
-    TcPack *use = get_pack(pk, tiles, kTcMaxN, ng);
+    TcPack *use = get_pack(pk, tiles, kTcMaxN, ng, st);
     if (!use) return fail(MP_E_NOMEM, "tensor-core tile table");
     SeedArgs A;
     A.a = a;

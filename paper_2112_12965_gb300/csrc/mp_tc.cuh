@@ -20,12 +20,18 @@ int tc_groups_bound(int sm_count, int64_t nq);
 void tc_free_pack(void *pack);
 
 // Launch the tensor-core join (kernel K3) of an FP32 query whose window
-// statistics are computed (ms_*: Split<float> means, rs_*: float4 terms); writes part[group * nq + row] (the same partial
-// format as the plain kernel) and *n_groups_out. *err is set to 1 on a
+// statistics are computed (ms_*: Split<float> means, rs_*: float4 terms);
+// writes part[group * nq + row] (the same partial format as the plain kernel),
+// the near-tie records of every row (near->slot may be null; near->ld = nq;
+// the call sets near->fb and near->u, the width's terms) and
+// *n_groups_out; *cspans_out / *cgroup_start_out receive the column groups'
+// chunk layout (valid until the dictionary is freed). *err is set to 1 on a
 // device-side timeout. variant: 0 = split BF16 (3 products), 1 = TF32.
+// The caller sizes part and near for tc_groups_bound groups.
 int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
             const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
-            Partial<float> *part, int32_t *err, int *n_groups_out, cudaStream_t st, fail_fn fail);
+            const void *rs_a, Partial<float> *part, NearRec *near, int32_t *err, int *n_groups_out,
+            const Span **cspans_out, const int32_t **cgroup_start_out, cudaStream_t st, fail_fn fail);
 
 // Top seeds of the plain kernel (K2s) on the tensor cores: for the query
 // windows r_s = s * stride, s < ceil(nq / stride), and every valid dictionary

@@ -336,3 +336,57 @@ def test_large_join_runs_in_row_chunks(mp, ctx):
     rows = np.unique(np.concatenate([edges, np.random.default_rng(4).choice(700_000, 40, replace=False)]))
     parity.check(dist, idx, q, b, offs, m, rows=rows, atol=1e-4)
     assert np.all((dist >= 0) & (dist <= 2 * math.sqrt(m) + 1e-9))
+
+
+def _near_copies_case():
+    """One dictionary segment holding seven copies of an ECG-like stretch, copy c perturbed by white noise of
+    its own scale, in decreasing order of that scale; the query embeds the unperturbed stretch. For the query
+    windows inside it, the copies' windows at the same offset lie within about 1.5e-5 of each other in
+    correlation (distances about 0.03 to 0.06 at m = 64, a few 1e-3 apart): well inside the plain kernel's
+    near-tie width, and within a few times the FP32 recurrence's own error."""
+    m = 64
+    rng = np.random.default_rng(2024)
+    stretch = synthetic.ecg_like(200, 61).astype(np.float64)
+    sd = float(np.std(stretch))
+    scales = 0.004 + 0.0004 * np.arange(7)[::-1]
+    copies = [stretch + s * sd * rng.standard_normal(len(stretch)) for s in scales]
+    b = np.concatenate(copies).astype(np.float32)
+    offs = np.array([0, len(b)], dtype=np.int64)
+    q = synthetic.ecg_like(3000, 62).astype(np.float64)
+    q[1000:1200] = stretch
+    return q.astype(np.float32), b, offs, m
+
+
+def test_near_tie_records_overflow_rescans_the_group(mp):
+    """Seven near-tied chunks per query window in one column group: more than the plain kernel's record slots.
+    The records overflow, the finalisation re-scores the whole column group for those windows, and every
+    row still matches the oracle (1e-4, the plain path's tolerance). The context's counters show that the
+    overflow path ran."""
+    q, b, offs, m = _near_copies_case()
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        mp.mp_counters(ctx, reset=True)
+        dist, idx = join(mp, ctx, q, b, offs, m)
+        c = mp.mp_counters(ctx)
+    finally:
+        mp.mp_shutdown(ctx)
+    od, oi, od2 = oracle.ab_join(q, b, offs, m)
+    rows = np.arange(1000, 1200 - m + 1)
+    # a wrong pick among the copies would miss the oracle's distance by the gap
+    assert np.mean(od2[rows] - od[rows] > 2e-4) > 0.9, "the copies' distances must differ by more than 1e-4"
+    parity.check(dist, idx, q, b, offs, m, atol=1e-4, oracle_out=(od, oi, od2))
+    assert c[mp.MP_COUNTER_OVERFLOW_ROWS] >= len(rows) // 2, c
+    assert c[mp.MP_COUNTER_OVERFLOW_CHUNKS] > 0, c
+
+
+@pytest.mark.parametrize("kernel", ["MP_KERNEL_TC_BF16X3", "MP_KERNEL_TC_TF32"])
+def test_near_copies_tensor_core_forms(mp, kernel):
+    """The same seven near-tied copies through the tensor-core forms: their records (32 slots) hold every
+    copy, and each row matches the oracle within the tensor-core tolerance."""
+    q, b, offs, m = _near_copies_case()
+    ctx = mp.mp_init(device=0, kernel=getattr(mp, kernel))
+    try:
+        dist, idx = join(mp, ctx, q, b, offs, m)
+    finally:
+        mp.mp_shutdown(ctx)
+    parity.check(dist, idx, q, b, offs, m, atol=1e-3)

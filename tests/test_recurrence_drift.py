@@ -25,7 +25,7 @@ MAX_STEPS = 640
 
 def _near_tie_width() -> float:
     with open(os.path.join(ROOT, "paper_2112_12965_gb300", "csrc", "mp_internal.cuh")) as f:
-        return float(re.search(r"kNearTieRho\s*=\s*([0-9.eE+-]+)f", f.read()).group(1))
+        return float(re.search(r"kNearRhoFP32\s*=\s*([0-9.eE+-]+)f", f.read()).group(1))
 
 
 def _stats(x, m):
