@@ -189,10 +189,11 @@ __device__ __forceinline__ int32_t near_entry(const FinalizeParams<T> &p, int64_
         const Partial<T> v = p.part[k * p.nq + i];
         return (v.g >= 0 && v.g != g && v.q >= lim) ? v.g : -1;
     }
-    const unsigned f = p.near.flag[k * p.near.ld + i];
+    const NearSlot *h = p.near.head(k, i);
+    const int32_t f = h->g;
     if (u == 1 && (f & kNearOverflow)) ovf = true;
-    if (u - 1 >= (int)(f & kNearCountMask)) return -1;
-    const NearSlot sl = p.near.slot[(k * p.near.S + u - 1) * p.near.ld + i];
+    if (u - 1 >= (f & kNearCountMask)) return -1;
+    const NearSlot sl = h[(int64_t)u * p.near.ld];
     return (sl.g != g && T(sl.q) >= lim) ? sl.g : -1;
 }
 
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                     int32_t gw;
                     rescore_chunk<T>(p.a, p.b, p.nb, p.npos_b, m, p.ms_b, p.rs_b, i, g, ma, lane, wa, wb, sc,
                                      gw, p.excl);
-                    if (p.near.slot != nullptr) {
+                    if (p.near.rec != nullptr) {
                         const T lim = q - near_width(p, i, p.rs_a[i].z, ma);  // the row is not constant: z > 0
                         auto consider = [&](int32_t cu) {
                             T s2;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                         if (any_ovf) {
                             // a record within the width was dropped: every chunk of that group
                             for (int k = 0; k < p.n_groups; ++k) {
-                                if (!(p.near.flag[(int64_t)k * p.near.ld + i] & kNearOverflow)) continue;
+                                if (!(p.near.head(k, i)->g & kNearOverflow)) continue;
                                 for (int sp = p.cgroup_start[k]; sp < p.cgroup_start[k + 1]; ++sp) {
                                     const Span span = p.cspans[sp];
                                     for (int c0 = 0; c0 < span.ncols; c0 += kChunk) {
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                     s_mhi[tid] = ma.hi;
                     s_mlo[tid] = ma.lo;
                     s_isa[tid] = isa;
-                    if (p.near.slot != nullptr) {
+                    if (p.near.rec != nullptr) {
                         // every other chunk whose approximate score came within the
                         // near-tie width of the best (other groups' winners and the
                         // join's near-tie records) is re-scored too, so that the
@@ -586,11 +587,12 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                                 if (nc < kFinMaxCand) s_cand[nc][tid] = v.g;
                                 ++nc;
                             }
-                            const unsigned f = p.near.flag[(int64_t)k * p.near.ld + i];
+                            const NearSlot *h = p.near.head(k, i);
+                            const int32_t f = h->g;
                             ovf |= (f & kNearOverflow) != 0;
-                            const int n = (int)(f & kNearCountMask);
-                            for (int u = 0; u < n && u < S; ++u) {
-                                const NearSlot sl = p.near.slot[((int64_t)k * S + u) * p.near.ld + i];
+                            const int n = f & kNearCountMask;
+                            for (int u = 1; u <= n && u <= S; ++u) {
+                                const NearSlot sl = h[(int64_t)u * p.near.ld];
                                 if (sl.g != g && T(sl.q) >= lim) {
                                     if (nc < kFinMaxCand) s_cand[nc][tid] = sl.g;
                                     ++nc;
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                 if (ncw < 0) {
                     // a record within the width was dropped: every chunk of that group
                     for (int k = 0; k < p.n_groups; ++k) {
-                        if (!(p.near.flag[(int64_t)k * p.near.ld + iw] & kNearOverflow)) continue;
+                        if (!(p.near.head(k, iw)->g & kNearOverflow)) continue;
                         for (int sp = p.cgroup_start[k]; sp < p.cgroup_start[k + 1]; ++sp) {
                             const Span span = p.cspans[sp];
                             for (int c0 = 0; c0 < span.ncols; c0 += kChunk) {

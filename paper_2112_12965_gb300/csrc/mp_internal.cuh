@@ -92,17 +92,20 @@ struct NearSlot {
     int32_t g;
     float q;
 };
-constexpr unsigned kNearCountMask = 0x3fu;  // flag bits 0-5: slots in use
-constexpr unsigned kNearOverflow = 0x80u;   // flag bit 7: a record within the width was dropped
+constexpr int32_t kNearCountMask = 0x3f;  // header bits 0-5: slots in use
+constexpr int32_t kNearOverflow = 0x80;   // header bit 7: a record within the width was dropped
 constexpr int kNearMaxSlots = 32;
 struct NearRec {
-    NearSlot *slot;   // [n_groups][S][ld]: slot u of (group k, row r) at (k * S + u) * ld + r; null: no records
-    uint8_t *flag;    // [n_groups][ld]: slots in use | kNearOverflow; the join zeroes the flags of its rows
-    int64_t ld;       // row stride of slot and flag
+    // [n_groups][1 + S][ld]: entry (k, 0, r) is the header of (group k, row r)
+    // (its g holds the slots in use | kNearOverflow; the join zeroes the headers
+    // of its rows), entries (k, 1 + u, r) its slots. Null: no records.
+    NearSlot *rec;
+    int64_t ld;       // row stride
     int32_t S;        // slots per (group, row), 1 .. kNearMaxSlots
     float rho;        // plain form: width in Pearson correlation
     const float *fb;  // tensor-core forms (rho unused): the dictionary's column factor F_b, below
     float u;          // tensor-core forms: bound on the relative error of the products and their sum
+    __host__ __device__ NearSlot *head(int64_t k, int64_t r) const { return rec + k * (S + 1) * ld + r; }
 };
 // Width of the plain FP32 recurrence, in correlation: 8x the largest drift
 // measured by a float32 model of the recurrence on the benchmark data (about
@@ -131,36 +134,38 @@ constexpr int kTcRows = 128;  // query windows per CTA of the tensor-core join (
 // Record chunk g with approximate score q for (group k, row r). floor_q is
 // the running best minus the width: a record below it can never come within
 // the width of the final best, so dropping it needs no overflow mark. The
-// caller owns (k, r) exclusively for the whole join.
+// caller owns (k, r) exclusively for the whole join. With all S slots in use,
+// kEvict replaces the lowest-scoring slot if q is higher, and the record
+// dropped (that one, or q) sets the overflow bit if it may still matter;
+// without kEvict q is dropped (less code, for the plain kernel's hot loop).
+template <bool kEvict>
 __device__ __forceinline__ void near_add(const NearRec &nr, int64_t k, int64_t r, int32_t g, float q, float floor_q)
 {
-    uint8_t *fp = nr.flag + k * nr.ld + r;
-    const unsigned f = *fp;
-    const int n = (int)(f & kNearCountMask);
-    NearSlot *base = nr.slot + k * (int64_t)nr.S * nr.ld + r;
+    NearSlot *h = nr.head(k, r);
+    const int32_t f = h->g;
+    const int n = f & kNearCountMask;
     if (n < nr.S) {
-        base[(int64_t)n * nr.ld] = NearSlot{g, q};
-        *fp = (uint8_t)((f & kNearOverflow) | (unsigned)(n + 1));
+        h[(int64_t)(n + 1) * nr.ld] = NearSlot{g, q};
+        h->g = f + 1;
         return;
     }
-    // all S slots in use: replace the lowest-scoring one if q is higher; the
-    // record dropped (that one, or q itself) sets the overflow bit if it may
-    // still lie within the width of the final best
-    int lo = 0;
-    float qlo = base[0].q;
-    for (int u = 1; u < nr.S; ++u) {
-        const float qu = base[(int64_t)u * nr.ld].q;
-        if (qu < qlo) {
-            qlo = qu;
-            lo = u;
+    float dropped = q;
+    if (kEvict) {
+        int lo = 1;
+        float qlo = h[nr.ld].q;
+        for (int u = 2; u <= nr.S; ++u) {
+            const float qu = h[(int64_t)u * nr.ld].q;
+            if (qu < qlo) {
+                qlo = qu;
+                lo = u;
+            }
+        }
+        if (q > qlo) {
+            dropped = qlo;
+            h[(int64_t)lo * nr.ld] = NearSlot{g, q};
         }
     }
-    float dropped = q;
-    if (q > qlo) {
-        dropped = qlo;
-        base[(int64_t)lo * nr.ld] = NearSlot{g, q};
-    }
-    if (dropped >= floor_q) *fp = (uint8_t)(f | kNearOverflow);
+    if (dropped >= floor_q) h->g = f | kNearOverflow;
 }
 #endif
 
@@ -182,7 +187,7 @@ struct PlainLaunch {
 // seed_top (may be null): the centred covariances of each warp's first query
 // window, row r / (32 * rows per lane) at column g, row stride seed_ld (as
 // written by tc_seeds); null makes the kernel compute them itself.
-// near (near.slot may be null; FP32 only): near-tie records of every query
+// near (near.rec may be null; FP32 only): near-tie records of every query
 // window; near.ld must equal the partial results' row stride.
 template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
@@ -251,7 +256,7 @@ template <typename T> struct FinalizeParams {
     double *out_dist;
     int64_t *out_idx;
     const int32_t *err;       // may be null; if *err != 0 a tensor-core wait ran out: NaN / -1 everywhere
-    NearRec near;             // near-tie records of the join (near.slot null: none), ld = nq
+    NearRec near;             // near-tie records of the join (near.rec null: none), ld = nq
     // chunk layout of the column groups, for windows whose records overflowed:
     // chunks g0 + 16 j of cspans[cgroup_start[k] .. cgroup_start[k+1]) are group k's
     const Span *cspans;

@@ -61,7 +61,7 @@ template <typename T> struct PlainParams {
     Partial<T> *part;
     const T *seed_top;  // top seeds from the tensor cores, or null
     int64_t seed_ld;
-    NearRec near;       // near-tie records (near.ld = ld_part), or near.slot null
+    NearRec near;       // near-tie records (near.ld = ld_part), or near.rec null
     int64_t ld_part;    // row stride of part and near (>= nq)
     int64_t row0;       // self-join: position in the series of query window 0
     int32_t excl;       // self-join: pairs with |g - (row0 + r)| < excl are left out (0: none)
@@ -270,7 +270,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             R.set_terms(j, v.x, v.y);
             if (kNear) {
                 if (v.z > T(0)) sig_max = fmax(sig_max, T(1) / v.z);
-                p.near.flag[(int64_t)grp * p.ld_part + r] = 0;  // no records yet
+                p.near.head(grp, r)->g = 0;  // no records yet
             }
         } else {
             R.set_terms(j, T(0), T(0));
@@ -494,8 +494,11 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                         for (int j = 0; j < kRows; ++j) {
                             if (fabs(cm[j] - best[j]) <= tq && r0 + j < p.nq) {
                                 const bool upd = cm[j] > best[j];
-                                near_add(p.near, grp, r0 + j, upd ? bchunk[j] : gch, (float)(upd ? best[j] : cm[j]),
-                                         (float)(fmax(cm[j], best[j]) - tq));
+                                // with all slots in use the new record is dropped (an
+                                // eviction loop in each of the kRows unrolled copies
+                                // cost 6 % of the kernel's time)
+                                near_add<false>(p.near, grp, r0 + j, upd ? bchunk[j] : gch,
+                                                (float)(upd ? best[j] : cm[j]), (float)(fmax(cm[j], best[j]) - tq));
                             }
                         }
                     }
@@ -608,19 +611,19 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     };
     if constexpr (sizeof(T) == 8) {
         // FP64 data: seeds from direct dot products, no near-tie records
-        if (seed_top != nullptr || near.slot != nullptr || L.excl > 0) return cudaErrorInvalidValue;
+        if (seed_top != nullptr || near.rec != nullptr || L.excl > 0) return cudaErrorInvalidValue;
         return launch(k_plain<T, R, false, false>);
     } else {
-        if (near.slot != nullptr && (near.ld != p.ld_part || near.S < 1 || near.S > kNearMaxSlots))
+        if (near.rec != nullptr && (near.ld != p.ld_part || near.S < 1 || near.S > kNearMaxSlots))
             return cudaErrorInvalidValue;
         if (L.excl > 0) {
             // self-join (dictionary learning): tensor-core seeds and near-tie records
-            if (seed_top == nullptr || near.slot == nullptr) return cudaErrorInvalidValue;
+            if (seed_top == nullptr || near.rec == nullptr) return cudaErrorInvalidValue;
             return launch(k_plain<T, R, true, true, true>);
         }
         if (seed_top != nullptr)
-            return near.slot != nullptr ? launch(k_plain<T, R, true, true>) : launch(k_plain<T, R, true, false>);
-        return near.slot != nullptr ? launch(k_plain<T, R, false, true>) : launch(k_plain<T, R, false, false>);
+            return near.rec != nullptr ? launch(k_plain<T, R, true, true>) : launch(k_plain<T, R, true, false>);
+        return near.rec != nullptr ? launch(k_plain<T, R, false, true>) : launch(k_plain<T, R, false, false>);
     }
 }
 

@@ -590,7 +590,7 @@ static int64_t plain_chunk_rows(const mp_dict *d, int32_t dtype, int64_t nq, int
 
 // Workspace layout of one join.
 struct JoinWs {
-    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_nflag, off_seed, total;
+    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_seed, total;
     int near_slots;
 };
 
@@ -620,13 +620,11 @@ static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t ext
     o = align_up(o + nq * 2 * e, 256);
     w.off_part = o;
     o = align_up(o + (size_t)n_groups * nq * (e == 8 ? sizeof(Partial<double>) : sizeof(Partial<float>)), 256);
-    // near-tie records of FP32 joins: near_slots slots and one flag byte per
+    // near-tie records of FP32 joins: a header and near_slots slots per
     // (column group, query window)
     w.near_slots = dtype == MP_F32 ? near_slots : 0;
     w.off_near = o;
-    o = align_up(o + (size_t)n_groups * w.near_slots * nq * sizeof(NearSlot), 256);
-    w.off_nflag = o;
-    if (dtype == MP_F32) o = align_up(o + (size_t)n_groups * nq, 256);
+    if (dtype == MP_F32) o = align_up(o + (size_t)n_groups * (w.near_slots + 1) * nq * sizeof(NearSlot), 256);
     w.off_seed = o;
     o = align_up(o + seed_bytes, 256);
     w.total = o;
@@ -638,8 +636,7 @@ static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t ext
 static NearRec near_rec(unsigned char *base, const JoinWs &w, int64_t ld)
 {
     NearRec r{};
-    r.slot = (NearSlot *)(base + w.off_near);
-    r.flag = base + w.off_nflag;
+    r.rec = (NearSlot *)(base + w.off_near);
     r.ld = ld;
     r.S = w.near_slots;
     r.rho = kNearRhoFP32;
@@ -654,8 +651,27 @@ static size_t join_seed_bytes(const mp_dict *d, int32_t dtype, int64_t nq, int32
     return seed_geometry(nq, d->nb - m + 1).bytes;
 }
 
+// Geometry of the plain join of nq query windows (row chunks included).
+static Geometry join_plain_geometry(const mp_ctx *ctx, const mp_dict *d, const DictStats *s, int32_t dtype,
+                                    int64_t nq, int32_t m, bool seeds)
+{
+    const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
+    return plain_geometry(ctx, plain_chunk_rows(d, dtype, nq, m, seeds), std::max<int64_t>(1, s->n_windows), rpl,
+                          dtype, m, (int64_t)s->seg_spans.size());
+}
+
+// The workspace layout join_device uses for this form: the plain form's column
+// groups with its near-tie slots, or the tensor-core forms' groups with theirs.
+static JoinWs join_layout(const mp_ctx *ctx, const mp_dict *d, const DictStats *s, int32_t dtype, int64_t nq,
+                          int32_t m, int kernel, bool seeds)
+{
+    const int groups = is_tc(kernel) ? tc_groups_bound(ctx->sm_count, nq)
+                                     : join_plain_geometry(ctx, d, s, dtype, nq, m, seeds).n_groups;
+    return join_ws_layout(nq, dtype, groups, 0, join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel));
+}
+
 // The join on device buffers; `base` is a device workspace of at least
-// join_ws_layout(...).total bytes. Everything is enqueued on `st`.
+// join_layout(...).total bytes (join_ws_bytes covers every form). Everything is enqueued on `st`.
 // With `seeds`, an FP32 plain join takes its top seeds from the tensor cores
 // (the workspace then holds join_seed_bytes(..., true) more bytes). The
 // error word at the front of the workspace is zeroed first; tensor-core
@@ -671,12 +687,10 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         return fail(MP_E_INTERNAL, "the self-join runs the FP32 plain kernel with tensor-core seeds");
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
-    const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     const int64_t crow = plain_chunk_rows(d, dtype, nq, m, seeds);  // query windows per plain launch
-    const Geometry geo = plain_geometry(ctx, crow, s->n_windows, rpl, dtype, m, (int64_t)s->seg_spans.size());
+    const Geometry geo = join_plain_geometry(ctx, d, s, dtype, nq, m, seeds);
     const bool tc = is_tc(kernel);
-    JoinWs w = join_ws_layout(nq, dtype, std::max(geo.n_groups, tc ? tc_groups_bound(ctx->sm_count, nq) : 1), 0,
-                              join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel));
+    const JoinWs w = join_layout(ctx, d, s, dtype, nq, m, kernel, seeds);
     int32_t *err = (int32_t *)(base + w.off_err);
     CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
     double *mean_a = (double *)(base + w.off_mean);
@@ -772,8 +786,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             Lc.row0 = r0;
             Lc.excl = excl;
             NearRec nc = near;  // this chunk's rows
-            nc.slot += r0;
-            nc.flag += r0;
+            nc.rec += r0;
             CUDA_TRY(launch_plain<float>(Lc, a + r0, rows + m - 1, rs_a + r0, ms_a + r0, (const float *)d->d_samples,
                                          d->nb, (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
                                          gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0, nc, st));
@@ -799,17 +812,9 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const mp_dict *d, const DictStats
                             int32_t m, bool seeds = true)
 {
     const int64_t nq = n - m + 1;
-    const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
-    const Geometry geo = plain_geometry(ctx, plain_chunk_rows(d, dtype, nq, m, seeds),
-                                        std::max<int64_t>(1, s->n_windows), rpl, dtype, m,
-                                        (int64_t)s->seg_spans.size());
-    // the plain form's groups or the tensor-core forms' (the wider TF32 records)
-    return std::max(join_ws_layout(nq, dtype, geo.n_groups, 0, join_seed_bytes(d, dtype, nq, m, seeds),
-                                   kNearSlotsPlain)
-                        .total,
-                    join_ws_layout(nq, dtype, tc_groups_bound(ctx->sm_count, nq), 0,
-                                   join_seed_bytes(d, dtype, nq, m, seeds), kNearSlotsTC)
-                        .total);
+    size_t b = join_layout(ctx, d, s, dtype, nq, m, MP_KERNEL_PLAIN, seeds).total;
+    if (dtype == MP_F32) b = std::max(b, join_layout(ctx, d, s, dtype, nq, m, MP_KERNEL_TC_BF16X3, seeds).total);
+    return b;
 }
 
 static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const DictStats *s, int64_t nq)
@@ -1994,14 +1999,13 @@ constexpr size_t kNoAllocMsOff = kNoAllocRsOff + kNoAllocMaxWindows * sizeof(flo
 constexpr size_t kNoAllocPartOff = kNoAllocMsOff + kNoAllocMaxWindows * sizeof(Split<float>);
 constexpr int kNoAllocNearSlots = 2;                        // near-tie record slots per (group, window)
 constexpr size_t kNoAllocNearOff = kNoAllocPartOff + kNoAllocMaxPartials * sizeof(Partial<float>);
-constexpr size_t kNoAllocNFlagOff = kNoAllocNearOff + kNoAllocMaxPartials * kNoAllocNearSlots * sizeof(NearSlot);
-constexpr size_t kNoAllocSpanOff = kNoAllocNFlagOff + kNoAllocMaxPartials;
+constexpr size_t kNoAllocSpanOff = kNoAllocNearOff + kNoAllocMaxPartials * (kNoAllocNearSlots + 1) * sizeof(NearSlot);
 constexpr size_t kNoAllocGroupOff = kNoAllocSpanOff + kNoAllocMaxSpans * sizeof(Span);
 constexpr size_t kNoAllocBytes = kNoAllocGroupOff + (kNoAllocMaxSpans + 1) * sizeof(int32_t);
 constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
-// About 47 MB: statistics of 2^19 query windows, 2^20 partial results with
+// About 54 MB: statistics of 2^19 query windows, 2^20 partial results with
 // their near-tie records, and 2^16 spans. Host code must not use this name as
 // an address: it is a host-side stand-in; the device address comes from
 // cudaGetSymbolAddress.
@@ -2152,8 +2156,7 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
         L.n_row_blocks = geo.n_row_blocks;
         L.n_groups = geo.n_groups;
         L.warps = geo.warps;
-        near.slot = (NearSlot *)(base + kNoAllocNearOff);
-        near.flag = base + kNoAllocNFlagOff;
+        near.rec = (NearSlot *)(base + kNoAllocNearOff);
         near.ld = nq;
         near.S = kNoAllocNearSlots;
         near.rho = kNearRhoFP32;

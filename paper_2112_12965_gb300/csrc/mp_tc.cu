@@ -66,7 +66,7 @@ struct TcArgs {
     const int32_t *group_start;
     Partial<float> *part;
     const float4 *rs_a;  // query terms (z = 1/std, 0 for a constant window)
-    NearRec near;        // near-tie records (ld = nq), or near.slot null
+    NearRec near;        // near-tie records (ld = nq), or near.rec null
     int32_t *err;
     int32_t ra_rows;   // rows of the query Hankel buffer
     int32_t nmax;      // widest tile
@@ -507,8 +507,8 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
         // near-tie width of this row in units of the score q = rho * m * std_a
         // (negative: no records, for rows past the end and constant rows)
         float tq = -1.f;
-        if (row < p.nq && p.near.slot != nullptr) {
-            p.near.flag[(int64_t)grp * p.near.ld + row] = 0;
+        if (row < p.nq && p.near.rec != nullptr) {
+            p.near.head(grp, row)->g = 0;
             const float za = p.rs_a[row].z;
             if (za > 0.f) {
                 // twice the products' error bound: u m sqrt(std_a^2 + da^2) F_b
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
                     // overtaken by less than tq (-inf on either side: no record)
                     if (fabsf(cm - best) <= tq) {
                         const bool upd = cm > best;
-                        near_add(p.near, grp, row, upd ? bchunk : gch, upd ? best : cm, fmaxf(cm, best) - tq);
+                        near_add<true>(p.near, grp, row, upd ? bchunk : gch, upd ? best : cm, fmaxf(cm, best) - tq);
                     }
                     if (cm > best) {
                         best = cm;
@@ -1063,7 +1063,7 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     int ng = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (2 * sm_count + n_row_blocks - 1) / n_row_blocks));
     TcPack *use = get_pack(pk, tiles, P.nmax, ng, st);
     if (!use) return fail(MP_E_NOMEM, "tensor-core tile table");
-    if (near->slot != nullptr) {
+    if (near->rec != nullptr) {
         if (!pack_colfactor(use, ms_b, rs_b, st)) return fail(MP_E_CUDA, "tensor-core column factor");
         // the products' error bound: one product's rounding plus the FP32 sum's
         near->fb = use->fb;
@@ -1085,7 +1085,7 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     A.part = part;
     A.rs_a = (const float4 *)rs_a;
     A.near = *near;
-    if (near->slot != nullptr && (near->ld != nq || near->S < 1 || near->S > kNearMaxSlots))
+    if (near->rec != nullptr && (near->ld != nq || near->S < 1 || near->S > kNearMaxSlots))
         return fail(MP_E_INTERNAL, "tensor-core join: near-tie record layout");
     A.err = err;
     A.ra_rows = P.ra_rows;

@@ -22,7 +22,7 @@ void tc_free_pack(void *pack);
 // Launch the tensor-core join (kernel K3) of an FP32 query whose window
 // statistics are computed (ms_*: Split<float> means, rs_*: float4 terms);
 // writes part[group * nq + row] (the same partial format as the plain kernel),
-// the near-tie records of every row (near->slot may be null; near->ld = nq;
+// the near-tie records of every row (near->rec may be null; near->ld = nq;
 // the call sets near->fb and near->u, the width's terms) and
 // *n_groups_out; *cspans_out / *cgroup_start_out receive the column groups'
 // chunk layout (valid until the dictionary is freed). *err is set to 1 on a
