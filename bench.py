@@ -39,12 +39,10 @@ L2_BYTES = 129 * 2**20
 PLAIN_OPS_PER_PAIR = 4
 # DRAM bytes of one k_plain launch on the full-size ECG workload (2^20 query
 # samples, 64 x 1024 dictionary, m = 256), from one single-pass ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum: 367.49 MB read (mostly the
-# 323 MB top-seed matrix) and 219.89 MB written (partials and near-tie
-# records). Valid for this kernel build (20 rows per lane, one 16-byte column
-# term per column) and workload only.
-PLAIN_DRAM_BYTES_FULL = 367.49e6 + 219.89e6
-SMS, LANES_PER_SM = 152, 128
+# dram__bytes_read.sum + dram__bytes_write.sum; None until the current kernel
+# build has been captured (the number is valid for one build and workload).
+PLAIN_DRAM_BYTES_FULL = None
+LANES_PER_SM = 128  # FP32 lanes per SM
 # query windows per top seed of the FP32 plain kernel: one per warp, 32 lanes x 20 rows
 SEED_STRIDE = 32 * 20
 
@@ -208,19 +206,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def roofline(kname, pairs, m, join_ms, peaks, peak_src, full_size=False):
+def roofline(kname, pairs, m, join_ms, peaks, peak_src, full_size=False, sms=152):
     """Roofline of the join kernel: ALU-issue bound (plain) or tensor bound (tcgen05).
 
     `traffic` (DRAM bytes per launch, from ncu) is known for the plain kernel on
     the full-size workload only; null otherwise."""
     if kname == "plain":
         mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-instructions/s
+        peak_ops = sms * LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-instructions/s
         achieved = pairs * PLAIN_OPS_PER_PAIR / (join_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
                 "frac": achieved / peak_ops, "traffic": PLAIN_DRAM_BYTES_FULL if full_size and PLAIN_DRAM_BYTES_FULL else None,
                 "kernel": "k_plain",
-                "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)",
+                "peak_source": f"{sms} SMs x {LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)",
                 "ops_per_pair": PLAIN_OPS_PER_PAIR}
     tflops_peak = peaks.get("bf16_tflops", 1900.0)
     mult = 3 if kname == "bf16x3" else 1
@@ -688,7 +686,8 @@ def main():
     peaks, peak_src = load_peaks()
     join_ms = phase_ms[mp.MP_PHASE_JOIN] / max(1, phase_n[mp.MP_PHASE_JOIN])
     clock = clk.summary()
-    roof = roofline(args.kernel, pairs, w.m, join_ms, peaks, peak_src, full_size=args.scale == 1.0)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    roof = roofline(args.kernel, pairs, w.m, join_ms, peaks, peak_src, full_size=args.scale == 1.0, sms=sms)
     # the other join forms on the same workload (same timing method)
     kernels = {}
     for kname in ("plain", "bf16x3", "tf32"):
@@ -699,7 +698,7 @@ def main():
             sm, pm, pn, _ = time_device_join(mp, ctx, d, w, max(3, args.steps // 2), args.warmup, flush)
             mp.mp_set_kernel(ctx, kernel_id(mp, args.kernel))
         jm = pm[mp.MP_PHASE_JOIN] / max(1, pn[mp.MP_PHASE_JOIN])
-        r = roofline(kname, pairs, w.m, jm, peaks, peak_src)
+        r = roofline(kname, pairs, w.m, jm, peaks, peak_src, sms=sms)
         kernels[kname] = {"pairs_per_s": pairs / (float(np.mean(sm)) / 1e3), "ms_per_step": float(np.mean(sm)),
                           "join_kernel_ms": jm, "join_pairs_per_s": pairs / (jm / 1e3),
                           "roofline_frac": r["frac"], "roofline_unit": r["unit"], "achieved": r["achieved"]}

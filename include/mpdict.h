@@ -35,8 +35,9 @@
  *
  * Errors: every call returns MP_OK (0) or a negative MP_E_* code and, on
  * error, leaves a message for mp_last_error(). Invalid arguments (null
- * pointers, m < 2, n < m, NaN or Inf samples, unsorted offsets, unknown dtype)
- * give MP_E_ARG and change nothing. A CUDA failure gives MP_E_CUDA.
+ * pointers, m outside [4, 8192], n < m, NaN or Inf samples, unsorted offsets,
+ * unknown dtype) give MP_E_ARG and change nothing. A CUDA failure gives
+ * MP_E_CUDA. Every call that takes a window length accepts 4 <= m <= 8192.
  *
  * Threads: a context may be used from several host threads; calls on one
  * context are serialised internally. Distinct contexts are independent.
@@ -88,9 +89,11 @@ typedef struct mp_config {
     int32_t max_batch;     /* serving: requests merged into one persistent launch */
     size_t mem_budget;     /* serving: device bytes that admitted requests may hold; 0 = half the free memory at init */
     const char *tune_cache;/* autotuner cache file (JSON lines, see mp_autotune), or NULL for none */
+    int32_t max_pending;   /* serving: submitted requests that may wait for admission; mp_submit gives
+                              MP_E_BUSY beyond (default 65536) */
 } mp_config;
 
-/* Default configuration (device 0, AUTO kernel, 8 in flight, batch 64). */
+/* Default configuration (device 0, AUTO kernel, 8 in flight, batch 64, 65536 pending). */
 int mp_config_default(mp_config *cfg);
 
 /* Create a context on cfg->device (NULL cfg: defaults). *ctx receives the handle. */
@@ -159,7 +162,7 @@ int mp_ab_join_corr(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t
  * windows of length m as samples arrive; each window is joined once, when
  * its last sample arrives.
  *   mp_stream_open    the stream of one dictionary, dtype (the dictionary's)
- *                     and m (>= 2); the dictionary must outlive the stream.
+ *                     and m (4 .. 8192); the dictionary must outlive the stream.
  *   mp_stream_append  appends n_new host samples and joins the windows that
  *                     end in them: *n_out of them (n_new once m - 1 samples
  *                     have been seen before; fewer at the start), written to
@@ -372,6 +375,17 @@ int mp_profile_read(mp_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
  * Waits for all work on the context's device; reset = 1 zeroes them.
  */
 int mp_counters(mp_ctx *ctx, int64_t *values, int32_t reset);
+
+/* Testing hooks: host-side fault injection for the tests of the failure paths
+ * (the paper has no counterpart). */
+#define MP_HOOK_FAIL_ALLOC 0 /* the next `value` device allocations of serving requests fail as if the device
+                                were out of memory: those requests end MP_FAILED */
+#define MP_HOOK_TC_WAIT 1    /* bound, in SM clocks, of the tensor-core join's waits of one of its roles on
+                                another (0: the default, about 2 s); a bound too short for the work makes the
+                                join time out (mp_ab_join: MP_E_TIMEOUT; device calls: NaN and index -1). The
+                                kernel's last wait, for its own tensor-core work before it frees the tensor
+                                memory, keeps the default */
+int mp_test_hook(mp_ctx *ctx, int32_t hook, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,9 @@ MP_COUNTER_OVERFLOW_ROWS = 2
 MP_COUNTER_OVERFLOW_CHUNKS = 3
 MP_COUNTER_COUNT = 4
 
+MP_HOOK_FAIL_ALLOC = 0
+MP_HOOK_TC_WAIT = 1
+
 MP_LEARN_MEMORY = 0
 MP_LEARN_EMAX = 1
 
@@ -81,6 +84,7 @@ class mp_config(ctypes.Structure):
         ("max_batch", ctypes.c_int32),
         ("mem_budget", ctypes.c_size_t),
         ("tune_cache", ctypes.c_char_p),
+        ("max_pending", ctypes.c_int32),
     ]
 
 
@@ -125,6 +129,7 @@ def _load():
                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mp_profile_read": ([P, P, P, i32], ctypes.c_int),
         "mp_counters": ([P, P, i32], ctypes.c_int),
+        "mp_test_hook": ([P, i32, i64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -333,6 +338,11 @@ def mp_counters(ctx, reset: bool = False) -> np.ndarray:
     v = np.zeros(MP_COUNTER_COUNT, dtype=np.int64)
     _check(lib.mp_counters(ctx, _ptr(v), 1 if reset else 0))
     return v
+
+
+def mp_test_hook(ctx, hook: int, value: int) -> None:
+    """Host-side fault injection for tests (MP_HOOK_*)."""
+    _check(lib.mp_test_hook(ctx, hook, value))
 
 
 def mp_autotune(ctx, d, m: int, n: int, tolerance: float = 1e-4) -> Tuple[int, int, float]:

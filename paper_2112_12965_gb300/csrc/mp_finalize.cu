@@ -742,12 +742,13 @@ template <typename T, int KPL> cudaError_t launch_blk(const FinalizeParams<T> &p
 {
     constexpr int kNB = 32 * fin_warps<T>();
     // windows per warp: 32, unless that leaves fewer than about eight CTAs per
-    // SM (152 SMs), as for the short requests of the serving path
-    const int64_t per = (p.nq + 152 * 8 * fin_warps<T>() - 1) / (152 * 8 * fin_warps<T>());
+    // SM, as for the short requests of the serving path
+    const int64_t sms = p.sm_count > 0 ? p.sm_count : 1;
+    const int64_t per = (p.nq + sms * 8 * fin_warps<T>() - 1) / (sms * 8 * fin_warps<T>());
     const int wpw = (int)(per < 1 ? 1 : (per > 32 ? 32 : per));
     const int nb = fin_warps<T>() * wpw;
     int64_t grid = (p.nq + nb - 1) / nb;  // one block of query windows per CTA and pass
-    if (grid > 152 * 64) grid = 152 * 64;
+    if (grid > sms * 64) grid = sms * 64;
     k_finalize_blk<T, KPL><<<(unsigned)grid, kNB, 0, st>>>(p, wpw);
     return cudaGetLastError();
 }
@@ -767,7 +768,8 @@ cudaError_t launch_finalize(const FinalizeParams<T> &p, cudaStream_t st)
         }
     }
     int64_t grid = (p.nq + 7) / 8;  // 8 warps (rows) per CTA
-    if (grid > 152 * 64) grid = 152 * 64;
+    const int64_t sms = p.sm_count > 0 ? p.sm_count : 1;
+    if (grid > sms * 64) grid = sms * 64;
     k_finalize<T><<<(unsigned)grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }

@@ -262,6 +262,7 @@ template <typename T> struct FinalizeParams {
     const Span *cspans;
     const int32_t *cgroup_start;
     unsigned long long *ctr;  // may be null; kFinCounters counters, added to (see below)
+    int32_t sm_count;         // the device's SMs (launch shape)
     int32_t out_corr;         // 1: write rho = 1 - d^2 / (2m) (Pearson's r for non-constant windows), -inf if none
     // Self-join of one series (dictionary learning): windows g with |g - i| < excl are
     // trivial matches of query window i and are left out; next_const[x] is the lowest

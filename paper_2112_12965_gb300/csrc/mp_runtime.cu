@@ -75,6 +75,9 @@ static int fail(int code, const char *fmt, ...)
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Window lengths every call accepts (MP_E_ARG outside).
+constexpr int kMinM = 4, kMaxM = 8192;
+
 static double now_s()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -213,6 +216,10 @@ struct mp_ctx {
 
     // finalisation counters (kFinCounters, summed on the device by every join)
     unsigned long long *d_counters = nullptr;
+
+    // testing hooks (mp_test_hook)
+    int64_t hook_fail_alloc = 0;  // serving allocations still to fail (under smu)
+    long long hook_tc_wait = 0;   // tensor-core role-wait bound in clocks (0: the default)
 };
 
 static void tune_load(mp_ctx *ctx, const char *path);
@@ -288,7 +295,7 @@ static int check_join_args(mp_ctx *ctx, const mp_dict *dict, const void *q, int3
     if (!ctx || !dict || !q) return fail(MP_E_ARG, "null argument");
     if (dtype != MP_F32 && dtype != MP_F64) return fail(MP_E_ARG, "unknown dtype %d", dtype);
     if (dtype != dict->dtype) return fail(MP_E_ARG, "query dtype differs from the dictionary's");
-    if (m < 2 || m > 8192) return fail(MP_E_ARG, "m=%d outside [2, 8192]", m);
+    if (m < kMinM || m > kMaxM) return fail(MP_E_ARG, "m=%d outside [%d, %d]", m, kMinM, kMaxM);
     if (n < m) return fail(MP_E_ARG, "query length %lld shorter than m=%d", (long long)n, m);
     if (n >= ((int64_t)1 << 40)) return fail(MP_E_ARG, "query too long");
     if (dict->ctx != ctx) return fail(MP_E_ARG, "dictionary belongs to another context");
@@ -486,6 +493,7 @@ static FinalizeParams<T> fin_params(mp_ctx *ctx, int64_t nq, int32_t m, int n_gr
     f.cspans = nullptr;
     f.cgroup_start = nullptr;
     f.ctr = ctx->d_counters;
+    f.sm_count = ctx->sm_count;
     f.out_corr = 0;
     f.excl = 0;
     f.next_const = nullptr;
@@ -746,7 +754,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
                 int rc = tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
                                  (const float *)d->d_samples, d->nb, s->seg_spans.data(),
                                  (int32_t)s->seg_spans.size(), s->ms, s->rs, a, n, m, ms_a, rs_a, part, &near, err,
-                                 &ng, &cspans, &cgs, st, fail);
+                                 &ng, &cspans, &cgs, ctx->hook_tc_wait, st, fail);
                 if (rc) return rc;
             }
             {
@@ -1074,7 +1082,9 @@ static void scheduler_loop(mp_ctx *ctx)
             std::shared_ptr<Request> r = ctx->pending.front();
             if (ctx->mem_used + r->bytes > ctx->mem_budget && ctx->n_inflight_reqs > 0) break;
             ctx->pending.pop_front();
-            if (cudaMallocAsync(&r->dmem, r->bytes, bt.stream) != cudaSuccess) {
+            const bool injected = ctx->hook_fail_alloc > 0;  // a testing hook: fail as if out of memory
+            if (injected) --ctx->hook_fail_alloc;
+            if (injected || cudaMallocAsync(&r->dmem, r->bytes, bt.stream) != cudaSuccess) {
                 cudaGetLastError();
                 pinned_give(ctx, r->h_stage, r->stage_bytes);
                 r->h_stage = nullptr;
@@ -1132,6 +1142,7 @@ int mp_config_default(mp_config *cfg)
     cfg->max_batch = 64;
     cfg->mem_budget = 0;
     cfg->tune_cache = nullptr;
+    cfg->max_pending = 1 << 16;
     return MP_OK;
 }
 
@@ -1147,6 +1158,7 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
     if (cfg.kernel < MP_KERNEL_AUTO || cfg.kernel > MP_KERNEL_TC_TF32) return fail(MP_E_ARG, "unknown kernel");
     if (cfg.max_inflight <= 0) cfg.max_inflight = 8;
     if (cfg.max_batch <= 0) cfg.max_batch = 64;
+    if (cfg.max_pending <= 0) cfg.max_pending = 1 << 16;
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (cfg.device < 0 || cfg.device >= ndev) return fail(MP_E_ARG, "device %d of %d", cfg.device, ndev);
@@ -1230,7 +1242,7 @@ int mp_dict_load(mp_ctx *ctx, const void *samples, int32_t dtype, const int64_t 
     if (!host_all_finite(samples, dtype, nb)) return fail(MP_E_ARG, "dictionary has NaN or Inf samples");
     if (n_ms < 0 || (n_ms > 0 && !ms)) return fail(MP_E_ARG, "bad ms");
     for (int32_t k = 0; k < n_ms; ++k)
-        if (ms[k] < 2 || ms[k] > 8192) return fail(MP_E_ARG, "m=%d outside [2, 8192]", ms[k]);
+        if (ms[k] < kMinM || ms[k] > kMaxM) return fail(MP_E_ARG, "m=%d outside [%d, %d]", ms[k], kMinM, kMaxM);
     CUDA_TRY(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lk(ctx->mu);
     std::unique_ptr<mp_dict> d(new mp_dict());
@@ -1408,7 +1420,7 @@ int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int3
     g_err.clear();
     if (!ctx || !d_x || !d_mean || !d_invstd || !d_const) return fail(MP_E_ARG, "null argument");
     if (dtype != MP_F32 && dtype != MP_F64) return fail(MP_E_ARG, "unknown dtype");
-    if (m < 2 || m > 8192 || n < m) return fail(MP_E_ARG, "bad n/m");
+    if (m < kMinM || m > kMaxM || n < m) return fail(MP_E_ARG, "bad n/m (m in [%d, %d], n >= m)", kMinM, kMaxM);
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     if (dtype == MP_F64)
@@ -1450,13 +1462,21 @@ int mp_submit(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype
     r->stage_bytes = std::max((size_t)n * dtype_size(dtype), (size_t)nq * 16);
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
+        if ((int64_t)ctx->pending.size() >= ctx->cfg.max_pending)
+            return fail(MP_E_BUSY, "%zu requests wait for admission (max_pending %d)", ctx->pending.size(),
+                        ctx->cfg.max_pending);
         r->h_stage = pinned_take(ctx, r->stage_bytes);
     }
     if (!r->h_stage) return fail(MP_E_NOMEM, "pinned staging of %zu bytes", r->stage_bytes);
     memcpy(r->h_stage, query, (size_t)n * dtype_size(dtype));
-    d->refs.fetch_add(1);
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
+        if ((int64_t)ctx->pending.size() >= ctx->cfg.max_pending) {  // filled while the query was copied
+            pinned_give(ctx, r->h_stage, r->stage_bytes);
+            return fail(MP_E_BUSY, "%zu requests wait for admission (max_pending %d)", ctx->pending.size(),
+                        ctx->cfg.max_pending);
+        }
+        d->refs.fetch_add(1);
         r->ticket = ctx->next_ticket++;
         r->t_submit = now_s();
         ctx->tickets[r->ticket] = r;
@@ -1519,6 +1539,22 @@ int mp_profile_read(mp_ctx *ctx, double *ms, int64_t *launches, int32_t reset)
     return MP_OK;
 }
 
+int mp_test_hook(mp_ctx *ctx, int32_t hook, int64_t value)
+{
+    g_err.clear();
+    if (!ctx || value < 0) return fail(MP_E_ARG, "bad argument");
+    if (hook == MP_HOOK_FAIL_ALLOC) {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->hook_fail_alloc = value;
+    } else if (hook == MP_HOOK_TC_WAIT) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->hook_tc_wait = (long long)value;
+    } else {
+        return fail(MP_E_ARG, "unknown hook %d", hook);
+    }
+    return MP_OK;
+}
+
 int mp_counters(mp_ctx *ctx, int64_t *values, int32_t reset)
 {
     g_err.clear();
@@ -1575,7 +1611,8 @@ struct mp_stream {
 extern "C" int mp_stream_open(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int32_t m, mp_stream **out)
 {
     g_err.clear();
-    if (!ctx || !dict || !out || m < 2 || (dtype != MP_F32 && dtype != MP_F64)) return fail(MP_E_ARG, "bad argument");
+    if (!ctx || !dict || !out || m < kMinM || m > kMaxM || (dtype != MP_F32 && dtype != MP_F64))
+        return fail(MP_E_ARG, "bad argument");
     if (dtype != dict->dtype) return fail(MP_E_ARG, "stream dtype must match the dictionary's");
     mp_stream *st = new mp_stream();
     st->ctx = ctx;
@@ -1669,7 +1706,7 @@ static int check_series(mp_ctx *ctx, const void *x, int32_t dtype, int64_t n, in
 {
     if (!ctx || !x) return fail(MP_E_ARG, "null argument");
     if (dtype != MP_F32) return fail(MP_E_ARG, "the self-join and dictionary learning take float32 samples");
-    if (m < 4 || m > 8192) return fail(MP_E_ARG, "m=%d outside [4, 8192]", m);
+    if (m < kMinM || m > kMaxM) return fail(MP_E_ARG, "m=%d outside [%d, %d]", m, kMinM, kMaxM);
     if (n < m) return fail(MP_E_ARG, "series shorter than m");
     return MP_OK;
 }
@@ -1890,7 +1927,7 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
 {
     g_err.clear();
     if (!ctx || !dict) return fail(MP_E_ARG, "null argument");
-    if (m < 2 || m > 8192 || n < m) return fail(MP_E_ARG, "bad n/m");
+    if (m < kMinM || m > kMaxM || n < m) return fail(MP_E_ARG, "bad n/m (m in [%d, %d], n >= m)", kMinM, kMaxM);
     CUDA_TRY(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lk(ctx->mu);
     mp_dict *d = const_cast<mp_dict *>(dict);

@@ -44,6 +44,7 @@ namespace mpd {
 namespace {
 
 constexpr int kTcMaxN = 256;           // TMEM columns (FP32 accumulators) per CTA
+constexpr long long kTcWaitCycles = 4000000000LL;  // bound of a wait, about 2 s
 constexpr size_t kTcSmemLimit = 225 * 1024;
 
 struct TcTile {
@@ -74,6 +75,7 @@ struct TcArgs {
     int32_t qg;        // K-blocks per stage (one stage = one tile's K-group)
     int32_t rb_rows;   // rows of a stage buffer: (qg - 1) * values-per-row + nmax
     int32_t n_stages;  // stage buffers in flight (1 or 2)
+    long long wait_cycles;  // bound of the roles' waits on each other (clocks)
 };
 
 // ---------------------------------------------------------------------------
@@ -283,14 +285,14 @@ __device__ __forceinline__ bool named_sync_and(int id, int nthreads, bool pred)
     return r != 0;
 }
 
-// Bounded wait that also gives up as soon as another role has aborted.
-__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+// Bounded wait (about `limit` clocks) that also gives up as soon as another
+// role has aborted.
+__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, long long limit)
 {
-    constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
     if (warp == kMmaWarp) {
         // ---------------- MMA issue (one lane) ----------------
         if (lane == 0) {
-            bool ok = role_wait(full_a, 0, abort_flag);
+            bool ok = role_wait(full_a, 0, abort_flag, p.wait_cycles);
             tc_fence_after();
             const uint32_t a0 = smem_u32(ha[0]), a1 = smem_u32(ha[NHL - 1]);
             int j = 0;  // stage counter
@@ -380,14 +382,14 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
                 const TcTile tile = p.tiles[t];
                 const int ab = (t - t_lo) & 1;
                 const int k_t = (t - t_lo) >> 1;
-                if (k_t >= 1 && !(ok = role_wait(&acc_empty[ab], (k_t - 1) & 1, abort_flag))) break;
+                if (k_t >= 1 && !(ok = role_wait(&acc_empty[ab], (k_t - 1) & 1, abort_flag, p.wait_cycles))) break;
                 tc_fence_after();
                 const uint32_t d_tmem = taddr + (uint32_t)(ab * kTcMaxN);
                 const uint32_t idesc = instr_desc<VARIANT>(tile.nmma);
                 for (int q0 = 0; q0 < p.nkb; q0 += p.qg, ++j) {
                     const int q1 = min(p.nkb, q0 + p.qg);
                     const int s = j % NS;
-                    if (!(ok = role_wait(&full_b[s], (j / NS) & 1, abort_flag))) break;
+                    if (!(ok = role_wait(&full_b[s], (j / NS) & 1, abort_flag, p.wait_cycles))) break;
                     tc_fence_after();
                     const uint32_t b0 = smem_u32(hb + (s * NHL) * st_bytes);
                     const uint32_t b1 = smem_u32(hb + (s * NHL + NHL - 1) * st_bytes);
@@ -413,7 +415,8 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
             }
             // every MMA issued so far must finish before the TMEM is released
             mma_commit(drain);
-            role_wait(drain, 0, abort_flag) || mbar_wait(drain, 0, 4000000000LL);
+            // (a bound of its own, never shortened: the TMEM is freed only after it)
+            role_wait(drain, 0, abort_flag, p.wait_cycles) || mbar_wait(drain, 0, kTcWaitCycles);
         }
         __syncwarp();
     } else if (warp < kEpiWarp0) {
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
                 if (NS == 2 && s != bgrp) continue;  // the other group's stage
                 const int q1 = min(p.nkb, q0 + p.qg);
                 if (j >= NS) {
-                    const bool w = role_wait(&empty_b[s], ((j / NS) - 1) & 1, abort_flag);
+                    const bool w = role_wait(&empty_b[s], ((j / NS) - 1) & 1, abort_flag, p.wait_cycles);
                     if (!(gok = named_sync_and(bar_id, nthr, w))) break;
                 }
                 const int rows = (q1 - q0 - 1) * EPR + tile.nmma;
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
                 colp[n] = v;
             }
             named_sync(kBarEpi, kRoleThreads);
-            ok = role_wait(&acc_full[ab], k_t & 1, abort_flag);
+            ok = role_wait(&acc_full[ab], k_t & 1, abort_flag, p.wait_cycles);
             if (!(ok = named_sync_and(kBarEpi, kRoleThreads, ok))) break;
             tc_fence_after();
             const uint32_t t_lane = taddr + (uint32_t)(ab * kTcMaxN) + ((uint32_t)(quad * 32) << 16);
@@ -1047,7 +1050,8 @@ void tc_free_pack(void *pack)
 int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
             const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
             const void *rs_a, Partial<float> *part, NearRec *near, int32_t *err, int *n_groups_out,
-            const Span **cspans_out, const int32_t **cgroup_start_out, cudaStream_t st, fail_fn fail)
+            const Span **cspans_out, const int32_t **cgroup_start_out, long long wait_cycles, cudaStream_t st,
+            fail_fn fail)
 {
     static_assert(sizeof(TcTile) == sizeof(Span) && offsetof(TcTile, g0) == offsetof(Span, g0) &&
                       offsetof(TcTile, nvalid) == offsetof(Span, ncols),
@@ -1094,6 +1098,7 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     A.qg = P.qg;
     A.rb_rows = P.rb_rows;
     A.n_stages = P.n_stages;
+    A.wait_cycles = wait_cycles > 0 ? wait_cycles : kTcWaitCycles;
     cudaError_t e;
     auto launch = [&](auto kern) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);

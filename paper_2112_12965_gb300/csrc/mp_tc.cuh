@@ -27,11 +27,14 @@ void tc_free_pack(void *pack);
 // *n_groups_out; *cspans_out / *cgroup_start_out receive the column groups'
 // chunk layout (valid until the dictionary is freed). *err is set to 1 on a
 // device-side timeout. variant: 0 = split BF16 (3 products), 1 = TF32.
-// The caller sizes part and near for tc_groups_bound groups.
+// The caller sizes part and near for tc_groups_bound groups. wait_cycles
+// bounds the kernel's waits of one role on another (<= 0: about 2 s); the
+// final wait for the MMAs before the TMEM is freed keeps its own bound.
 int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
             const void *ms_b, const void *rs_b, const float *a, int64_t n, int32_t m, const void *ms_a,
             const void *rs_a, Partial<float> *part, NearRec *near, int32_t *err, int *n_groups_out,
-            const Span **cspans_out, const int32_t **cgroup_start_out, cudaStream_t st, fail_fn fail);
+            const Span **cspans_out, const int32_t **cgroup_start_out, long long wait_cycles, cudaStream_t st,
+            fail_fn fail);
 
 // Top seeds of the plain kernel (K2s) on the tensor cores: for the query
 // windows r_s = s * stride, s < ceil(nq / stride), and every valid dictionary

@@ -36,6 +36,7 @@ def test_roofline_objects():
     assert plain_full["frac"] == pytest.approx(plain_full["achieved"] / plain_full["peak"])
     # the measured DRAM traffic belongs to the full-size workload only
     assert plain_full["traffic"] == bench.PLAIN_DRAM_BYTES_FULL and plain_small["traffic"] is None
+    assert plain_full["peak"] == pytest.approx(152 * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12)
     tc = bench.roofline("bf16x3", pairs, m, 1.0, peaks, "test")
     assert tc["bound"] == "tensor" and tc["flops_per_pair"] == 2 * m * 3 and tc["traffic"] is None
     tf = bench.roofline("tf32", pairs, m, 1.0, peaks, "test")

@@ -34,7 +34,7 @@ def test_window_stats_match_oracle(mp, ctx):
     rng = np.random.default_rng(5)
     x = np.concatenate([rng.standard_normal(3000).cumsum() + 5000.0, np.full(300, 7.25),
                         rng.standard_normal(700)]).astype(np.float32)
-    for m in (3, 64, 257, 1024):
+    for m in (4, 64, 257, 1024):
         xt = torch.from_numpy(x).cuda()
         nw = len(x) - m + 1
         mean = torch.empty(nw, dtype=torch.float64, device="cuda")
@@ -125,7 +125,7 @@ def test_ecg_m1024_original_series_and_lemma_1(mp, ctx):
 EDGE_CASES = {
     # name: (query length, segment lengths, m, generator)
     "ragged_segments": (3001, [700, 129, 64, 1500, 63, 2], 64, "rw"),
-    "m2": (400, [50, 3, 1, 70], 2, "rw"),
+    "m4": (400, [50, 3, 1, 4, 70], 4, "rw"),
     "m37_odd": (1777, [300, 36, 37, 38, 900], 37, "ecg"),
     "one_row": (100, [250, 300], 100, "rw"),
     "one_window_segments": (2500, [96] * 40, 96, "rw"),
@@ -214,7 +214,7 @@ def test_argument_errors(mp, ctx):
     d = mp.mp_dict_load(ctx, b, [0, 1000], [32])
     try:
         q = synthetic.random_walk(200, 2).astype(np.float32)
-        for bad_m in (1, 201):
+        for bad_m in (1, 2, 3, 201, 8193):
             with pytest.raises(mp.MPError) as e:
                 mp.mp_ab_join(ctx, d, q, bad_m)
             assert e.value.code == mp.MP_E_ARG

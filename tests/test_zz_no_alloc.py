@@ -64,3 +64,36 @@ def test_noalloc_join_matches_device_join_on_two_calls(mp):
         mp.mp_dict_free(ctx, d)
     finally:
         mp.mp_shutdown(ctx)
+
+
+def test_noalloc_join_allocates_no_device_memory(mp):
+    """The defining property: after the first call on the device (which resolves the scratch array's address),
+    a call leaves the device's free memory unchanged. A regular join on a fresh context, by contrast, grows
+    the context's workspace."""
+    import torch
+
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        w = synthetic.workload("ecg_1m_m256", scale=1 / 16)
+        d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+        qt = torch.from_numpy(w.query).cuda()
+        nq = len(w.query) - w.m + 1
+        dist = torch.empty(nq, dtype=torch.float64, device="cuda")
+        idx = torch.empty(nq, dtype=torch.int64, device="cuda")
+        stream = torch.cuda.Stream()
+
+        def call(fn):
+            fn(ctx, d, qt.data_ptr(), mp.MP_F32, len(w.query), w.m, dist.data_ptr(), idx.data_ptr(),
+               stream.cuda_stream)
+            stream.synchronize()
+
+        call(mp.mp_ab_join_noalloc)  # first call on the device
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            call(mp.mp_ab_join_noalloc)
+        assert torch.cuda.mem_get_info()[0] == free0
+        call(mp.mp_ab_join_device)  # the context's workspace: allocated now
+        assert torch.cuda.mem_get_info()[0] < free0
+        mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)
