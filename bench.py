@@ -8,9 +8,11 @@ statistics, join kernel, finalisation with the exact distance of each pick).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--kernel plain|bf16x3|tf32|auto] [--serving-requests R]
 
-Prints one JSON line (rank 0). With N > 1 (launched by torchrun) every rank
-joins its own query of the same size (weak scaling, no data-path collective);
-the value is the total pairs of all ranks divided by the slowest rank's time.
+Prints one JSON line (rank 0). With N > 1 (launched by torchrun) the query has
+N times the headline's windows and is partitioned by query rows: every rank
+joins its run of windows plus their m - 1 halo samples (weak scaling, no
+data-path collective); the value is the total pairs of all ranks divided by
+the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -314,69 +316,6 @@ def time_e2e(mp, ctx, d, w, steps, warmup):
     return t, len(qa) * 4, nq * 16
 
 
-def serving_run(mp, n_requests, seed=7):
-    """A short serving run: Poisson arrivals of mixed requests; p50/p99 latency and throughput."""
-    import synthetic
-
-    if n_requests <= 0:
-        return None
-    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=8, max_batch=16)
-    try:
-        dicts = synthetic.serving_dictionaries(n_dicts=16, seed=100)
-        handles = [mp.mp_dict_load(ctx, b, offs, [64, 128, 256]) for b, offs in dicts]
-        reqs = synthetic.serving_requests(n_requests, rate_hz=1.0, seed=seed, n_dicts=16, max_log2=18)
-        # 1) capacity: everything submitted at once
-        outs, tickets, pairs = [], [], 0
-        t0 = time.perf_counter()
-        for r in reqs:
-            nq = len(r.query) - r.m + 1
-            od, oi = np.empty(nq), np.empty(nq, dtype=np.int64)
-            outs.append((od, oi))
-            tickets.append(mp.mp_submit(ctx, handles[r.dict_id], r.query, r.m, od, oi))
-            pairs += nq * mp.mp_dict_windows(handles[r.dict_id], r.m)
-        mp.mp_drain(ctx, 600.0)
-        cap_s = time.perf_counter() - t0
-        failed = sum(mp.mp_poll(ctx, t)[0] != mp.MP_DONE for t in tickets)
-        if failed:
-            raise RuntimeError(f"serving: {failed} of {len(tickets)} requests failed")
-        capacity_rps = len(reqs) / cap_s
-        # 2) offered load at 0.5x capacity, Poisson arrivals
-        rate = 0.5 * capacity_rps
-        rng = np.random.default_rng(seed + 1)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
-        outs, tickets = [], []
-        t0 = time.perf_counter()
-        for a, r in zip(arrivals, reqs):
-            while time.perf_counter() - t0 < a:
-                time.sleep(0.0001)
-            nq = len(r.query) - r.m + 1
-            od, oi = np.empty(nq), np.empty(nq, dtype=np.int64)
-            outs.append((od, oi))
-            tickets.append(mp.mp_submit(ctx, handles[r.dict_id], r.query, r.m, od, oi))
-        lats = []
-        pending = set(tickets)
-        while pending:
-            for t in list(pending):
-                st, lat = mp.mp_poll(ctx, t)
-                if st != mp.MP_PENDING:
-                    if st != mp.MP_DONE:
-                        raise RuntimeError(f"serving: request {t} failed")
-                    lats.append(lat)
-                    pending.discard(t)
-            time.sleep(0.0002)
-        wall = time.perf_counter() - t0
-        for h in handles:
-            mp.mp_dict_free(ctx, h)
-        lats = np.array(lats) * 1e3
-        return {"requests": len(reqs), "offered_rps": rate, "p50_ms": float(np.percentile(lats, 50)),
-                "p99_ms": float(np.percentile(lats, 99)), "throughput_rps": len(reqs) / wall,
-                "capacity_rps": capacity_rps, "capacity_pairs_per_s": pairs / cap_s,
-                "mix": "query 2^U samples U~U(10,18), random walk / ECG 50:50, m in {64,128,256}, "
-                       "16 resident dictionaries of 2^14..2^18 samples"}
-    finally:
-        mp.mp_shutdown(ctx)
-
-
 def _device_join_timed(mp, ctx, d, q, m, reps=3):
     """Join a host query on the device; returns (dist, idx, join ms per call: the join kernel plus, for
     the plain form, its tensor-core seed kernel)."""
@@ -398,6 +337,8 @@ def _device_join_timed(mp, ctx, d, q, m, reps=3):
     ms, n = mp.mp_profile_read(ctx, reset=True)
     mp.mp_profile(ctx, False)
     per_call = (ms[mp.MP_PHASE_JOIN] + ms[mp.MP_PHASE_SEEDS]) / reps  # a large join runs in several row chunks
+    _device_join_timed.last_phases = {"stats": ms[0] / reps, "join": ms[1] / reps, "finalize": ms[2] / reps,
+                                      "seeds": ms[3] / reps}
     return dd.cpu().numpy(), di.cpu().numpy(), float(per_call)
 
 
@@ -416,11 +357,18 @@ def study_precision(mp, rows=256):
         d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
         for kname in ("plain", "bf16x3", "tf32"):
             mp.mp_set_kernel(ctx, kernel_id(mp, kname))
+            mp.mp_counters(ctx, reset=True)
             dist, idx, jm = _device_join_timed(mp, ctx, d, w.query, w.m, reps=2)
+            ph = _device_join_timed.last_phases
+            c = mp.mp_counters(ctx, reset=True) / 3  # three joins: a warm-up and two timed
             err = np.abs(dist[r] - od)
             uniq = (od2 - od) > 1e-3
             out["forms"][kname] = {
-                "join_ms": jm, "pairs_per_s": w.pairs / (jm / 1e3),
+                "join_ms": jm, "pairs_per_s": w.pairs / (jm / 1e3), "phases_ms": ph,
+                "step_pairs_per_s": w.pairs / (sum(ph.values()) / 1e3),
+                "near_rows_per_join": float(c[mp.MP_COUNTER_NEAR_ROWS]),
+                "near_chunks_per_join": float(c[mp.MP_COUNTER_NEAR_CHUNKS]),
+                "overflow_rows_per_join": float(c[mp.MP_COUNTER_OVERFLOW_ROWS]),
                 "abs_err_max": float(err.max()), "abs_err_p99": float(np.percentile(err, 99)),
                 "abs_err_median": float(np.median(err)), "abs_err_mean": float(err.mean()),
                 "index_match": float(np.mean(idx[r] == oi)),
@@ -523,10 +471,15 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
     return out
 
 
-def study_serving(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256, window=64):
-    """Continuous-batching serving: capacity, then Poisson load at fractions of it; p50/p99 latency."""
+def serving_run(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256, window=64):
+    """The serving workload: 10,000 join requests, query lengths log-uniform in [2^10, 2^20] samples
+    (random walk and ECG-like 50:50), m uniform in {64, 128, 256}, against 16 resident dictionaries of
+    2^14..2^18 samples. First the capacity (a window of requests kept outstanding), then Poisson arrivals
+    at each fraction of it; p50/p99 latency and throughput per load. Every request must succeed."""
     import synthetic
 
+    if n_requests <= 0:
+        return None
     rng = np.random.default_rng(seed)
     dicts = synthetic.serving_dictionaries(n_dicts=16, seed=100)
     # a pool of queries, log-uniform in [2^10, 2^20] samples, random walk / ECG-like 50:50
@@ -539,7 +492,7 @@ def study_serving(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256
     reqs = [(int(rng.integers(0, pool_size)), int(rng.integers(0, 16)), int(rng.choice([64, 128, 256])))
             for _ in range(n_requests)]
     ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=16, max_batch=32)
-    out = {"study": "serving", "requests": n_requests,
+    out = {"requests": n_requests,
            "mix": "query 2^U samples, U ~ U(10, 20), random walk / ECG-like 50:50 from a pool of "
                   f"{pool_size} series; m uniform in {{64, 128, 256}}; 16 resident dictionaries of 2^14..2^18 "
                   "samples cut into segments of 512..4096", "loads": {}}
@@ -572,7 +525,8 @@ def study_serving(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256
             for t in list(live):
                 st, _ = mp.mp_poll(ctx, t)
                 if st != mp.MP_PENDING:
-                    assert st == mp.MP_DONE
+                    if st != mp.MP_DONE:
+                        raise RuntimeError(f"serving: request {t} failed")
                     del live[t]
                     done += 1
             time.sleep(0.0001)
@@ -595,7 +549,8 @@ def study_serving(mp, n_requests=10000, loads=(0.5, 0.9), seed=11, pool_size=256
                 for t in list(live):
                     st, l = mp.mp_poll(ctx, t)
                     if st != mp.MP_PENDING:
-                        assert st == mp.MP_DONE
+                        if st != mp.MP_DONE:
+                            raise RuntimeError(f"serving: request {t} failed")
                         lat.append(l)
                         del live[t]
                 time.sleep(0.0001)
@@ -619,7 +574,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "auto"])
-    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", choices=["precision", "dict-vs-orig", "serving", "learn"], default=None,
                     help="run a study instead of the headline benchmark (one JSON line)")
@@ -653,7 +608,7 @@ def main():
         if args.study == "precision":
             res = study_precision(mp)
         elif args.study == "serving":
-            res = study_serving(mp)
+            res = dict(study="serving", **serving_run(mp))
         elif args.study == "learn":
             res = study_learn(mp)
         else:
@@ -663,8 +618,14 @@ def main():
         return
 
     w = synthetic.workload(WORKLOAD, scale=args.scale)
-    if rank > 0:  # weak scaling: each rank joins its own query of the same size
-        w.query = synthetic.ecg_like(len(w.query), 2 + 1000 * rank, n_malformed=min(20, len(w.query) // 400)).astype(np.float32)
+    if world > 1:
+        # weak scaling over the query-row partition: one ECG-like query of world x the headline's windows,
+        # rank r joining its contiguous run of windows (plus their m - 1 halo samples); the per-rank
+        # profiles concatenate to the whole profile with no exchange between ranks
+        nq1 = len(w.query) - w.m + 1
+        full = synthetic.ecg_like(world * nq1 + w.m - 1, 2, n_malformed=20 * world).astype(np.float32)
+        lo, hi = shard_rows(len(full), w.m, world, rank)
+        w.query = full[lo:hi]
     ctx = mp.mp_init(device=local_rank, kernel=kernel_id(mp, args.kernel))
     d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -677,8 +638,9 @@ def main():
     torch.cuda.synchronize()
     total_ms = max_over_ranks(float(np.sum(step_ms)), world, device="cuda")
     ms_per_step = total_ms / args.steps
-    pairs = w.pairs
-    value = world * pairs * args.steps / (total_ms / 1e3)
+    pairs = w.pairs  # this rank's
+    total_pairs = world * nq1 * w.n_dict_windows if world > 1 else pairs  # the windows of all shards
+    value = total_pairs * args.steps / (total_ms / 1e3)
 
     e2e_t, h2d, d2h = time_e2e(mp, ctx, d, w, max(3, args.steps // 2), 1)
     e2e_value = pairs / float(np.mean(e2e_t))
@@ -710,7 +672,8 @@ def main():
         "config": {"workload": WORKLOAD_DESC, "n_query_windows": w.n_rows, "n_dict_windows": w.n_dict_windows,
                    "pairs_per_step_per_gpu": pairs, "kernel": args.kernel, "scale": args.scale,
                    "l2": "flushed between timed steps (512 MB write outside the timed events)",
-                   "parallelism": f"{world} independent queries (weak scaling)" if world > 1 else "1 GPU"},
+                   "parallelism": (f"one query of {world} x the windows, sharded by query rows over {world} GPUs "
+                                   "(weak scaling, no data-path collective)") if world > 1 else "1 GPU"},
         "phases_ms": {"stats": phase_ms[0] / max(1, phase_n[0]), "seeds": phase_ms[3] / max(1, phase_n[3]),
                       "join": join_ms, "finalize": phase_ms[2] / max(1, phase_n[2])},
         "roofline": roof,
@@ -725,6 +688,10 @@ def main():
     if rank == 0:
         serving = serving_run(mp, args.serving_requests)
         if serving:
+            # headline percentiles at half the capacity; the synchronous join's rate for comparison
+            half = serving["loads"].get("0.5x", {})
+            serving = {"p50_ms": half.get("p50_ms"), "p99_ms": half.get("p99_ms"), **serving,
+                       "capacity_vs_sync_join": serving["capacity_pairs_per_s"] / value}
             line["serving"] = serving
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)

@@ -860,10 +860,18 @@ static Geometry serve_geometry(const mp_ctx *ctx, int64_t nq, const DictStats *s
 // Device bytes of a request: its query, its outputs (dist, idx) and a
 // workspace for either way it may run (alone through join_device, or in the
 // batched kernel).
+// Query windows from which a serving request of FP32 data runs alone on the
+// batch's stream, with the headline join's kernels (tensor-core top seeds and
+// the packed plain kernel at three CTAs per SM), rather than as items of the
+// batched kernel (its own scalar seeds, two CTAs per SM). Such a request fills
+// the GPU by itself: 2^16 windows are 26 row blocks in each column group.
+constexpr int64_t kServeAloneRows = (int64_t)1 << 16;
+static bool serve_alone(const Request &r) { return r.n - r.m + 1 >= kServeAloneRows; }
+
 static size_t request_ws_bytes(const mp_ctx *ctx, const Request &r, const DictStats *s)
 {
     const int64_t nq = r.n - r.m + 1;
-    size_t ws = join_ws_bytes(ctx, r.dict, s, r.dtype, r.n, r.m, false);
+    size_t ws = join_ws_bytes(ctx, r.dict, s, r.dtype, r.n, r.m, r.dtype == MP_F32 && serve_alone(r));
     if (s->n_windows > 0 && r.dtype == MP_F32)
         ws = std::max(ws, join_ws_layout(nq, r.dtype, serve_geometry(ctx, nq, s, r.dtype, r.m).n_groups, 0).total);
     return ws;
@@ -965,14 +973,16 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         int64_t *idx = (int64_t *)(p + nq * 8);
         p += align_up(nq * 16, 256);
         CUDA_TRY(cudaMemcpyAsync(q, r.h_stage, (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
-        if (s->n_windows == 0 || r.dtype == MP_F64 || resolve_kernel(ctx, r.dtype, r.m, s, nq) != MP_KERNEL_PLAIN) {
-            // Requests that do not fit the batched FP32 plain kernel run alone.
+        const int kern = s->n_windows > 0 ? resolve_kernel(ctx, r.dtype, r.m, s, nq) : MP_KERNEL_PLAIN;
+        if (s->n_windows == 0 || r.dtype == MP_F64 || kern != MP_KERNEL_PLAIN || serve_alone(r)) {
+            // Requests that do not fit the batched FP32 plain kernel, and
+            // large ones, run alone on the batch's stream.
             if (s->n_windows == 0) {
                 r.no_windows = true;  // +inf / -1, written at completion
                 continue;
             }
-            rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p,
-                             resolve_kernel(ctx, r.dtype, r.m, s, nq), false);
+            rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p, kern,
+                             r.dtype == MP_F32 && serve_alone(r));
             if (rc) return rc;
             CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
             continue;

@@ -4,14 +4,18 @@
 // population standard deviation. They are kept in FP64 because sums of
 // squares cancel badly in FP32 when a series carries a large offset (random
 // walks). Each CTA handles a tile of consecutive windows:
-//   1. the tile's samples are staged in shared memory with coalesced loads,
-//      shifted by the tile's first sample (the statistics are shift
-//      invariant, and the shift keeps the prefix sums small);
+//   1. the tile's samples are staged in shared memory with coalesced 16-byte
+//      vector loads, then shifted by the tile's first sample (the statistics
+//      are shift invariant, and the shift keeps the prefix sums small);
 //   2. a block-wide prefix sum gives, for every window, sum(y) and sum(y^2)
 //      over its m samples in O(1);
 //   3. an integer prefix count of neighbouring samples that differ gives the
 //      exact constant-window flag.
 #include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <type_traits>
 
 #include "mp_internal.cuh"
 
@@ -105,12 +109,42 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
     __shared__ int warp_tot_i[kStatsThreads / 32];
     __shared__ double tot;
 
-    const double shift = (double)x[w0];
-    for (int e = threadIdx.x; e < E; e += kStatsThreads) {
-        const int64_t j = w0 - 1 + e;
-        ys[e] = (j >= 0 && j < n) ? (double)x[j] - shift : 0.0;
+    // 1. The tile's raw samples, staged with 16-byte vector loads (the
+    //    ragged ends, samples outside [0, n) and unaligned series take scalar
+    //    loads), in the space of the y^2 prefix, which is written only later.
+    T *xs = reinterpret_cast<T *>(p2);
+    constexpr int V = 16 / sizeof(T);
+    using VecT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const int64_t base = w0 - 1;  // sample of e = 0
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    const int64_t a0 = (base >= 0 ? base : base - (V - 1)) / V * V;  // base rounded down to a vector
+    const int nvec = (int)((base + E - a0 + V - 1) / V);
+    for (int v = threadIdx.x; v < nvec; v += kStatsThreads) {
+        const int64_t g = a0 + (int64_t)v * V;
+        T vals[V];
+        if (vec_ok && g >= 0 && g + V <= n) {
+            const VecT u = *reinterpret_cast<const VecT *>(x + g);
+            memcpy(vals, &u, sizeof u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) vals[k] = (g + k >= 0 && g + k < n) ? x[g + k] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int64_t e = g + k - base;
+            if (e >= 0 && e < E) xs[e] = vals[k];
+        }
     }
     __syncthreads();
+    // 2. Shifted samples (FP64) and the "differs from the next sample" bits.
+    const double shift = (double)xs[1];  // x[w0]
+    for (int e = threadIdx.x; e < E; e += kStatsThreads) {
+        const int64_t j = base + e;
+        const T xv = xs[e];
+        ys[e] = (j >= 0 && j < n) ? (double)xv - shift : 0.0;
+        pc[e] = (e + 1 < E && j >= 0 && j + 1 < n && xv != xs[e + 1]) ? 1 : 0;
+    }
+    __syncthreads();  // the raw samples are no longer read
 
     // Each thread owns a contiguous chunk of the E samples.
     const int per = (E + kStatsThreads - 1) / kStatsThreads;
@@ -121,8 +155,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
         const double y = ys[e];
         s1 += y;
         s2 += y * y;
-        const int64_t j = w0 - 1 + e;
-        if (e + 1 < E && j >= 0 && j + 1 < n) sc += (x[j] != x[j + 1]) ? 1 : 0;
+        sc += pc[e];
     }
     const double o1 = block_exclusive_scan(s1, warp_tot, &tot);
     const double o2 = block_exclusive_scan(s2, warp_tot, &tot);
@@ -135,8 +168,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
         int ac = oc;
         for (int e = e_lo; e < e_hi; ++e) {
             const double y = ys[e];
-            const int64_t j = w0 - 1 + e;
-            const int d = (e + 1 < E && j >= 0 && j + 1 < n) ? ((x[j] != x[j + 1]) ? 1 : 0) : 0;
+            const int d = pc[e];
             ys[e] = a1;  // exclusive prefix: sum of y over [0, e)
             p2[e] = a2;
             pc[e] = ac;

@@ -266,6 +266,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on `bar`,
+// which this call arms with the expected byte count (one arrival).
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void named_sync(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -332,8 +345,11 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
     float *raw = reinterpret_cast<float *>(hb + NS * NHL * st_bytes);  // query staging, then two tile stagings
     const int raw_tile = p.nmax + p.m + EPR;  // samples a tile's stages read
     const int raw_a = p.ra_rows + EPR;
-    float *raw_b[2] = {raw + raw_a, raw + raw_a + raw_tile};
-    float4 *colp = reinterpret_cast<float4 *>(raw + ((raw_a + 2 * raw_tile + 3) & ~3));
+    // a tile buffer also holds the bulk copy's alignment slack (up to 3 values
+    // before the tile, rounding to 4 after): raw_tile + 8 values, 16-byte aligned
+    const int raw_tb = raw_tile + 8;
+    float *raw_b[2] = {raw + raw_a, raw + raw_a + raw_tb};
+    float4 *colp = reinterpret_cast<float4 *>(raw + ((raw_a + 2 * raw_tb + 3) & ~3));
     uint64_t *bars = reinterpret_cast<uint64_t *>(colp + kTcMaxN);
     uint64_t *full_a = bars + 0;
     uint64_t *full_b = bars + 1;     // [2]
@@ -341,7 +357,8 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
     uint64_t *acc_full = bars + 5;   // [2]
     uint64_t *acc_empty = bars + 7;  // [2]
     uint64_t *drain = bars + 9;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+    uint64_t *copy_b = bars + 10;    // [2]: bulk copies of the tile samples
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 12);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -365,6 +382,8 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
             mbar_init(&acc_empty[b], kRoleThreads);
         }
         mbar_init(drain, 1);
+        mbar_init(&copy_b[0], 1);
+        mbar_init(&copy_b[1], 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -426,6 +445,51 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
         // worth of MMA time per build; with one buffer both groups build it.
         const int bt = tid - kBuildWarp0 * 32;  // 0 .. 255
         const int bgrp = bt >> 7, gt = bt & (kRoleThreads - 1);
+        // Each tile's samples b[g0 .. g0 + nmma + m + values-per-row) are staged
+        // once in shared memory (two tile buffers). One builder copies the
+        // next tile's samples with a bulk asynchronous copy (cp.async.bulk,
+        // completing on an mbarrier) at the top of the current tile, so that
+        // the copy overlaps the current tile's builds and MMAs; at the tile's
+        // end the builders shift them in place by the next tile's mean.
+        constexpr int kPre = 6;  // covers nmax + m + values-per-row <= kPre * 256
+        float pre[kPre];
+        int issued0 = 0, issued1 = 0;  // bt == 0: copies issued into each buffer
+        auto issue_copy = [&](int t) {
+            const TcTile tl = p.tiles[t];
+            const int buf = (t - t_lo) & 1;
+            const int64_t a = tl.g0 & ~(int64_t)3;  // 16-byte aligned source
+            int64_t c = (tl.g0 - a + raw_tile + 3) & ~(int64_t)3;
+            const int64_t lim = (p.nb + 16 - a) & ~(int64_t)3;  // the dictionary buffer's readable end
+            if (c > lim) c = lim;
+            fence_async_smem();  // the buffer's earlier (generic) accesses come first
+            bulk_copy_g2s(raw_b[buf], p.b + a, (uint32_t)c * 4u, &copy_b[buf]);
+            issued0 += buf == 0;
+            issued1 += buf == 1;
+        };
+        // wait for tile t's copy and shift its samples to the start of the
+        // buffer (zeros past the dictionary); false if a wait gave up
+        auto land_tile = [&](int t) -> bool {
+            const int buf = (t - t_lo) & 1;
+            const bool w = role_wait(&copy_b[buf], ((t - t_lo) >> 1) & 1, abort_flag, p.wait_cycles);
+            if (!named_sync_and(kBarBuild, kBuildThreads, w)) return false;
+            const TcTile tl = p.tiles[t];
+            const float sb = p.ms_b[tl.g0].hi;
+            const int o = (int)(tl.g0 & 3);
+            float *dst = raw_b[buf];
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const int e = bt + k * kBuildThreads;
+                pre[k] = (e < raw_tile && tl.g0 + e < p.nb) ? dst[o + e] - sb : 0.f;
+            }
+            named_sync(kBarBuild, kBuildThreads);
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const int e = bt + k * kBuildThreads;
+                if (e < raw_tile) dst[e] = pre[k];
+            }
+            return true;
+        };
+        if (bt == 0 && t_lo < t_hi) issue_copy(t_lo);
         const float s_a = p.ms_a[i0 < p.nq ? i0 : p.nq - 1].hi;
         for (int e = bt; e < raw_a; e += kBuildThreads) {
             const int64_t jj = i0 + e;
@@ -435,43 +499,17 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
         build_hankel<VARIANT>(raw, p.ra_rows, ha[0], ha[1], bt, kBuildThreads);
         fence_async_smem();
         mbar_arrive(full_a);
-        // Each tile's samples b[g0 .. g0 + nmma + m + values-per-row) are staged
-        // once in shared memory (two tile buffers); the next tile's samples are
-        // loaded into registers at the top of the current tile, so their
-        // global-memory latency overlaps the current tile's MMAs.
-        constexpr int kPre = 6;  // covers nmax + m + values-per-row <= kPre * 256
-        float pre[kPre];
-        auto load_tile = [&](int t) {
-            const TcTile tl = p.tiles[t];
-            const float sb = p.ms_b[tl.g0].hi;
-#pragma unroll
-            for (int k = 0; k < kPre; ++k) {
-                const int e = bt + k * kBuildThreads;
-                const int64_t jj = tl.g0 + e;
-                pre[k] = (e < raw_tile && jj < p.nb) ? p.b[jj] - sb : 0.f;
-            }
-        };
-        auto store_tile = [&](float *dst) {
-#pragma unroll
-            for (int k = 0; k < kPre; ++k) {
-                const int e = bt + k * kBuildThreads;
-                if (e < raw_tile) dst[e] = pre[k];
-            }
-        };
-        if (t_lo < t_hi) {
-            load_tile(t_lo);
-            store_tile(raw_b[0]);
-        }
+        bool ok = t_lo >= t_hi || land_tile(t_lo);
         named_sync(kBarBuild, kBuildThreads);
         const int nthr = NS == 2 ? kRoleThreads : kBuildThreads;
         const int tt = NS == 2 ? gt : bt;
         const int bar_id = NS == 2 ? kBarGroup0 + bgrp : kBarBuild;
         int j = 0;
-        bool ok = true;
         for (int t = t_lo; ok && t < t_hi; ++t) {
             const TcTile tile = p.tiles[t];
             const float *rt = raw_b[(t - t_lo) & 1];
-            if (t + 1 < t_hi) load_tile(t + 1);
+            // the other buffer's last tile (t - 1) is built: it takes tile t + 1
+            if (bt == 0 && t + 1 < t_hi) issue_copy(t + 1);
             j = (t - t_lo) * ((p.nkb + p.qg - 1) / p.qg);  // stages before this tile
             bool gok = true;
             for (int q0 = 0; q0 < p.nkb; q0 += p.qg, ++j) {
@@ -490,9 +528,13 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
             }
             // every builder takes the same branch (j is recomputed per tile below)
             if (!(ok = named_sync_and(kBarBuild, kBuildThreads, gok))) break;
-            if (t + 1 < t_hi) store_tile(raw_b[(t + 1 - t_lo) & 1]);
+            if (t + 1 < t_hi && !(ok = land_tile(t + 1))) break;
             named_sync(kBarBuild, kBuildThreads);
         }
+        // a copy still in flight (a wait gave up) must land before the shared
+        // memory is released: its own bound, never shortened
+        if (bt == 0 && issued0 > 0) mbar_wait(&copy_b[0], (uint32_t)((issued0 - 1) & 1), kTcWaitCycles);
+        if (bt == 0 && issued1 > 0) mbar_wait(&copy_b[1], (uint32_t)((issued1 - 1) & 1), kTcWaitCycles);
     } else {
         // ---------------- epilogue: one query window per thread ----------------
         const int quad = warp & 3;                 // TMEM lanes this warp may read
@@ -848,9 +890,9 @@ struct TcPlan {
 
 size_t plan_smem(const TcPlan &P)
 {
-    const size_t raw = (size_t)(P.ra_rows + P.epr) + 2 * (size_t)(P.nmax + P.m + P.epr);
+    const size_t raw = (size_t)(P.ra_rows + P.epr) + 2 * (size_t)(P.nmax + P.m + P.epr + 8);
     return 1024 + (size_t)P.nhl * 128 * ((size_t)P.ra_rows + (size_t)P.n_stages * P.rb_rows) +
-           ((raw + 3) & ~(size_t)3) * 4 + kTcMaxN * sizeof(float4) + 11 * 8 + 16;
+           ((raw + 3) & ~(size_t)3) * 4 + kTcMaxN * sizeof(float4) + 13 * 8 + 16;
 }
 
 // Estimated SM clocks per tile: the MMAs (or the shared-memory traffic they
