@@ -250,6 +250,7 @@ def seed_roofline(w, seeds_ms, peaks, peak_src):
 
 def kernel_id(mp, name):
     return {"plain": mp.MP_KERNEL_PLAIN, "bf16x3": mp.MP_KERNEL_TC_BF16X3, "tf32": mp.MP_KERNEL_TC_TF32,
+            "bf16": mp.MP_KERNEL_TC_BF16,
             "auto": mp.MP_KERNEL_AUTO}[name]
 
 
@@ -451,6 +452,40 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
             n_win += len(sd)
         t_stream = time.perf_counter() - t0
         mp.mp_stream_close(st)
+        # the same appends without waiting (mp_stream_submit: each append a serving request), up to
+        # 256 outstanding; equal to the synchronous appends' results
+        st = mp.mp_stream_open(ctx, d, mp.MP_F32, m)
+        t0 = time.perf_counter()
+        live, outs, n_win_async = {}, [], 0
+        for a in range(0, len(q), 1024):
+            piece = q[a : a + 1024]
+            od, oi = np.empty(len(piece)), np.empty(len(piece), dtype=np.int64)
+            while True:
+                try:
+                    t, k, _ = mp.mp_stream_submit(st, piece, od, oi)
+                    break
+                except mp.MPError as e:  # admission queue full: wait for some
+                    if e.code != mp.MP_E_BUSY:
+                        raise
+                    time.sleep(0.0001)
+            outs.append((od, oi, k))
+            n_win_async += k
+            if t:
+                live[t] = True
+            while len(live) >= 256:
+                for tk in list(live):
+                    stt, _ = mp.mp_poll(ctx, tk)
+                    if stt != mp.MP_PENDING:
+                        if stt != mp.MP_DONE:
+                            raise RuntimeError("stream append failed")
+                        del live[tk]
+        mp.mp_drain(ctx, 600.0)
+        for tk in list(live):
+            stt, _ = mp.mp_poll(ctx, tk)
+            if stt != mp.MP_DONE:
+                raise RuntimeError("stream append failed")
+        t_async = time.perf_counter() - t0
+        mp.mp_stream_close(st)
         n_w = mp.mp_dict_windows(d, m)
         mp.mp_dict_free(ctx, d)
         # the float64 oracle's Algorithm 1 on a 1/32 sample (the same loop, for context)
@@ -465,6 +500,8 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
             "profile_self_join_min_max": [float(np.min(P)), float(np.max(P))],
             "stream_appends_of_1024": int((len(q) + 1023) // 1024), "stream_windows": n_win,
             "stream_windows_per_s": n_win / t_stream, "stream_pairs_per_s": n_win * n_w / t_stream,
+            "stream_submit_windows_per_s": n_win_async / t_async,
+            "stream_submit_pairs_per_s": n_win_async * n_w / t_async,
             "oracle_learn_s_on_1_32": t_or, "oracle_cores": os.cpu_count()})
     finally:
         mp.mp_shutdown(ctx)

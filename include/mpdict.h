@@ -71,6 +71,13 @@ extern "C" {
 #define MP_KERNEL_PLAIN 1     /* diagonal recurrence on the FP32 (F64 data: FP64) pipes */
 #define MP_KERNEL_TC_BF16X3 2 /* tcgen05 Hankel tiles, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
 #define MP_KERNEL_TC_TF32 3   /* tcgen05 Hankel tiles, one TF32 product, FP32 accumulation */
+#define MP_KERNEL_TC_BF16 4   /* tcgen05 Hankel tiles, one BF16 product, FP32 accumulation */
+/* Every form picks each row's window exactly: the join kernels keep an
+ * approximate score per 16-window chunk and record every chunk that comes
+ * within the form's error of the best (the tensor-core forms bound that error
+ * from their operands' rounding), and the finalisation re-scores those chunks
+ * and recomputes the chosen pair's distance from its definition. The forms
+ * differ in speed, and in how many chunks they leave to re-score. */
 
 /* request states (mp_poll) */
 #define MP_PENDING 0
@@ -178,6 +185,19 @@ int mp_stream_open(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int32_t m, m
 int mp_stream_append(mp_stream *stream, const void *samples, int64_t n_new, double *out_dist, int64_t *out_idx,
                      int64_t *n_out, int64_t *first_window);
 int mp_stream_close(mp_stream *stream);
+/*
+ * The append of mp_stream_append without waiting for the result: the windows
+ * that end in the new samples become one serving request (see mp_submit), so
+ * that appends of this stream and of other streams are batched on the device
+ * while the caller keeps appending. out_dist / out_idx (host, room for n_new
+ * values) must stay valid until mp_poll(*ticket) reports MP_DONE or
+ * MP_FAILED; *n_out and *first_window are set at once; *ticket is 0 when no
+ * window ended (fewer than m samples seen so far). The samples are copied.
+ * Errors as mp_submit (MP_E_BUSY when the admission queue is full); on error
+ * nothing of the append is kept.
+ */
+int mp_stream_submit(mp_stream *stream, const void *samples, int64_t n_new, double *out_dist, int64_t *out_idx,
+                     uint64_t *ticket, int64_t *n_out, int64_t *first_window);
 
 /*
  * Self-join matrix profile of one float32 series (the input of Algorithm 1,

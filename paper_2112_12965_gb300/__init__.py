@@ -36,6 +36,7 @@ MP_KERNEL_AUTO = 0
 MP_KERNEL_PLAIN = 1
 MP_KERNEL_TC_BF16X3 = 2
 MP_KERNEL_TC_TF32 = 3
+MP_KERNEL_TC_BF16 = 4
 
 MP_PHASE_STATS = 0
 MP_PHASE_JOIN = 1
@@ -111,6 +112,8 @@ def _load():
         "mp_stream_open": ([P, P, i32, i32, ctypes.POINTER(P)], ctypes.c_int),
         "mp_stream_append": ([P, P, i64, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "mp_stream_close": ([P], ctypes.c_int),
+        "mp_stream_submit": ([P, P, i64, P, P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64),
+                              ctypes.POINTER(i64)], ctypes.c_int),
         "mp_self_join": ([P, P, i32, i64, i32, i32, P, P], ctypes.c_int),
         "mp_learn_dictionary": ([P, P, i32, i64, i32, ctypes.c_double, i32, ctypes.c_double, i32, P, P,
                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(i32)],
@@ -275,6 +278,20 @@ def mp_stream_append(stream, samples: np.ndarray) -> Tuple[np.ndarray, np.ndarra
                                 ctypes.byref(first)))
     k = n_out.value
     return dist[:k].copy(), idx[:k].copy(), first.value
+
+
+def mp_stream_submit(stream, samples: np.ndarray, out_dist: np.ndarray, out_idx: np.ndarray) -> Tuple[int, int, int]:
+    """Append samples without waiting; returns (ticket or 0, windows, first window). The outputs (float64 /
+    int64, at least len(samples) long) must stay alive until mp_poll reports the ticket done."""
+    x = np.ascontiguousarray(samples)
+    n = len(x)
+    assert out_dist.dtype == np.float64 and out_idx.dtype == np.int64 and len(out_dist) >= n and len(out_idx) >= n
+    t = ctypes.c_uint64()
+    n_out = ctypes.c_int64()
+    first = ctypes.c_int64()
+    _check(lib.mp_stream_submit(stream, _ptr(x) if n else None, n, _ptr(out_dist), _ptr(out_idx), ctypes.byref(t),
+                                ctypes.byref(n_out), ctypes.byref(first)))
+    return t.value, n_out.value, first.value
 
 
 def mp_stream_close(stream) -> None:

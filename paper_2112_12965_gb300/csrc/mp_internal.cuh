@@ -94,7 +94,7 @@ struct NearSlot {
 };
 constexpr int32_t kNearCountMask = 0x3f;  // header bits 0-5: slots in use
 constexpr int32_t kNearOverflow = 0x80;   // header bit 7: a record within the width was dropped
-constexpr int kNearMaxSlots = 32;
+constexpr int kNearMaxSlots = 63;
 struct NearRec {
     // [n_groups][1 + S][ld]: entry (k, 0, r) is the header of (group k, row r)
     // (its g holds the slots in use | kNearOverflow; the join zeroes the headers
@@ -124,10 +124,12 @@ constexpr float kNearRhoFP32 = 4e-5f;
 //   split BF16 (hi*hi + hi*lo + lo*hi): hi + lo within 2^-18 of each operand,
 //     lo*lo left out: 3 * 2^-18
 //   FP32 sum of the m (TF32) or 3m (split BF16) products: 2^-23 per product
+//   single BF16 product: operands rounded to 8 significant bits (2^-9 each)
 constexpr float kTcUnitTF32 = 9.7752e-4f;    // 2^-10 + 2^-21
 constexpr float kTcUnitBF16X3 = 1.1445e-5f;  // 3 * 2^-18
+constexpr float kTcUnitBF16 = 3.9101e-3f;    // 2^-8 + 2^-17
 constexpr int kNearSlotsPlain = 4;
-constexpr int kNearSlotsTC = 32;
+constexpr int kNearSlotsTC = 63;
 constexpr int kTcRows = 128;  // query windows per CTA of the tensor-core join (one per TMEM lane)
 
 #ifdef __CUDACC__

@@ -603,7 +603,12 @@ struct JoinWs {
 };
 
 // Near-tie record slots per (column group, query window) a join form uses.
-static bool is_tc(int kernel) { return kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32; }
+static bool is_tc(int kernel)
+{
+    return kernel == MP_KERNEL_TC_BF16X3 || kernel == MP_KERNEL_TC_TF32 || kernel == MP_KERNEL_TC_BF16;
+}
+// tc_join's variant of a tensor-core form
+static int tc_variant(int kernel) { return kernel == MP_KERNEL_TC_TF32 ? 1 : (kernel == MP_KERNEL_TC_BF16 ? 2 : 0); }
 static int near_slots_for(int kernel) { return is_tc(kernel) ? kNearSlotsTC : kNearSlotsPlain; }
 
 // near_slots: record slots per (column group, query window) of FP32 joins.
@@ -751,7 +756,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             const int32_t *cgs = nullptr;
             {
                 PhaseTimer t(ctx, MP_PHASE_JOIN, st);
-                int rc = tc_join(ctx->sm_count, kernel == MP_KERNEL_TC_TF32 ? 1 : 0, &s->tc_pack,
+                int rc = tc_join(ctx->sm_count, tc_variant(kernel), &s->tc_pack,
                                  (const float *)d->d_samples, d->nb, s->seg_spans.data(),
                                  (int32_t)s->seg_spans.size(), s->ms, s->rs, a, n, m, ms_a, rs_a, part, &near, err,
                                  &ng, &cspans, &cgs, ctx->hook_tc_wait, st, fail);
@@ -838,6 +843,7 @@ static int resolve_kernel(const mp_ctx *ctx, int32_t dtype, int32_t m, const Dic
     }
     if (k == MP_KERNEL_TC_BF16X3 && !tc_supported(0, m)) k = MP_KERNEL_PLAIN;
     if (k == MP_KERNEL_TC_TF32 && !tc_supported(1, m)) k = MP_KERNEL_PLAIN;
+    if (k == MP_KERNEL_TC_BF16 && !tc_supported(2, m)) k = MP_KERNEL_PLAIN;
     return k;
 }
 
@@ -1165,7 +1171,7 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
         cfg = *cfg_in;
     else
         mp_config_default(&cfg);
-    if (cfg.kernel < MP_KERNEL_AUTO || cfg.kernel > MP_KERNEL_TC_TF32) return fail(MP_E_ARG, "unknown kernel");
+    if (cfg.kernel < MP_KERNEL_AUTO || cfg.kernel > MP_KERNEL_TC_BF16) return fail(MP_E_ARG, "unknown kernel");
     if (cfg.max_inflight <= 0) cfg.max_inflight = 8;
     if (cfg.max_batch <= 0) cfg.max_batch = 64;
     if (cfg.max_pending <= 0) cfg.max_pending = 1 << 16;
@@ -1231,7 +1237,7 @@ int mp_set_kernel(mp_ctx *ctx, int32_t kernel)
 {
     g_err.clear();
     if (!ctx) return fail(MP_E_ARG, "null ctx");
-    if (kernel < MP_KERNEL_AUTO || kernel > MP_KERNEL_TC_TF32) return fail(MP_E_ARG, "unknown kernel %d", kernel);
+    if (kernel < MP_KERNEL_AUTO || kernel > MP_KERNEL_TC_BF16) return fail(MP_E_ARG, "unknown kernel %d", kernel);
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->kernel = kernel;
     return MP_OK;
@@ -1658,6 +1664,34 @@ extern "C" int mp_stream_append(mp_stream *st, const void *samples, int64_t n_ne
     return MP_OK;
 }
 
+extern "C" int mp_stream_submit(mp_stream *st, const void *samples, int64_t n_new, double *out_dist,
+                                int64_t *out_idx, uint64_t *ticket, int64_t *n_out, int64_t *first_window)
+{
+    g_err.clear();
+    if (!st || !n_out || !ticket || n_new < 0 || (n_new > 0 && (!samples || !out_dist || !out_idx)))
+        return fail(MP_E_ARG, "bad argument");
+    const size_t es = dtype_size(st->dtype);
+    const int64_t kept = (int64_t)(st->tail.size() / es);
+    const int64_t n = kept + n_new;
+    *n_out = 0;
+    *ticket = 0;
+    const int64_t first = std::max<int64_t>(0, st->n_seen - st->m + 1);
+    std::vector<unsigned char> buf(st->tail);
+    buf.insert(buf.end(), (const unsigned char *)samples, (const unsigned char *)samples + (size_t)n_new * es);
+    if (n >= st->m) {
+        // a serving request of [kept | new]: batched with the stream's other
+        // appends and any other requests; the query is copied at submission
+        int rc = mp_submit(st->ctx, st->dict, buf.data(), st->dtype, n, st->m, out_dist, out_idx, ticket);
+        if (rc) return rc;
+        *n_out = n - st->m + 1;
+    }
+    if (first_window) *first_window = first;
+    const int64_t keep = std::min<int64_t>(n, st->m - 1);
+    st->tail.assign(buf.end() - (ptrdiff_t)(keep * (int64_t)es), buf.end());
+    st->n_seen += n_new;
+    return MP_OK;
+}
+
 extern "C" int mp_stream_close(mp_stream *st)
 {
     g_err.clear();
@@ -1916,7 +1950,7 @@ static void tune_load(mp_ctx *ctx, const char *path)
         TuneVal v;
         if (sscanf(line, "{\"dtype\": %d, \"m\": %d, \"wlog\": %d, \"qlog\": %d, \"kernel\": %d, \"groups\": %d, \"ms\": %lf",
                    &k.dtype, &k.m, &k.wlog, &k.qlog, &v.kernel, &v.groups, &v.ms) == 7 &&
-            v.kernel >= MP_KERNEL_PLAIN && v.kernel <= MP_KERNEL_TC_TF32 && v.groups >= 1)
+            v.kernel >= MP_KERNEL_PLAIN && v.kernel <= MP_KERNEL_TC_BF16 && v.groups >= 1)
             ctx->tune[k] = v;  // a later line overrides an earlier one
     }
     fclose(f);

@@ -4,9 +4,10 @@
 // population standard deviation. They are kept in FP64 because sums of
 // squares cancel badly in FP32 when a series carries a large offset (random
 // walks). Each CTA handles a tile of consecutive windows:
-//   1. the tile's samples are staged in shared memory with coalesced 16-byte
-//      vector loads, then shifted by the tile's first sample (the statistics
-//      are shift invariant, and the shift keeps the prefix sums small);
+//   1. the tile's samples are read with coalesced 16-byte vector loads,
+//      shifted by the tile's first sample (the statistics are shift
+//      invariant, and the shift keeps the prefix sums small) and staged in
+//      shared memory;
 //   2. a block-wide prefix sum gives, for every window, sum(y) and sum(y^2)
 //      over its m samples in O(1);
 //   3. an integer prefix count of neighbouring samples that differ gives the
@@ -109,19 +110,20 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
     __shared__ int warp_tot_i[kStatsThreads / 32];
     __shared__ double tot;
 
-    // 1. The tile's raw samples, staged with 16-byte vector loads (the
-    //    ragged ends, samples outside [0, n) and unaligned series take scalar
-    //    loads), in the space of the y^2 prefix, which is written only later.
-    T *xs = reinterpret_cast<T *>(p2);
+    // The tile's samples, read with 16-byte vector loads (the ragged ends,
+    // samples outside [0, n) and unaligned series take scalar loads): each
+    // thread shifts its samples and compares each with the next (the next
+    // vector's first sample is one more, cached, load).
     constexpr int V = 16 / sizeof(T);
     using VecT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const double shift = (double)x[w0];
     const int64_t base = w0 - 1;  // sample of e = 0
     const bool vec_ok = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
     const int64_t a0 = (base >= 0 ? base : base - (V - 1)) / V * V;  // base rounded down to a vector
     const int nvec = (int)((base + E - a0 + V - 1) / V);
     for (int v = threadIdx.x; v < nvec; v += kStatsThreads) {
         const int64_t g = a0 + (int64_t)v * V;
-        T vals[V];
+        T vals[V + 1];
         if (vec_ok && g >= 0 && g + V <= n) {
             const VecT u = *reinterpret_cast<const VecT *>(x + g);
             memcpy(vals, &u, sizeof u);
@@ -129,22 +131,17 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
 #pragma unroll
             for (int k = 0; k < V; ++k) vals[k] = (g + k >= 0 && g + k < n) ? x[g + k] : T(0);
         }
+        vals[V] = (g + V >= 0 && g + V < n) ? x[g + V] : T(0);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            const int64_t e = g + k - base;
-            if (e >= 0 && e < E) xs[e] = vals[k];
+            const int64_t e = g + k - base, j = g + k;
+            if (e >= 0 && e < E) {
+                ys[e] = (j >= 0 && j < n) ? (double)vals[k] - shift : 0.0;
+                pc[e] = (e + 1 < E && j >= 0 && j + 1 < n && vals[k] != vals[k + 1]) ? 1 : 0;
+            }
         }
     }
     __syncthreads();
-    // 2. Shifted samples (FP64) and the "differs from the next sample" bits.
-    const double shift = (double)xs[1];  // x[w0]
-    for (int e = threadIdx.x; e < E; e += kStatsThreads) {
-        const int64_t j = base + e;
-        const T xv = xs[e];
-        ys[e] = (j >= 0 && j < n) ? (double)xv - shift : 0.0;
-        pc[e] = (e + 1 < E && j >= 0 && j + 1 < n && xv != xs[e + 1]) ? 1 : 0;
-    }
-    __syncthreads();  // the raw samples are no longer read
 
     // Each thread owns a contiguous chunk of the E samples.
     const int per = (E + kStatsThreads - 1) / kStatsThreads;

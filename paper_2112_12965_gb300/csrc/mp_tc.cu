@@ -145,14 +145,14 @@ __device__ __forceinline__ uint32_t instr_desc(int n)
 {
     // D = F32 (bits 4-5), A/B format (bits 7-9, 10-12): BF16 = 1, TF32 = 2;
     // both K-major; N >> 3 at bits 17-22; M >> 4 at bits 24-28 (M = 128).
-    const uint32_t fmt = VARIANT == 0 ? 1u : 2u;
+    const uint32_t fmt = (VARIANT == 0 || VARIANT == 3) ? 1u : 2u;
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 template <int VARIANT>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
-    if (VARIANT == 0)
+    if (VARIANT == 0 || VARIANT == 3)
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -195,7 +195,8 @@ __device__ __forceinline__ float to_tf32(float x)
 }
 
 // Write one 16-byte chunk (EPC values) of an operand row: BF16 hi and lo
-// halves (VARIANT 0), TF32 values (1), or TF32 hi and lo halves (2).
+// halves (VARIANT 0), TF32 values (1), TF32 hi and lo halves (2), or BF16
+// values (3).
 template <int VARIANT>
 __device__ __forceinline__ void put_chunk(const float *x, unsigned char *hi, unsigned char *lo, uint32_t off)
 {
@@ -214,6 +215,14 @@ __device__ __forceinline__ void put_chunk(const float *x, unsigned char *hi, uns
         *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
     } else if (VARIANT == 1) {
         *reinterpret_cast<float4 *>(hi + off) = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+    } else if (VARIANT == 3) {
+        uint32_t h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+            h[e] = *reinterpret_cast<const uint32_t *>(&hh);
+        }
+        *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
     } else {
         // TF32 hi and lo halves (x - hi is exact in FP32)
         float h[4], l[4];
@@ -237,7 +246,7 @@ template <int VARIANT>
 __device__ __forceinline__ void build_hankel(const float *raw, int rows, unsigned char *hi, unsigned char *lo, int t,
                                              int nthr)
 {
-    constexpr int EPC = VARIANT == 0 ? 8 : 4;  // values per 16-byte chunk
+    constexpr int EPC = (VARIANT == 0 || VARIANT == 3) ? 8 : 4;  // values per 16-byte chunk
     const int c = t & 7, groups = nthr >> 3, rg = t >> 3;
     const int rpg = (rows + groups - 1) / groups;
     const int r0 = rg * rpg, r1 = min(rows, r0 + rpg);
@@ -331,9 +340,11 @@ constexpr uint32_t kTmemCols = 2 * kTcMaxN;  // two accumulators of 256 FP32 col
 template <int VARIANT>
 __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
 {
-    constexpr int EPR = VARIANT == 0 ? 64 : 32;   // K values per 128-byte row (one K-block)
-    constexpr int KSTEP = VARIANT == 0 ? 16 : 8;  // K values per MMA
-    constexpr int NHL = VARIANT == 0 ? 2 : 1;     // hi/lo buffers
+    // VARIANT 0: split BF16 (3 products), 1: TF32, 3: single BF16 product
+    constexpr bool kBF = VARIANT == 0 || VARIANT == 3;
+    constexpr int EPR = kBF ? 64 : 32;       // K values per 128-byte row (one K-block)
+    constexpr int KSTEP = kBF ? 16 : 8;      // K values per MMA
+    constexpr int NHL = VARIANT == 0 ? 2 : 1;  // hi/lo buffers
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
@@ -905,7 +916,7 @@ double plan_clocks(const TcPlan &P, int m)
     const double reads = ksteps * P.nprod * (128.0 + P.nmax) * 32.0;
     const int groups = (P.nkb + P.qg - 1) / P.qg;
     const double writes = (double)groups * P.rb_rows * 128.0 * P.nhl;
-    const double build = (double)groups * P.rb_rows * 8.0 / kBuildThreads * (P.variant == 0 ? 16.0 : 10.0);
+    const double build = (double)groups * P.rb_rows * 8.0 / kBuildThreads * (P.variant == 1 ? 10.0 : 16.0);
     const double smem = (reads + writes) / 128.0;
     return std::max(mma, smem) + (P.n_stages == 1 ? build : 0.0);
 }
@@ -915,8 +926,8 @@ bool make_plan(int variant, int m, TcPlan *out)
     TcPlan P;
     P.variant = variant;
     P.m = m;
-    P.epr = variant == 0 ? 64 : 32;
-    P.kstep = variant == 0 ? 16 : 8;
+    P.epr = variant == 1 ? 32 : 64;
+    P.kstep = variant == 1 ? 8 : 16;
     P.nhl = variant == 0 ? 2 : 1;
     P.nprod = variant == 0 ? 3 : 1;
     if (m < P.kstep || m % P.kstep != 0) return false;
@@ -1113,7 +1124,9 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
         if (!pack_colfactor(use, ms_b, rs_b, st)) return fail(MP_E_CUDA, "tensor-core column factor");
         // the products' error bound: one product's rounding plus the FP32 sum's
         near->fb = use->fb;
-        near->u = variant == 1 ? kTcUnitTF32 + (float)m * 0x1p-23f : kTcUnitBF16X3 + 3.f * (float)m * 0x1p-23f;
+        near->u = variant == 1   ? kTcUnitTF32 + (float)m * 0x1p-23f
+                  : variant == 2 ? kTcUnitBF16 + (float)m * 0x1p-23f
+                                 : kTcUnitBF16X3 + 3.f * (float)m * 0x1p-23f;
     }
     TcArgs A;
     A.a = a;
@@ -1151,8 +1164,10 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     };
     if (variant == 0)
         launch(k_tc<0>);
-    else
+    else if (variant == 1)
         launch(k_tc<1>);
+    else
+        launch(k_tc<3>);
     if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core kernel launch: %s", cudaGetErrorString(e));
     *n_groups_out = ng;
     // the column groups' chunks, for the finalisation of overflowed records

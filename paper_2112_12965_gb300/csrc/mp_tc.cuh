@@ -10,9 +10,10 @@ namespace mpd {
 
 typedef int (*fail_fn)(int, const char *, ...);
 
-// Whether the tensor-core kernel handles window length m (variant 0: split
-// BF16, m a multiple of 16, up to about 600; variant 1: TF32, m a multiple of
-// 8, up to about 1100 -- the query operand of all m stays in shared memory).
+// Whether the tensor-core kernel handles window length m (variants 0: split
+// BF16 and 2: single BF16, m a multiple of 16, up to about 600 and 1100;
+// variant 1: TF32, m a multiple of 8, up to about 1100 -- the query operand
+// of all m stays in shared memory).
 bool tc_supported(int variant, int m);
 // Upper bound of the column groups tc_join uses for nq query windows.
 int tc_groups_bound(int sm_count, int64_t nq);
@@ -26,7 +27,8 @@ void tc_free_pack(void *pack);
 // the call sets near->fb and near->u, the width's terms) and
 // *n_groups_out; *cspans_out / *cgroup_start_out receive the column groups'
 // chunk layout (valid until the dictionary is freed). *err is set to 1 on a
-// device-side timeout. variant: 0 = split BF16 (3 products), 1 = TF32.
+// device-side timeout. variant: 0 = split BF16 (3 products), 1 = TF32, 2 = one
+// BF16 product.
 // The caller sizes part and near for tc_groups_bound groups. wait_cycles
 // bounds the kernel's waits of one role on another (<= 0: about 2 s); the
 // final wait for the MMAs before the TMEM is freed keeps its own bound.

@@ -117,6 +117,40 @@ def test_correlation_output_matches_oracle(mp):
         mp.mp_shutdown(ctx)
 
 
+def test_stream_submit_equals_one_shot_join(mp):
+    """Appends without waiting (each one a serving request, batched with the others) give the one-shot join."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        m = 128
+        train = synthetic.ecg_like(1 << 15, 73).astype(np.float32)
+        db, offs = synthetic.cut_dictionary(train, 16, 700)
+        d = mp.mp_dict_load(ctx, db, offs, [m])
+        x = synthetic.ecg_like(30000, 74, n_malformed=4).astype(np.float32)
+        full_d, full_i = mp.mp_ab_join(ctx, d, x, m)
+        st = mp.mp_stream_open(ctx, d, mp.MP_F32, m)
+        cuts = [0, 100, 127, 1024, 2048, 3000, 4096, 9000, 20000, 29000, 30000]
+        pieces = []
+        for a, c in zip(cuts[:-1], cuts[1:]):
+            od, oi = np.full(c - a, np.nan), np.full(c - a, -7, dtype=np.int64)
+            t, k, first = mp.mp_stream_submit(st, x[a:c], od, oi)
+            assert k == max(0, c - m + 1) - max(0, a - m + 1) and (t != 0) == (k > 0)
+            pieces.append((t, od, oi, k, first))
+        for t, *_ in pieces:
+            if t:
+                while mp.mp_poll(ctx, t)[0] == mp.MP_PENDING:
+                    pass
+        mp.mp_stream_close(st)
+        got_d = np.concatenate([od[:k] for _, od, _, k, _ in pieces])
+        got_i = np.concatenate([oi[:k] for _, _, oi, k, _ in pieces])
+        assert [f for t, *_, f in pieces if t][0] == 0 and len(got_d) == len(full_d)
+        np.testing.assert_allclose(got_d, full_d, rtol=0, atol=1e-4)
+        diff = got_i != full_i  # a different pick only between windows the re-scoring cannot tell apart
+        assert diff.mean() < 1e-3 and np.all(np.abs(got_d[diff] - full_d[diff]) <= 1e-4)
+        mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)
+
+
 def test_streaming_join_equals_one_shot_join(mp):
     """Appending a series in uneven pieces joins every window once, as the one-shot join does."""
     ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)

@@ -383,7 +383,7 @@ def test_near_tie_records_overflow_rescans_the_group(mp):
 
 @pytest.mark.parametrize("kernel", ["MP_KERNEL_TC_BF16X3", "MP_KERNEL_TC_TF32"])
 def test_near_copies_tensor_core_forms(mp, kernel):
-    """The same seven near-tied copies through the tensor-core forms: their records (32 slots) hold every
+    """The same seven near-tied copies through the tensor-core forms: their records (63 slots) hold every
     copy, and each row matches the oracle within the tensor-core tolerance."""
     q, b, offs, m = _near_copies_case()
     ctx = mp.mp_init(device=0, kernel=getattr(mp, kernel))

@@ -1,13 +1,13 @@
-"""Tensor-core join (tcgen05, TF32 and split BF16) against the CPU oracle (needs a GB300).
+"""Tensor-core join (tcgen05: split BF16, TF32, single BF16) against the CPU oracle (needs a GB300).
 
 Tolerance of both forms (the tensor-core contract): distances within 1e-3
 absolute, indices exact where the oracle's best and second-best distances
 differ by more than 1e-3. The finalisation recomputes the chosen pair's
 distance exactly, and the kernels record every chunk whose approximate score
 lies within twice the products' error bound of the best (TF32: 11-bit
-operands; split BF16: 3 * 2^-18; plus the FP32 sum), which the finalisation
-re-scores exactly. So the pick does not depend on the products' rounding,
-for either form and any window length.
+operands; split BF16: 3 * 2^-18; single BF16: 8-bit operands; plus the FP32
+sum), which the finalisation re-scores exactly. So the pick does not depend
+on the products' rounding, for any form and window length.
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ import synthetic
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = {"bf16x3": 2, "tf32": 3}
+VARIANTS = {"bf16x3": 2, "tf32": 3, "bf16": 4}
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +56,9 @@ def test_tc_tiny(mp, ctxs, variant):
 SHAPES = [("bf16x3", 16), ("bf16x3", 48), ("bf16x3", 128), ("bf16x3", 256),
           # short windows whose spread is near the noise floor: the operands'
           # shifts multiply the TF32 rounding, and the width grows with them
-          ("tf32", 16), ("tf32", 48), ("tf32", 128), ("tf32", 256)]
+          ("tf32", 16), ("tf32", 48), ("tf32", 128), ("tf32", 256),
+          # one BF16 product: 8-bit operands, a wide width, many chunks re-scored
+          ("bf16", 16), ("bf16", 128), ("bf16", 256)]
 
 
 @pytest.mark.parametrize("variant,m", SHAPES)
@@ -78,7 +80,7 @@ def test_tc_ecg_m256_all_rows(mp, ctxs, variant):
 
 def test_tc_transport_m512_sampled(mp, ctxs):
     w = synthetic.workload("transport_4m_m512", scale=1 / 16)
-    for variant in ("tf32", "bf16x3"):
+    for variant in ("tf32", "bf16x3", "bf16"):
         dist, idx = join(mp, ctxs[variant], w.query, w.dict_samples, w.offsets, w.m)
         rows = np.random.default_rng(3).choice(len(dist), 128, replace=False)
         check(variant, dist, idx, w.query, w.dict_samples, w.offsets, w.m, rows=rows)
@@ -89,7 +91,7 @@ def test_tc_matches_plain_on_random_walk_offsets(mp, ctxs):
     q = (synthetic.random_walk(5000, 31) + 3000.0).astype(np.float32)
     b = (synthetic.random_walk(6000, 32) - 2000.0).astype(np.float32)
     offs = np.array([0, 2500, 6000])
-    for variant in ("tf32", "bf16x3"):
+    for variant in ("tf32", "bf16x3", "bf16"):
         dist, idx = join(mp, ctxs[variant], q, b, offs, 128)
         check(variant, dist, idx, q, b, offs, 128, rows=np.arange(0, len(q) - 127, 7))
 
