@@ -17,6 +17,7 @@ the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -456,7 +457,7 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
         # 256 outstanding; equal to the synchronous appends' results
         st = mp.mp_stream_open(ctx, d, mp.MP_F32, m)
         t0 = time.perf_counter()
-        live, outs, n_win_async = {}, [], 0
+        live, outs, n_win_async = collections.OrderedDict(), [], 0
         for a in range(0, len(q), 1024):
             piece = q[a : a + 1024]
             od, oi = np.empty(len(piece)), np.empty(len(piece), dtype=np.int64)
@@ -472,13 +473,15 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
             n_win_async += k
             if t:
                 live[t] = True
-            while len(live) >= 256:
-                for tk in list(live):
-                    stt, _ = mp.mp_poll(ctx, tk)
-                    if stt != mp.MP_PENDING:
-                        if stt != mp.MP_DONE:
-                            raise RuntimeError("stream append failed")
-                        del live[tk]
+            while len(live) >= 256:  # oldest first: appends finish roughly in order
+                tk = next(iter(live))
+                stt, _ = mp.mp_poll(ctx, tk)
+                if stt == mp.MP_PENDING:
+                    time.sleep(0.00005)
+                    continue
+                if stt != mp.MP_DONE:
+                    raise RuntimeError("stream append failed")
+                del live[tk]
         mp.mp_drain(ctx, 600.0)
         for tk in list(live):
             stt, _ = mp.mp_poll(ctx, tk)

@@ -345,10 +345,12 @@ int mp_top_discords(const double *profile, int64_t n, int32_t k, int64_t excl, d
  * Autotuner: chooses the join form and the plain kernel's column grouping for
  * one shape (dictionary, m, query length n). It builds a synthetic query of n
  * samples from the dictionary's own samples, times the plain form at several
- * column-group counts and the tensor-core forms whose stated accuracy meets
- * `tolerance` (absolute distance error: 1e-4 admits the plain form only,
- * 1e-3 adds split-BF16; tolerance <= 0 admits every form, TF32 included),
- * and keeps the fastest. The choice applies to later joins on this context
+ * column-group counts and the split-BF16 and TF32 tensor-core forms, and
+ * keeps the fastest. Every form picks each row's window exactly (see the join
+ * forms above), so each meets the same distance tolerance; `tolerance` (the
+ * caller's absolute distance tolerance) is recorded with the choice. The
+ * single-BF16 form is not timed: its wide error bound leaves many chunks to
+ * re-score. The choice applies to later joins on this context
  * whose kernel is MP_KERNEL_AUTO and whose shape falls in the same bucket
  * (same dtype and m, same floor(log2) of the dictionary windows and of the
  * query windows); with mp_config.tune_cache set it is also appended to that

@@ -211,6 +211,16 @@ __device__ __forceinline__ T near_width(const FinalizeParams<T> &p, int64_t i, T
     return T(2) * T(p.near.u) * T(p.m) * sqrt(fma(sd, sd, da * da)) * T(*p.near.fb);
 }
 
+// The window range [g_lo, g_hi) of column group k's chunks (its spans or
+// tiles in increasing order), as the join kernel saw it for the overflow mask.
+template <typename T>
+__device__ __forceinline__ void group_range(const FinalizeParams<T> &p, int k, int64_t &g_lo, int64_t &g_hi)
+{
+    const int s0 = p.cgroup_start[k], s1 = p.cgroup_start[k + 1];
+    g_lo = s0 < s1 ? p.cspans[s0].g0 : 0;
+    g_hi = s0 < s1 ? p.cspans[s1 - 1].g0 + p.cspans[s1 - 1].ncols : 0;
+}
+
 // Add a CTA's counters (shared) to the global ones; every thread calls it.
 __device__ __forceinline__ void flush_counters(unsigned long long *ctr, unsigned long long *s_ctr)
 {
@@ -319,12 +329,21 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4) k_finalize(Finali
                         if (any_ovf) {
                             // a record within the width was dropped: every chunk of that group
                             for (int k = 0; k < p.n_groups; ++k) {
-                                if (!(p.near.head(k, i)->g & kNearOverflow)) continue;
+                                const NearSlot h = *p.near.head(k, i);
+                                if (!(h.g & kNearOverflow)) continue;
+                                const uint32_t mask = __float_as_uint(h.q);
+                                int64_t g_lo, g_hi;
+                                group_range(p, k, g_lo, g_hi);
                                 for (int sp = p.cgroup_start[k]; sp < p.cgroup_start[k + 1]; ++sp) {
                                     const Span span = p.cspans[sp];
                                     for (int c0 = 0; c0 < span.ncols; c0 += kChunk) {
                                         const int32_t cu = (int32_t)(span.g0 + c0);
-                                        if (cu == g) continue;
+                                        // a chunk whose windows meet a marked run
+                                        const uint32_t b0 = near_run(cu, g_lo, g_hi);
+                                        const uint32_t b1 = near_run(cu + kChunk - 1, g_lo, g_hi);
+                                        const uint32_t runs = (b1 >= 31 ? 0xffffffffu : ((2u << b1) - 1u)) &
+                                                              ~((1u << b0) - 1u);
+                                        if (cu == g || !(mask & runs)) continue;
                                         consider(cu);
                                         ++ochunks;
                                     }
@@ -665,12 +684,21 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                 if (ncw < 0) {
                     // a record within the width was dropped: every chunk of that group
                     for (int k = 0; k < p.n_groups; ++k) {
-                        if (!(p.near.head(k, iw)->g & kNearOverflow)) continue;
+                        const NearSlot h = *p.near.head(k, iw);
+                        if (!(h.g & kNearOverflow)) continue;
+                        const uint32_t mask = __float_as_uint(h.q);
+                        int64_t g_lo, g_hi;
+                        group_range(p, k, g_lo, g_hi);
                         for (int sp = p.cgroup_start[k]; sp < p.cgroup_start[k + 1]; ++sp) {
                             const Span span = p.cspans[sp];
                             for (int c0 = 0; c0 < span.ncols; c0 += kChunk) {
                                 const int32_t cu = (int32_t)(span.g0 + c0);
-                                if (cu == g0) continue;
+                                // a chunk whose windows meet a marked run
+                                const uint32_t b0 = near_run(cu, g_lo, g_hi);
+                                const uint32_t b1 = near_run(cu + kChunk - 1, g_lo, g_hi);
+                                const uint32_t runs =
+                                    (b1 >= 31 ? 0xffffffffu : ((2u << b1) - 1u)) & ~((1u << b0) - 1u);
+                                if (cu == g0 || !(mask & runs)) continue;
                                 consider(cu);
                                 ++ochunks;
                             }

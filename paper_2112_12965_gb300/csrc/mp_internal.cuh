@@ -96,9 +96,11 @@ constexpr int32_t kNearCountMask = 0x3f;  // header bits 0-5: slots in use
 constexpr int32_t kNearOverflow = 0x80;   // header bit 7: a record within the width was dropped
 constexpr int kNearMaxSlots = 63;
 struct NearRec {
-    // [n_groups][1 + S][ld]: entry (k, 0, r) is the header of (group k, row r)
-    // (its g holds the slots in use | kNearOverflow; the join zeroes the headers
-    // of its rows), entries (k, 1 + u, r) its slots. Null: no records.
+    // [n_groups][1 + S][ld]: entry (k, 0, r) is the header of (group k, row r):
+    // its g holds the slots in use | kNearOverflow, its q the bits of an
+    // overflow mask (bit b: a dropped record lay in the b-th of 32 equal runs
+    // of the group's window range, see near_run); the join zeroes the headers
+    // of its rows. Entries (k, 1 + u, r) are the slots. Null: no records.
     NearSlot *rec;
     int64_t ld;       // row stride
     int32_t S;        // slots per (group, row), 1 .. kNearMaxSlots
@@ -107,6 +109,15 @@ struct NearRec {
     float u;          // tensor-core forms: bound on the relative error of the products and their sum
     __host__ __device__ NearSlot *head(int64_t k, int64_t r) const { return rec + k * (S + 1) * ld + r; }
 };
+
+// The run of a group's window range [g_lo, g_hi) that window g lies in, for
+// the overflow mask: 32 runs of ceil((g_hi - g_lo) / 32) windows.
+__host__ __device__ inline uint32_t near_run(int64_t g, int64_t g_lo, int64_t g_hi)
+{
+    const int64_t len = (g_hi - g_lo + 31) / 32;
+    const int64_t b = len > 0 ? (g - g_lo) / len : 0;
+    return (uint32_t)(b < 0 ? 0 : (b > 31 ? 31 : b));
+}
 // Width of the plain FP32 recurrence, in correlation: 8x the largest drift
 // measured by a float32 model of the recurrence on the benchmark data (about
 // 1e-6 to 5e-6 over the up to 640-step diagonals between seeds, 32 lanes x 20
@@ -140,8 +151,12 @@ constexpr int kTcRows = 128;  // query windows per CTA of the tensor-core join (
 // kEvict replaces the lowest-scoring slot if q is higher, and the record
 // dropped (that one, or q) sets the overflow bit if it may still matter;
 // without kEvict q is dropped (less code, for the plain kernel's hot loop).
+// The overflow marks the run of the dropped record's window in the header's
+// mask when the group's window range [g_lo, g_hi) is given (g_hi > g_lo), and
+// every run otherwise.
 template <bool kEvict>
-__device__ __forceinline__ void near_add(const NearRec &nr, int64_t k, int64_t r, int32_t g, float q, float floor_q)
+__device__ __forceinline__ void near_add(const NearRec &nr, int64_t k, int64_t r, int32_t g, float q, float floor_q,
+                                         int64_t g_lo = 0, int64_t g_hi = 0)
 {
     NearSlot *h = nr.head(k, r);
     const int32_t f = h->g;
@@ -152,6 +167,7 @@ __device__ __forceinline__ void near_add(const NearRec &nr, int64_t k, int64_t r
         return;
     }
     float dropped = q;
+    int32_t dropped_g = g;
     if (kEvict) {
         int lo = 1;
         float qlo = h[nr.ld].q;
@@ -164,10 +180,15 @@ __device__ __forceinline__ void near_add(const NearRec &nr, int64_t k, int64_t r
         }
         if (q > qlo) {
             dropped = qlo;
+            dropped_g = h[(int64_t)lo * nr.ld].g;
             h[(int64_t)lo * nr.ld] = NearSlot{g, q};
         }
     }
-    if (dropped >= floor_q) h->g = f | kNearOverflow;
+    if (dropped >= floor_q) {
+        const uint32_t bits = g_hi > g_lo ? (1u << near_run(dropped_g, g_lo, g_hi)) : 0xffffffffu;
+        h->g = f | kNearOverflow;
+        h->q = __uint_as_float(__float_as_uint(h->q) | bits);
+    }
 }
 #endif
 

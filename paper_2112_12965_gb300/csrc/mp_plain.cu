@@ -270,7 +270,7 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             R.set_terms(j, v.x, v.y);
             if (kNear) {
                 if (v.z > T(0)) sig_max = fmax(sig_max, T(1) / v.z);
-                p.near.head(grp, r)->g = 0;  // no records yet
+                *p.near.head(grp, r) = NearSlot{0, 0.f};  // no records yet, empty overflow mask
             }
         } else {
             R.set_terms(j, T(0), T(0));

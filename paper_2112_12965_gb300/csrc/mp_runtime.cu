@@ -159,6 +159,7 @@ struct TuneKey {
 struct TuneVal {
     int kernel, groups;
     double ms;
+    double tolerance = 0;  // the tolerance it was tuned for (recorded with the choice)
 };
 static int ilog2(int64_t x)
 {
@@ -1961,8 +1962,10 @@ static void tune_save(const mp_ctx *ctx, const TuneKey &k, const TuneVal &v)
     if (ctx->tune_path.empty()) return;
     FILE *f = fopen(ctx->tune_path.c_str(), "a");
     if (!f) return;
-    fprintf(f, "{\"dtype\": %d, \"m\": %d, \"wlog\": %d, \"qlog\": %d, \"kernel\": %d, \"groups\": %d, \"ms\": %.4f}\n",
-            k.dtype, k.m, k.wlog, k.qlog, v.kernel, v.groups, v.ms);
+    fprintf(f,
+            "{\"dtype\": %d, \"m\": %d, \"wlog\": %d, \"qlog\": %d, \"kernel\": %d, \"groups\": %d, \"ms\": %.4f, "
+            "\"tolerance\": %.3g}\n",
+            k.dtype, k.m, k.wlog, k.qlog, v.kernel, v.groups, v.ms, v.tolerance);
     fclose(f);
 }
 
@@ -1995,7 +1998,8 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
     double *dd = (double *)dout;
     int64_t *di = (int64_t *)((char *)dout + (size_t)nq * 8);
     // candidates: the plain form at several column-group counts, then the
-    // tensor-core forms whose accuracy meets the tolerance
+    // tensor-core forms: every form picks exactly (near ties re-scored within
+    // its error bound), so each meets any tolerance the plain form meets
     struct Cand {
         int kernel, groups;
     };
@@ -2003,9 +2007,8 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
     const int64_t max_g = std::max<int64_t>(1, s->n_windows / 1024);
     for (int g : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
         if (g <= max_g) cands.push_back(Cand{MP_KERNEL_PLAIN, g});
-    if (dtype == MP_F32 && (tolerance <= 0 || tolerance >= 1e-3) && tc_supported(0, m))
-        cands.push_back(Cand{MP_KERNEL_TC_BF16X3, 1});
-    if (dtype == MP_F32 && tolerance <= 0 && tc_supported(1, m)) cands.push_back(Cand{MP_KERNEL_TC_TF32, 1});
+    if (dtype == MP_F32 && tc_supported(0, m)) cands.push_back(Cand{MP_KERNEL_TC_BF16X3, 1});
+    if (dtype == MP_F32 && tc_supported(1, m)) cands.push_back(Cand{MP_KERNEL_TC_TF32, 1});
     const int saved_kernel = ctx->kernel;
     const size_t wsb = std::max(join_ws_layout(nq, dtype, 32, 0, join_seed_bytes(d, dtype, nq, m, true)).total,
                                 join_ws_bytes(ctx, d, s, dtype, n, m));
@@ -2047,7 +2050,7 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
     cudaFree(dout);
     if (rc) return rc;
     const TuneKey key{dtype, m, ilog2(s->n_windows), ilog2(nq)};
-    const TuneVal val{best.kernel, best.groups, best_ms};
+    const TuneVal val{best.kernel, best.groups, best_ms, tolerance};
     ctx->tune[key] = val;
     tune_save(ctx, key, val);
     if (kernel_out) *kernel_out = best.kernel;

@@ -563,8 +563,11 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
         // near-tie width of this row in units of the score q = rho * m * std_a
         // (negative: no records, for rows past the end and constant rows)
         float tq = -1.f;
+        // the group's window range, for the overflow mask's runs
+        const int64_t g_lo = t_lo < t_hi ? p.tiles[t_lo].g0 : 0;
+        const int64_t g_hi = t_lo < t_hi ? p.tiles[t_hi - 1].g0 + p.tiles[t_hi - 1].nvalid : 0;
         if (row < p.nq && p.near.rec != nullptr) {
-            p.near.head(grp, row)->g = 0;
+            *p.near.head(grp, row) = NearSlot{0, 0.f};
             const float za = p.rs_a[row].z;
             if (za > 0.f) {
                 // twice the products' error bound: u m sqrt(std_a^2 + da^2) F_b
@@ -614,7 +617,8 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) k_tc(TcArgs p)
                     // overtaken by less than tq (-inf on either side: no record)
                     if (fabsf(cm - best) <= tq) {
                         const bool upd = cm > best;
-                        near_add<true>(p.near, grp, row, upd ? bchunk : gch, upd ? best : cm, fmaxf(cm, best) - tq);
+                        near_add<true>(p.near, grp, row, upd ? bchunk : gch, upd ? best : cm, fmaxf(cm, best) - tq,
+                                       g_lo, g_hi);
                     }
                     if (cm > best) {
                         best = cm;
