@@ -210,13 +210,15 @@ struct PlainLaunch {
 // seed_top (may be null): the centred covariances of each warp's first query
 // window, row r / (32 * rows per lane) at column g, row stride seed_ld (as
 // written by tc_seeds); null makes the kernel compute them itself.
-// near (near.rec may be null; FP32 only): near-tie records of every query
-// window; near.ld must equal the partial results' row stride.
+// left (null exactly when seed_top is): the left seeds of every span s and
+// query window r of the launch at left[s * left_ld + r] (as written by
+// tc_left_seeds). near (near.rec may be null; FP32 only): near-tie records of
+// every query window; near.ld must equal the partial results' row stride.
 template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
-                         const NearRec &near, cudaStream_t st);
+                         const T *left, int64_t left_ld, const NearRec &near, cudaStream_t st);
 template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
 template <typename T> size_t plain_smem_bytes(int warps, int m, int rows_per_lane = plain_rows_per_lane<T>());
 // Resident CTAs per SM of the plain kernel for this shape (occupancy API).
@@ -241,6 +243,8 @@ struct PlainRequest {
     Partial<float> *part;
     const float *seed_top;  // always null: batched work computes its own seeds
     int64_t seed_ld;
+    const float *left;      // always null
+    int64_t left_ld;
     NearRec near;           // near-tie records (required), ld = nq
     int64_t ld_part;        // nq
     int64_t row0;           // 0

@@ -26,7 +26,8 @@
 // seeds from the tensor-core kernel K2s (a dense product, computed once per
 // join); the other forms compute them here as direct dot products per column
 // block. At the first column of each span (a run of columns inside one
-// segment) every row gets a "left seed", a direct dot product. Dictionary
+// segment) every row gets a "left seed": from the tensor-core kernel K2l for
+// FP32 joins, else a direct dot product. Dictionary
 // windows never cross a segment (Def. 8) because spans never do. Each lane
 // keeps, for its rows, the running maximum of q per 16-column chunk and the
 // chunk that raised it (plus near-tie records); the partial result per (row,
@@ -61,6 +62,8 @@ template <typename T> struct PlainParams {
     Partial<T> *part;
     const T *seed_top;  // top seeds from the tensor cores, or null
     int64_t seed_ld;
+    const T *left;      // left seeds from the tensor cores, [span][left_ld] (with seed_top), or null
+    int64_t left_ld;
     NearRec near;       // near-tie records (near.ld = ld_part), or near.rec null
     int64_t ld_part;    // row stride of part and near (>= nq)
     int64_t row0;       // self-join: position in the series of query window 0
@@ -367,7 +370,13 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
             }
 
             // ---- left seeds at the first column of the span ----
-            if (cb == 0) {
+            if (kSeeds && cb == 0) {
+                // from the tensor cores: the centred covariances of the lane's
+                // rows with the span's first window
+                const T *lp = p.left + (int64_t)s * p.left_ld + r0;
+#pragma unroll
+                for (int j = 0; j < kRows; ++j) R.set(j, r0 + j < p.nq ? lp[j] : T(0));
+            } else if (cb == 0) {
                 T acc[kRows];
 #pragma unroll
                 for (int j = 0; j < kRows; ++j) acc[j] = T(0);
@@ -577,7 +586,7 @@ template <typename T>
 cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec4_t<T> *rs_a, const Split<T> *ms_a,
                          const T *b, int64_t nb, const vec4_t<T> *rs_b, const Split<T> *ms_b, const Span *spans,
                          const int32_t *group_start, Partial<T> *part, const T *seed_top, int64_t seed_ld,
-                         const NearRec &near, cudaStream_t st)
+                         const T *left, int64_t left_ld, const NearRec &near, cudaStream_t st)
 {
     PlainParams<T> p{};
     p.a = a;
@@ -596,6 +605,8 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     p.part = part;
     p.seed_top = seed_top;
     p.seed_ld = seed_ld;
+    p.left = left;
+    p.left_ld = left_ld;
     p.near = near;
     p.ld_part = L.ld_part > 0 ? L.ld_part : L.nq;
     p.row0 = L.row0;
@@ -611,11 +622,12 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     };
     if constexpr (sizeof(T) == 8) {
         // FP64 data: seeds from direct dot products, no near-tie records
-        if (seed_top != nullptr || near.rec != nullptr || L.excl > 0) return cudaErrorInvalidValue;
+        if (seed_top != nullptr || left != nullptr || near.rec != nullptr || L.excl > 0) return cudaErrorInvalidValue;
         return launch(k_plain<T, R, false, false>);
     } else {
         if (near.rec != nullptr && (near.ld != p.ld_part || near.S < 1 || near.S > kNearMaxSlots))
             return cudaErrorInvalidValue;
+        if ((seed_top == nullptr) != (left == nullptr)) return cudaErrorInvalidValue;  // both seeds, or neither
         if (L.excl > 0) {
             // self-join (dictionary learning): tensor-core seeds and near-tie records
             if (seed_top == nullptr || near.rec == nullptr) return cudaErrorInvalidValue;
@@ -665,10 +677,12 @@ template size_t plain_smem_bytes<double>(int, int, int);
 template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,
                                          const Split<float> *, const float *, int64_t, const float4 *,
                                          const Split<float> *, const Span *, const int32_t *, Partial<float> *,
-                                         const float *, int64_t, const NearRec &, cudaStream_t);
+                                         const float *, int64_t, const float *, int64_t, const NearRec &,
+                                         cudaStream_t);
 template cudaError_t launch_plain<double>(const PlainLaunch &, const double *, int64_t, const dvec4 *,
                                           const Split<double> *, const double *, int64_t, const dvec4 *,
                                           const Split<double> *, const Span *, const int32_t *, Partial<double> *,
-                                          const double *, int64_t, const NearRec &, cudaStream_t);
+                                          const double *, int64_t, const double *, int64_t, const NearRec &,
+                                          cudaStream_t);
 
 }  // namespace mpd

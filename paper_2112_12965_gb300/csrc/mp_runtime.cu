@@ -599,7 +599,7 @@ static int64_t plain_chunk_rows(const mp_dict *d, int32_t dtype, int64_t nq, int
 
 // Workspace layout of one join.
 struct JoinWs {
-    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_seed, total;
+    size_t off_err, off_mean, off_inv, off_cflag, off_rs, off_ms, off_part, off_near, off_seed, off_left, total;
     int near_slots;
 };
 
@@ -614,7 +614,7 @@ static int near_slots_for(int kernel) { return is_tc(kernel) ? kNearSlotsTC : kN
 
 // near_slots: record slots per (column group, query window) of FP32 joins.
 static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t extra_front, size_t seed_bytes = 0,
-                             int near_slots = kNearSlotsPlain)
+                             int near_slots = kNearSlotsPlain, size_t left_bytes = 0)
 {
     JoinWs w;
     // error word of the tensor-core kernels at the front
@@ -641,6 +641,9 @@ static JoinWs join_ws_layout(int64_t nq, int32_t dtype, int n_groups, size_t ext
     if (dtype == MP_F32) o = align_up(o + (size_t)n_groups * (w.near_slots + 1) * nq * sizeof(NearSlot), 256);
     w.off_seed = o;
     o = align_up(o + seed_bytes, 256);
+    // left seeds of the FP32 plain join (row chunk of the query windows)
+    w.off_left = o;
+    o = align_up(o + left_bytes, 256);
     w.total = o;
     return w;
 }
@@ -665,6 +668,23 @@ static size_t join_seed_bytes(const mp_dict *d, int32_t dtype, int64_t nq, int32
     return seed_geometry(nq, d->nb - m + 1).bytes;
 }
 
+// Spans get_grouping cuts the dictionary's windows into for n_groups column
+// groups (a segment contributes one span per group it meets).
+static int64_t grouping_spans(const DictStats *s, int n_groups)
+{
+    const int64_t target = (std::max<int64_t>(1, s->n_windows) + n_groups - 1) / n_groups;
+    int64_t n = 0, cum = 0;
+    for (const Span &seg : s->seg_spans) {
+        n += (cum + seg.ncols - 1) / target - cum / target + 1;
+        cum += seg.ncols;
+    }
+    return n;
+}
+
+// Row stride of the left seeds: the query windows of one row chunk, rounded up
+// to 4 (16-byte rows).
+static int64_t left_ld_for(int64_t crow) { return (crow + 3) & ~(int64_t)3; }
+
 // Geometry of the plain join of nq query windows (row chunks included).
 static Geometry join_plain_geometry(const mp_ctx *ctx, const mp_dict *d, const DictStats *s, int32_t dtype,
                                     int64_t nq, int32_t m, bool seeds)
@@ -679,9 +699,15 @@ static Geometry join_plain_geometry(const mp_ctx *ctx, const mp_dict *d, const D
 static JoinWs join_layout(const mp_ctx *ctx, const mp_dict *d, const DictStats *s, int32_t dtype, int64_t nq,
                           int32_t m, int kernel, bool seeds)
 {
-    const int groups = is_tc(kernel) ? tc_groups_bound(ctx->sm_count, nq)
-                                     : join_plain_geometry(ctx, d, s, dtype, nq, m, seeds).n_groups;
-    return join_ws_layout(nq, dtype, groups, 0, join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel));
+    if (is_tc(kernel))
+        return join_ws_layout(nq, dtype, tc_groups_bound(ctx->sm_count, nq), 0,
+                              join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel));
+    const int groups = join_plain_geometry(ctx, d, s, dtype, nq, m, seeds).n_groups;
+    size_t left = 0;
+    if (seeds && dtype == MP_F32)
+        left = (size_t)grouping_spans(s, groups) * left_ld_for(plain_chunk_rows(d, dtype, nq, m, seeds)) * 4;
+    return join_ws_layout(nq, dtype, groups, 0, join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel),
+                          left);
 }
 
 // The join on device buffers; `base` is a device workspace of at least
@@ -732,7 +758,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
             CUDA_TRY(launch_plain<double>(L, a, n, rs_a, ms_a, (const double *)d->d_samples, d->nb,
                                           (const dvec4 *)s->rs, (const Split<double> *)s->ms, gr->spans,
-                                          gr->group_start, part, nullptr, 0, NearRec{}, st));
+                                          gr->group_start, part, nullptr, 0, nullptr, 0, NearRec{}, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
@@ -778,9 +804,16 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         }
         Partial<float> *part = (Partial<float> *)(base + w.off_part);
         const NearRec near = near_rec(base, w, nq);
-        float *seed_top = nullptr;
+        float *seed_top = nullptr, *left = nullptr;
         const SeedGeo sg = seed_geometry(nq, d->nb - m + 1);
-        if (seeds) seed_top = (float *)(base + w.off_seed);
+        const int64_t left_ld = left_ld_for(crow);
+        if (seeds) {
+            seed_top = (float *)(base + w.off_seed);
+            left = (float *)(base + w.off_left);
+            if (gr->n_spans != grouping_spans(s, geo.n_groups))
+                return fail(MP_E_INTERNAL, "left-seed layout: %d spans, %lld expected", gr->n_spans,
+                            (long long)grouping_spans(s, geo.n_groups));
+        }
         // row chunks (one chunk unless the seed matrix would exceed its cap)
         for (int64_t r0 = 0; r0 < nq; r0 += crow) {
             const int64_t rows = std::min<int64_t>(crow, nq - r0);
@@ -789,6 +822,9 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
                 int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb, s->seg_spans.data(),
                                   (int32_t)s->seg_spans.size(), s->ms, a + r0, rows + m - 1, m, ms_a + r0,
                                   32 * kPlainRowsPerLane, seed_top, sg.ld, err, st, fail);
+                if (rc) return rc;
+                rc = tc_left_seeds(a + r0, rows + m - 1, m, ms_a + r0, (const float *)d->d_samples, d->nb, s->ms,
+                                   gr->spans, gr->n_spans, left, left_ld, err, st, fail);
                 if (rc) return rc;
             }
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
@@ -803,7 +839,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             nc.rec += r0;
             CUDA_TRY(launch_plain<float>(Lc, a + r0, rows + m - 1, rs_a + r0, ms_a + r0, (const float *)d->d_samples,
                                          d->nb, (const float4 *)s->rs, (const Split<float> *)s->ms, gr->spans,
-                                         gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0, nc, st));
+                                         gr->group_start, part + r0, seed_top, seeds ? sg.ld : 0, left,
+                                         seeds ? left_ld : 0, nc, st));
         }
         {
             PhaseTimer t(ctx, MP_PHASE_FINALIZE, st);
@@ -2010,8 +2047,17 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
     if (dtype == MP_F32 && tc_supported(0, m)) cands.push_back(Cand{MP_KERNEL_TC_BF16X3, 1});
     if (dtype == MP_F32 && tc_supported(1, m)) cands.push_back(Cand{MP_KERNEL_TC_TF32, 1});
     const int saved_kernel = ctx->kernel;
-    const size_t wsb = std::max(join_ws_layout(nq, dtype, 32, 0, join_seed_bytes(d, dtype, nq, m, true)).total,
-                                join_ws_bytes(ctx, d, s, dtype, n, m));
+    // the workspace of the largest candidate: each forced grouping with its left seeds, and every form
+    size_t wsb = join_ws_bytes(ctx, d, s, dtype, n, m);
+    for (const Cand &c : cands) {
+        if (c.kernel != MP_KERNEL_PLAIN) continue;
+        const size_t left = dtype == MP_F32 ? (size_t)grouping_spans(s, c.groups) *
+                                                  left_ld_for(plain_chunk_rows(d, dtype, nq, m, true)) * 4
+                                            : 0;
+        wsb = std::max(wsb, join_ws_layout(nq, dtype, c.groups, 0, join_seed_bytes(d, dtype, nq, m, true),
+                                           kNearSlotsPlain, left)
+                                .total);
+    }
     rc = ensure_ws(ctx, wsb);
     if (rc) {
         cudaFree(dq);
@@ -2245,7 +2291,8 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
         near.S = kNoAllocNearSlots;
         near.rho = kNearRhoFP32;
         CUDA_TRY(launch_plain<float>(L, a, n, rs_a, ms_a, (const float *)d->d_samples, d->nb, (const float4 *)s->rs,
-                                     (const Split<float> *)s->ms, d_spans, d_gstart, part, nullptr, 0, near, st));
+                                     (const Split<float> *)s->ms, d_spans, d_gstart, part, nullptr, 0, nullptr, 0,
+                                     near, st));
         n_groups = geo.n_groups;
     }
     // with no dictionary window (n_groups = 0, g_first = -1) this writes +inf / -1

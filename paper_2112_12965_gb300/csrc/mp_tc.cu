@@ -893,6 +893,170 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
 }
 
 // ---------------------------------------------------------------------------
+// K2l: the plain kernel's left seeds on the tensor cores
+// ---------------------------------------------------------------------------
+// Each span (a run of dictionary windows inside one segment) starts the plain
+// recurrence's diagonals from "left seeds": the centred covariance of every
+// query window r with the span's first window g_s,
+//     L[s, r] = sum_k (a[r + k] - mean_a[r]) * (b[g_s + k] - mean_b[g_s]).
+// For 128 consecutive query windows (the TMEM lanes) and up to 256 spans this
+// is a dense product with K = m. Per K-block (32 values of k) the query
+// windows form a row-shifted Hankel operand of the block's samples (shifted
+// by its first window's mean, hi part) and the spans' first windows a
+// gathered K-major operand (each centred on its own mean's hi part, zero past
+// m). The products are TF32 hi/lo as in K2s, so a left seed carries about
+// FP32's error. The epilogue removes the shifts and stores L[s][r]: for one
+// span, consecutive threads hold consecutive query windows, so the stores are
+// coalesced as they come.
+struct LeftArgs {
+    const float *a;
+    int64_t nq;
+    int32_t m;
+    const Split<float> *ms_a;
+    const float *b;
+    int64_t nb;
+    const Split<float> *ms_b;
+    const Span *spans;
+    int32_t n_spans;
+    float *left;  // [n_spans][ld]
+    int64_t ld;
+    int32_t *err;
+};
+
+constexpr int kLeftThreads = 256;
+constexpr int kLeftRows = 128;
+constexpr int kLeftSpans = 256;                                     // spans per CTA (TMEM columns)
+constexpr int kLeftRaw = kLeftRows + kSeedEpr;                      // query samples of one K-block
+constexpr int kLeftGather = kLeftSpans * 8 / kLeftThreads;          // 16-byte B chunks per thread
+static_assert(kLeftRaw <= 2 * kLeftThreads, "two query samples per thread at most");
+
+size_t left_smem_bytes()
+{
+    // 1024-byte alignment slack, query operand (hi, lo), span operand (hi, lo),
+    // staged query samples, column terms, barrier and TMEM slot
+    return 1024 + 2 * (size_t)kLeftRows * 128 + 2 * (size_t)kLeftSpans * 128 + (kLeftRaw + 8) * 4 +
+           kLeftSpans * 4 + 16;
+}
+
+__global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *a_hi = base, *a_lo = base + kLeftRows * 128;
+    unsigned char *b_hi = base + 2 * kLeftRows * 128, *b_lo = b_hi + kLeftSpans * 128;
+    float *raw = reinterpret_cast<float *>(b_lo + kLeftSpans * 128);
+    float *colp = raw + kLeftRaw + 8;  // m * (mean_b - s_b) = m * mean's lo part, per span
+    uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kLeftSpans);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t R0 = (int64_t)blockIdx.x * kLeftRows;  // first query window
+    const int s0 = blockIdx.y * kLeftSpans;               // first span
+    const int ns = min(kLeftSpans, p.n_spans - s0);
+    const int nmma = (ns + 15) & ~15;
+    const int m = p.m;
+    const int nkb = (m + kSeedEpr - 1) / kSeedEpr;
+
+    if (warp == 0) tmem_alloc(tmem_slot, kLeftSpans);
+    if (tid == 0) mbar_init(bar, 1);
+    // per span: its first window and mean (the column terms)
+    for (int n = tid; n < kLeftSpans; n += kLeftThreads)
+        colp[n] = n < ns ? (float)m * p.ms_b[p.spans[s0 + n].g0].lo : 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+
+    const float s_a = p.ms_a[R0 < p.nq ? R0 : p.nq - 1].hi;
+    const uint32_t idesc = instr_desc<kSeedVariant>(nmma);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int q = 0; q < nkb; ++q) {
+        const int k0 = q * kSeedEpr;
+        // query samples a[R0 + k0 + e], shifted (zeros past the series)
+        for (int e = tid; e < kLeftRaw; e += kLeftThreads) {
+            const int64_t j = R0 + k0 + e;
+            raw[e] = j < p.nq + m - 1 ? p.a[j] - s_a : 0.f;
+        }
+        // spans' first windows: thread fills 16-byte chunk c of span rows n
+#pragma unroll
+        for (int u = 0; u < kLeftGather; ++u) {
+            const int idx = tid + u * kLeftThreads;
+            const int n = idx >> 3, c = idx & 7;
+            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            if (n < ns) {
+                const int64_t g0 = p.spans[s0 + n].g0;
+                const float sb = p.ms_b[g0].hi;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = k0 + 4 * c + e;
+                    x[e] = (k < m && g0 + k < p.nb) ? p.b[g0 + k] - sb : 0.f;
+                }
+            }
+            if (n < nmma)
+                put_chunk<kSeedVariant>(x, b_hi, b_lo, (uint32_t)n * 128u + (uint32_t)((c ^ (n & 7)) << 4));
+        }
+        __syncthreads();
+        build_hankel<kSeedVariant>(raw, kLeftRows, a_hi, a_lo, tid, kLeftThreads);
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(a_hi), a1 = smem_u32(a_lo);
+            const uint32_t b0 = smem_u32(b_hi), b1 = smem_u32(b_lo);
+            // the span operand is 0 past m
+            const int ksteps = (min(kSeedEpr, m - k0) + kSeedKstep - 1) / kSeedKstep;
+            for (int k = 0; k < ksteps; ++k) {
+                const uint32_t acc = (q == 0 && k == 0) ? 0u : 1u;
+                mma<kSeedVariant>(taddr, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, acc);
+                mma<kSeedVariant>(taddr, smem_desc(a0 + 32u * k), smem_desc(b1 + 32u * k), idesc, 1u);
+                mma<kSeedVariant>(taddr, smem_desc(a1 + 32u * k), smem_desc(b0 + 32u * k), idesc, 1u);
+            }
+            mma_commit(bar);
+        }
+        // the next K-block rewrites the operands: wait for these MMAs
+        const bool w = mbar_wait(bar, phase, kSeedWaitCycles);
+        phase ^= 1u;
+        ok = __syncthreads_and(w ? 1 : 0) != 0;
+        tc_fence_after();
+        if (!ok) break;
+    }
+    if (ok) {
+        // epilogue: thread tid % 128 reads its query window's accumulator row (a
+        // warp reads the TMEM lane quarter warp % 4); the two groups of 4 warps
+        // take alternate 32-span groups
+        const int lrow = tid & (kLeftRows - 1), half = tid / kLeftRows;
+        const int64_t r = R0 + lrow;
+        float da = 0.f;
+        if (r < p.nq) {
+            const Split<float> ma = p.ms_a[r];
+            da = (ma.hi - s_a) + ma.lo;
+        }
+        const uint32_t t_lane = taddr + ((uint32_t)((warp & 3) * 32) << 16);
+        for (int c32 = 32 * half; c32 < nmma; c32 += 64) {
+            uint32_t v[32];
+            tmem_ld32(t_lane + (uint32_t)c32, v);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const int n = c32 + u;
+                if (n < ns && r < p.nq)
+                    p.left[(int64_t)(s0 + n) * p.ld + r] = fmaf(-da, colp[n], __uint_as_float(v[u]));
+            }
+        }
+    } else {
+        // a wait ran out: give the MMAs in flight time to finish before the
+        // TMEM and shared memory are released, and report the error
+        mbar_wait(bar, phase ^ 1u, kSeedWaitCycles);
+        if (tid == 0) atomicExch(p.err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, kLeftSpans);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct TcPlan {
@@ -1220,6 +1384,37 @@ int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core seed kernel launch: %s", cudaGetErrorString(e));
+    return MP_OK;
+}
+
+int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const float *b, int64_t nb,
+                  const void *ms_b, const Span *spans, int32_t n_spans, float *left, int64_t ld, int32_t *err,
+                  cudaStream_t st, fail_fn fail)
+{
+    const int64_t nq = n - m + 1;
+    if (m < 1 || nq <= 0 || n_spans <= 0) return MP_OK;
+    if (ld < nq) return fail(MP_E_INTERNAL, "left seeds: row stride %lld below %lld rows", (long long)ld, (long long)nq);
+    LeftArgs A;
+    A.a = a;
+    A.nq = nq;
+    A.m = m;
+    A.ms_a = (const Split<float> *)ms_a;
+    A.b = b;
+    A.nb = nb;
+    A.ms_b = (const Split<float> *)ms_b;
+    A.spans = spans;
+    A.n_spans = n_spans;
+    A.left = left;
+    A.ld = ld;
+    A.err = err;
+    const size_t smem = left_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_left_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        const dim3 grid((unsigned)((nq + kLeftRows - 1) / kLeftRows), (unsigned)((n_spans + kLeftSpans - 1) / kLeftSpans));
+        k_left_seed<<<grid, kLeftThreads, smem, st>>>(A);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fail(MP_E_CUDA, "tensor-core left-seed kernel launch: %s", cudaGetErrorString(e));
     return MP_OK;
 }
 

@@ -49,4 +49,14 @@ int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *
              const void *ms_b, const float *a, int64_t n, int32_t m, const void *ms_a, int32_t stride, float *seeds,
              int64_t ld, int32_t *err, cudaStream_t st, fail_fn fail);
 
+// Left seeds of the plain kernel (K2l) on the tensor cores: for every query
+// window r < n - m + 1 and span s < n_spans (device spans, the column groups'
+// runs of windows), left[s * ld + r] = the centred covariance
+// sum_k (a[r + k] - mean_a[r]) (b[g_s + k] - mean_b[g_s]) with g_s the span's
+// first window, in FP32 (three TF32 products of a hi/lo split). ld >= the
+// query windows. *err is set to 1 on a device-side timeout. Any m >= 1.
+int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const float *b, int64_t nb,
+                  const void *ms_b, const Span *spans, int32_t n_spans, float *left, int64_t ld, int32_t *err,
+                  cudaStream_t st, fail_fn fail);
+
 }  // namespace mpd
