@@ -102,6 +102,7 @@ struct DictStats {
         Span *spans = nullptr;
         int32_t *group_start = nullptr;
         int32_t n_spans = 0;
+        unsigned char *left_ops = nullptr;  // the spans' operand of the left-seed kernel (built at first use)
     };
     std::map<int, Grouping> groupings;
     void *tc_pack = nullptr;   // tensor-core operand cache (owned by the tc module)
@@ -462,6 +463,7 @@ static void free_stats(DictStats *s)
     for (auto &kv : s->groupings) {
         cudaFree(kv.second.spans);
         cudaFree(kv.second.group_start);
+        cudaFree(kv.second.left_ops);
     }
     tc_free_pack(s->tc_pack);
 }
@@ -813,6 +815,24 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             if (gr->n_spans != grouping_spans(s, geo.n_groups))
                 return fail(MP_E_INTERNAL, "left-seed layout: %d spans, %lld expected", gr->n_spans,
                             (long long)grouping_spans(s, geo.n_groups));
+            if (!gr->left_ops) {
+                // the spans' operand of the left-seed kernel: once per (dictionary, m, grouping);
+                // synchronised, so that joins on any stream find it complete
+                unsigned char *ops = nullptr;
+                if (cudaMalloc(&ops, tc_left_operand_bytes(gr->n_spans, m)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(MP_E_NOMEM, "left-seed operand");
+                }
+                int rc2 = tc_left_operand((const float *)d->d_samples, d->nb, s->ms, gr->spans, gr->n_spans, m, ops, st,
+                                          fail);
+                if (rc2 == MP_OK && cudaStreamSynchronize(st) != cudaSuccess)
+                    rc2 = fail(MP_E_CUDA, "left-seed operand: %s", cudaGetErrorString(cudaGetLastError()));
+                if (rc2) {
+                    cudaFree(ops);
+                    return rc2;
+                }
+                gr->left_ops = ops;
+            }
         }
         // row chunks (one chunk unless the seed matrix would exceed its cap)
         for (int64_t r0 = 0; r0 < nq; r0 += crow) {
@@ -823,8 +843,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
                                   (int32_t)s->seg_spans.size(), s->ms, a + r0, rows + m - 1, m, ms_a + r0,
                                   32 * kPlainRowsPerLane, seed_top, sg.ld, err, st, fail);
                 if (rc) return rc;
-                rc = tc_left_seeds(a + r0, rows + m - 1, m, ms_a + r0, (const float *)d->d_samples, d->nb, s->ms,
-                                   gr->spans, gr->n_spans, left, left_ld, err, st, fail);
+                rc = tc_left_seeds(a + r0, rows + m - 1, m, ms_a + r0, s->ms, gr->spans, gr->n_spans, gr->left_ops,
+                                   left, left_ld, err, st, fail);
                 if (rc) return rc;
             }
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);

@@ -899,43 +899,72 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
 // recurrence's diagonals from "left seeds": the centred covariance of every
 // query window r with the span's first window g_s,
 //     L[s, r] = sum_k (a[r + k] - mean_a[r]) * (b[g_s + k] - mean_b[g_s]).
-// For 128 consecutive query windows (the TMEM lanes) and up to 256 spans this
-// is a dense product with K = m. Per K-block (32 values of k) the query
-// windows form a row-shifted Hankel operand of the block's samples (shifted
-// by its first window's mean, hi part) and the spans' first windows a
-// gathered K-major operand (each centred on its own mean's hi part, zero past
-// m). The products are TF32 hi/lo as in K2s, so a left seed carries about
-// FP32's error. The epilogue removes the shifts and stores L[s][r]: for one
-// span, consecutive threads hold consecutive query windows, so the stores are
-// coalesced as they come.
+// For 128 consecutive query windows (the TMEM lanes) and up to 128 spans this
+// is a dense product with K = m. The spans' operand does not depend on the
+// query: k_left_operand builds it once per (dictionary, m, column grouping),
+// in the MMA's swizzled K-major layout (each first window centred on its own
+// mean's hi part, zero past m, TF32 hi and lo), one 32 KB block per span tile
+// and K-block (32 values of k). Per K-block a CTA copies the block into shared
+// memory with one bulk asynchronous copy (the next block's copy overlaps the
+// current MMAs) and builds the query's row-shifted Hankel operand from the
+// block's samples (shifted by the CTA's first window's mean, hi part; the next
+// block's samples are loaded into registers while the MMAs run). The products
+// are TF32 hi/lo as in K2s, so a left seed carries about FP32's error. The
+// epilogue removes the shifts and stores L[s][r]: for one span, consecutive
+// threads hold consecutive query windows, so the stores are coalesced as they
+// come.
+constexpr int kLeftThreads = 256;
+constexpr int kLeftRows = 128;
+constexpr int kLeftSpans = 128;                     // spans per CTA (TMEM columns, MMA N <= 128)
+constexpr int kLeftRaw = kLeftRows + kSeedEpr;      // query samples of one K-block
+constexpr uint32_t kLeftHalf = kLeftSpans * 128;    // bytes of one (hi or lo) span operand block
+constexpr uint32_t kLeftBlock = 2 * kLeftHalf;      // hi then lo
+static_assert(kLeftRaw <= kLeftThreads, "one query sample per thread");
+
 struct LeftArgs {
     const float *a;
     int64_t nq;
     int32_t m;
     const Split<float> *ms_a;
-    const float *b;
-    int64_t nb;
     const Split<float> *ms_b;
     const Span *spans;
     int32_t n_spans;
-    float *left;  // [n_spans][ld]
+    const unsigned char *ops;  // [span tile][K-block] blocks of kLeftBlock bytes (k_left_operand)
+    float *left;               // [n_spans][ld]
     int64_t ld;
     int32_t *err;
 };
 
-constexpr int kLeftThreads = 256;
-constexpr int kLeftRows = 128;
-constexpr int kLeftSpans = 256;                                     // spans per CTA (TMEM columns)
-constexpr int kLeftRaw = kLeftRows + kSeedEpr;                      // query samples of one K-block
-constexpr int kLeftGather = kLeftSpans * 8 / kLeftThreads;          // 16-byte B chunks per thread
-static_assert(kLeftRaw <= 2 * kLeftThreads, "two query samples per thread at most");
+// The spans' operand blocks: grid (span tiles, K-blocks), 256 threads.
+__global__ void __launch_bounds__(256) k_left_operand(const Span *spans, int32_t n_spans, int32_t m,
+                                                      const float *b, int64_t nb, const Split<float> *ms_b,
+                                                      unsigned char *ops)
+{
+    const int tile = blockIdx.x, q = blockIdx.y, nkb = gridDim.y;
+    unsigned char *hi = ops + ((size_t)tile * nkb + q) * kLeftBlock, *lo = hi + kLeftHalf;
+    const int k0 = q * kSeedEpr;
+    for (int idx = threadIdx.x; idx < kLeftSpans * 8; idx += blockDim.x) {
+        const int n = idx >> 3, c = idx & 7, s = tile * kLeftSpans + n;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (s < n_spans) {
+            const int64_t g0 = spans[s].g0;
+            const float sb = ms_b[g0].hi;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = k0 + 4 * c + e;
+                x[e] = (k < m && g0 + k < nb) ? b[g0 + k] - sb : 0.f;
+            }
+        }
+        put_chunk<kSeedVariant>(x, hi, lo, (uint32_t)n * 128u + (uint32_t)((c ^ (n & 7)) << 4));
+    }
+}
 
 size_t left_smem_bytes()
 {
-    // 1024-byte alignment slack, query operand (hi, lo), span operand (hi, lo),
-    // staged query samples, column terms, barrier and TMEM slot
-    return 1024 + 2 * (size_t)kLeftRows * 128 + 2 * (size_t)kLeftSpans * 128 + (kLeftRaw + 8) * 4 +
-           kLeftSpans * 4 + 16;
+    // 1024-byte alignment slack, query operand (hi, lo), two span operand
+    // blocks, staged query samples, column terms, barriers and TMEM slot
+    return 1024 + 2 * (size_t)kLeftRows * 128 + 2 * (size_t)kLeftBlock + (kLeftRaw + 8) * 4 + kLeftSpans * 4 +
+           3 * 8 + 16;
 }
 
 __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
@@ -944,69 +973,62 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *a_hi = base, *a_lo = base + kLeftRows * 128;
-    unsigned char *b_hi = base + 2 * kLeftRows * 128, *b_lo = b_hi + kLeftSpans * 128;
-    float *raw = reinterpret_cast<float *>(b_lo + kLeftSpans * 128);
+    unsigned char *bst[2] = {base + 2 * kLeftRows * 128, base + 2 * kLeftRows * 128 + kLeftBlock};
+    float *raw = reinterpret_cast<float *>(bst[1] + kLeftBlock);
     float *colp = raw + kLeftRaw + 8;  // m * (mean_b - s_b) = m * mean's lo part, per span
-    uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kLeftSpans);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kLeftSpans);  // MMAs done
+    uint64_t *cbar = bar + 1;                                         // [2] span blocks landed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 3);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t R0 = (int64_t)blockIdx.x * kLeftRows;  // first query window
-    const int s0 = blockIdx.y * kLeftSpans;               // first span
+    const int tile = blockIdx.y, s0 = tile * kLeftSpans;  // first span
     const int ns = min(kLeftSpans, p.n_spans - s0);
     const int nmma = (ns + 15) & ~15;
     const int m = p.m;
     const int nkb = (m + kSeedEpr - 1) / kSeedEpr;
+    const unsigned char *ops = p.ops + (size_t)tile * nkb * kLeftBlock;
 
     if (warp == 0) tmem_alloc(tmem_slot, kLeftSpans);
-    if (tid == 0) mbar_init(bar, 1);
-    // per span: its first window and mean (the column terms)
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(&cbar[0], 1);
+        mbar_init(&cbar[1], 1);
+    }
     for (int n = tid; n < kLeftSpans; n += kLeftThreads)
         colp[n] = n < ns ? (float)m * p.ms_b[p.spans[s0 + n].g0].lo : 0.f;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = *tmem_slot;
+    if (tid == 0) bulk_copy_g2s(bst[0], ops, kLeftBlock, &cbar[0]);
 
     const float s_a = p.ms_a[R0 < p.nq ? R0 : p.nq - 1].hi;
+    const int64_t na = p.nq + m - 1;
+    float xr = 0.f;  // this thread's query sample of the next K-block
+    auto load_raw = [&](int q) {
+        const int64_t j = R0 + q * kSeedEpr + tid;
+        xr = (tid < kLeftRaw && j < na) ? p.a[j] - s_a : 0.f;
+    };
+    load_raw(0);
     const uint32_t idesc = instr_desc<kSeedVariant>(nmma);
     uint32_t phase = 0;
+    int copies = 1;  // bulk copies issued
     bool ok = true;
     for (int q = 0; q < nkb; ++q) {
-        const int k0 = q * kSeedEpr;
-        // query samples a[R0 + k0 + e], shifted (zeros past the series)
-        for (int e = tid; e < kLeftRaw; e += kLeftThreads) {
-            const int64_t j = R0 + k0 + e;
-            raw[e] = j < p.nq + m - 1 ? p.a[j] - s_a : 0.f;
-        }
-        // spans' first windows: thread fills 16-byte chunk c of span rows n
-#pragma unroll
-        for (int u = 0; u < kLeftGather; ++u) {
-            const int idx = tid + u * kLeftThreads;
-            const int n = idx >> 3, c = idx & 7;
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (n < ns) {
-                const int64_t g0 = p.spans[s0 + n].g0;
-                const float sb = p.ms_b[g0].hi;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = k0 + 4 * c + e;
-                    x[e] = (k < m && g0 + k < p.nb) ? p.b[g0 + k] - sb : 0.f;
-                }
-            }
-            if (n < nmma)
-                put_chunk<kSeedVariant>(x, b_hi, b_lo, (uint32_t)n * 128u + (uint32_t)((c ^ (n & 7)) << 4));
-        }
+        // the query's Hankel operand of this K-block (the previous MMAs are done)
+        if (tid < kLeftRaw) raw[tid] = xr;
         __syncthreads();
         build_hankel<kSeedVariant>(raw, kLeftRows, a_hi, a_lo, tid, kLeftThreads);
         fence_async_smem();
-        __syncthreads();
+        const bool w = mbar_wait(&cbar[q & 1], (uint32_t)((q >> 1) & 1), kSeedWaitCycles);
+        if (!(ok = __syncthreads_and(w ? 1 : 0) != 0)) break;
         if (tid == 0) {
             tc_fence_after();
             const uint32_t a0 = smem_u32(a_hi), a1 = smem_u32(a_lo);
-            const uint32_t b0 = smem_u32(b_hi), b1 = smem_u32(b_lo);
+            const uint32_t b0 = smem_u32(bst[q & 1]), b1 = b0 + kLeftHalf;
             // the span operand is 0 past m
-            const int ksteps = (min(kSeedEpr, m - k0) + kSeedKstep - 1) / kSeedKstep;
+            const int ksteps = (min(kSeedEpr, m - q * kSeedEpr) + kSeedKstep - 1) / kSeedKstep;
             for (int k = 0; k < ksteps; ++k) {
                 const uint32_t acc = (q == 0 && k == 0) ? 0u : 1u;
                 mma<kSeedVariant>(taddr, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, acc);
@@ -1014,11 +1036,18 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
                 mma<kSeedVariant>(taddr, smem_desc(a1 + 32u * k), smem_desc(b0 + 32u * k), idesc, 1u);
             }
             mma_commit(bar);
+            // the other block's last MMAs (K-block q - 1) are done: it takes K-block q + 1
+            if (q + 1 < nkb) {
+                fence_async_smem();
+                bulk_copy_g2s(bst[(q + 1) & 1], ops + (size_t)(q + 1) * kLeftBlock, kLeftBlock, &cbar[(q + 1) & 1]);
+                ++copies;
+            }
         }
-        // the next K-block rewrites the operands: wait for these MMAs
-        const bool w = mbar_wait(bar, phase, kSeedWaitCycles);
+        if (q + 1 < nkb) load_raw(q + 1);  // overlaps the MMAs
+        // the next K-block rewrites the query operand: wait for these MMAs
+        const bool wm = mbar_wait(bar, phase, kSeedWaitCycles);
         phase ^= 1u;
-        ok = __syncthreads_and(w ? 1 : 0) != 0;
+        ok = __syncthreads_and(wm ? 1 : 0) != 0;
         tc_fence_after();
         if (!ok) break;
     }
@@ -1045,10 +1074,14 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
             }
         }
     } else {
-        // a wait ran out: give the MMAs in flight time to finish before the
-        // TMEM and shared memory are released, and report the error
-        mbar_wait(bar, phase ^ 1u, kSeedWaitCycles);
-        if (tid == 0) atomicExch(p.err, 1);
+        // a wait ran out: the MMAs and the copies in flight must finish before
+        // the TMEM and shared memory are released (their own bounds); report it
+        if (tid == 0) {
+            mbar_wait(bar, phase ^ 1u, kSeedWaitCycles);
+            const int last = copies - 1;  // the last copy went to block last & 1, its use (last >> 1)
+            mbar_wait(&cbar[last & 1], (uint32_t)((last >> 1) & 1), kSeedWaitCycles);
+            atomicExch(p.err, 1);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -1387,9 +1420,26 @@ int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *
     return MP_OK;
 }
 
-int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const float *b, int64_t nb,
-                  const void *ms_b, const Span *spans, int32_t n_spans, float *left, int64_t ld, int32_t *err,
-                  cudaStream_t st, fail_fn fail)
+size_t tc_left_operand_bytes(int32_t n_spans, int32_t m)
+{
+    const int64_t tiles = (n_spans + kLeftSpans - 1) / kLeftSpans, nkb = (m + kSeedEpr - 1) / kSeedEpr;
+    return (size_t)(tiles * nkb) * kLeftBlock;
+}
+
+int tc_left_operand(const float *b, int64_t nb, const void *ms_b, const Span *spans, int32_t n_spans, int32_t m,
+                    unsigned char *ops, cudaStream_t st, fail_fn fail)
+{
+    if (n_spans <= 0 || m < 1) return MP_OK;
+    const dim3 grid((unsigned)((n_spans + kLeftSpans - 1) / kLeftSpans), (unsigned)((m + kSeedEpr - 1) / kSeedEpr));
+    k_left_operand<<<grid, 256, 0, st>>>(spans, n_spans, m, b, nb, (const Split<float> *)ms_b, ops);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(MP_E_CUDA, "left-seed operand kernel launch: %s", cudaGetErrorString(e));
+    return MP_OK;
+}
+
+int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const void *ms_b, const Span *spans,
+                  int32_t n_spans, const unsigned char *ops, float *left, int64_t ld, int32_t *err, cudaStream_t st,
+                  fail_fn fail)
 {
     const int64_t nq = n - m + 1;
     if (m < 1 || nq <= 0 || n_spans <= 0) return MP_OK;
@@ -1399,11 +1449,10 @@ int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const 
     A.nq = nq;
     A.m = m;
     A.ms_a = (const Split<float> *)ms_a;
-    A.b = b;
-    A.nb = nb;
     A.ms_b = (const Split<float> *)ms_b;
     A.spans = spans;
     A.n_spans = n_spans;
+    A.ops = ops;
     A.left = left;
     A.ld = ld;
     A.err = err;

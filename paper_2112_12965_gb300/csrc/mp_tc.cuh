@@ -53,10 +53,15 @@ int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *
 // window r < n - m + 1 and span s < n_spans (device spans, the column groups'
 // runs of windows), left[s * ld + r] = the centred covariance
 // sum_k (a[r + k] - mean_a[r]) (b[g_s + k] - mean_b[g_s]) with g_s the span's
-// first window, in FP32 (three TF32 products of a hi/lo split). ld >= the
-// query windows. *err is set to 1 on a device-side timeout. Any m >= 1.
-int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const float *b, int64_t nb,
-                  const void *ms_b, const Span *spans, int32_t n_spans, float *left, int64_t ld, int32_t *err,
-                  cudaStream_t st, fail_fn fail);
+// first window, in FP32 (three TF32 products of a hi/lo split). ops is the
+// spans' operand (tc_left_operand_bytes bytes) that tc_left_operand builds
+// once for the dictionary, m and spans. ld >= the query windows. *err is set
+// to 1 on a device-side timeout. Any m >= 1.
+size_t tc_left_operand_bytes(int32_t n_spans, int32_t m);
+int tc_left_operand(const float *b, int64_t nb, const void *ms_b, const Span *spans, int32_t n_spans, int32_t m,
+                    unsigned char *ops, cudaStream_t st, fail_fn fail);
+int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const void *ms_b, const Span *spans,
+                  int32_t n_spans, const unsigned char *ops, float *left, int64_t ld, int32_t *err, cudaStream_t st,
+                  fail_fn fail);
 
 }  // namespace mpd
