@@ -427,7 +427,8 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
     import synthetic
 
     x = synthetic.ecg_like(n_b, seed).astype(np.float32)
-    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    # up to 256 requests (stream appends) admitted at once, 128 per batched launch
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=256, max_batch=128)
     out = {"study": "dictionary learning (Algorithm 1) and streaming",
            "workload": f"ECG-like training series of {n_b} samples (seed {seed}, normal beats), m={m}, context k=1.5, "
                        f"memory budget {budget_frac:.0%} of the series"}

@@ -904,11 +904,11 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
 // query: k_left_operand builds it once per (dictionary, m, column grouping),
 // in the MMA's swizzled K-major layout (each first window centred on its own
 // mean's hi part, zero past m, TF32 hi and lo), one 32 KB block per span tile
-// and K-block (32 values of k). Per K-block a CTA copies the block into shared
-// memory with one bulk asynchronous copy (the next block's copy overlaps the
-// current MMAs) and builds the query's row-shifted Hankel operand from the
-// block's samples (shifted by the CTA's first window's mean, hi part; the next
-// block's samples are loaded into registers while the MMAs run). The products
+// and K-block (32 values of k). A CTA stages its windows' samples for every
+// K-block once (shifted by its first window's mean, hi part). Per K-block it
+// copies the span block into shared memory with one bulk asynchronous copy
+// (the next block's copy overlaps the current MMAs) and builds the query's
+// row-shifted Hankel operand from the staged samples. The products
 // are TF32 hi/lo as in K2s, so a left seed carries about FP32's error. The
 // epilogue removes the shifts and stores L[s][r]: for one span, consecutive
 // threads hold consecutive query windows, so the stores are coalesced as they
@@ -916,10 +916,10 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
 constexpr int kLeftThreads = 256;
 constexpr int kLeftRows = 128;
 constexpr int kLeftSpans = 128;                     // spans per CTA (TMEM columns, MMA N <= 128)
-constexpr int kLeftRaw = kLeftRows + kSeedEpr;      // query samples of one K-block
 constexpr uint32_t kLeftHalf = kLeftSpans * 128;    // bytes of one (hi or lo) span operand block
 constexpr uint32_t kLeftBlock = 2 * kLeftHalf;      // hi then lo
-static_assert(kLeftRaw <= kLeftThreads, "one query sample per thread");
+// query samples a CTA stages: its 128 windows' samples for every K-block
+__host__ __device__ constexpr int left_raw(int m) { return kLeftRows + (m + kSeedEpr - 1) / kSeedEpr * kSeedEpr; }
 
 struct LeftArgs {
     const float *a;
@@ -959,11 +959,11 @@ __global__ void __launch_bounds__(256) k_left_operand(const Span *spans, int32_t
     }
 }
 
-size_t left_smem_bytes()
+size_t left_smem_bytes(int m)
 {
     // 1024-byte alignment slack, query operand (hi, lo), two span operand
     // blocks, staged query samples, column terms, barriers and TMEM slot
-    return 1024 + 2 * (size_t)kLeftRows * 128 + 2 * (size_t)kLeftBlock + (kLeftRaw + 8) * 4 + kLeftSpans * 4 +
+    return 1024 + 2 * (size_t)kLeftRows * 128 + 2 * (size_t)kLeftBlock + (left_raw(m) + 8) * 4 + kLeftSpans * 4 +
            3 * 8 + 16;
 }
 
@@ -974,8 +974,9 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *a_hi = base, *a_lo = base + kLeftRows * 128;
     unsigned char *bst[2] = {base + 2 * kLeftRows * 128, base + 2 * kLeftRows * 128 + kLeftBlock};
+    const int n_raw = left_raw(p.m);
     float *raw = reinterpret_cast<float *>(bst[1] + kLeftBlock);
-    float *colp = raw + kLeftRaw + 8;  // m * (mean_b - s_b) = m * mean's lo part, per span
+    float *colp = raw + n_raw + 8;  // m * (mean_b - s_b) = m * mean's lo part, per span
     uint64_t *bar = reinterpret_cast<uint64_t *>(colp + kLeftSpans);  // MMAs done
     uint64_t *cbar = bar + 1;                                         // [2] span blocks landed
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 3);
@@ -1003,23 +1004,22 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
     const uint32_t taddr = *tmem_slot;
     if (tid == 0) bulk_copy_g2s(bst[0], ops, kLeftBlock, &cbar[0]);
 
+    // the CTA's query samples for every K-block, shifted (zeros past the
+    // series), while the first span block is in flight
     const float s_a = p.ms_a[R0 < p.nq ? R0 : p.nq - 1].hi;
     const int64_t na = p.nq + m - 1;
-    float xr = 0.f;  // this thread's query sample of the next K-block
-    auto load_raw = [&](int q) {
-        const int64_t j = R0 + q * kSeedEpr + tid;
-        xr = (tid < kLeftRaw && j < na) ? p.a[j] - s_a : 0.f;
-    };
-    load_raw(0);
+    for (int e = tid; e < n_raw; e += kLeftThreads) {
+        const int64_t j = R0 + e;
+        raw[e] = j < na ? p.a[j] - s_a : 0.f;
+    }
     const uint32_t idesc = instr_desc<kSeedVariant>(nmma);
     uint32_t phase = 0;
     int copies = 1;  // bulk copies issued
     bool ok = true;
+    __syncthreads();  // the staged samples
     for (int q = 0; q < nkb; ++q) {
         // the query's Hankel operand of this K-block (the previous MMAs are done)
-        if (tid < kLeftRaw) raw[tid] = xr;
-        __syncthreads();
-        build_hankel<kSeedVariant>(raw, kLeftRows, a_hi, a_lo, tid, kLeftThreads);
+        build_hankel<kSeedVariant>(raw + q * kSeedEpr, kLeftRows, a_hi, a_lo, tid, kLeftThreads);
         fence_async_smem();
         const bool w = mbar_wait(&cbar[q & 1], (uint32_t)((q >> 1) & 1), kSeedWaitCycles);
         if (!(ok = __syncthreads_and(w ? 1 : 0) != 0)) break;
@@ -1043,7 +1043,6 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
                 ++copies;
             }
         }
-        if (q + 1 < nkb) load_raw(q + 1);  // overlaps the MMAs
         // the next K-block rewrites the query operand: wait for these MMAs
         const bool wm = mbar_wait(bar, phase, kSeedWaitCycles);
         phase ^= 1u;
@@ -1456,7 +1455,8 @@ int tc_left_seeds(const float *a, int64_t n, int32_t m, const void *ms_a, const 
     A.left = left;
     A.ld = ld;
     A.err = err;
-    const size_t smem = left_smem_bytes();
+    const size_t smem = left_smem_bytes(m);
+    if (smem > kTcSmemLimit) return fail(MP_E_ARG, "left seeds: m=%d needs %zu bytes of shared memory", m, smem);
     cudaError_t e = cudaFuncSetAttribute(k_left_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         const dim3 grid((unsigned)((nq + kLeftRows - 1) / kLeftRows), (unsigned)((n_spans + kLeftSpans - 1) / kLeftSpans));
