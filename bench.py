@@ -6,7 +6,7 @@ samples with FP64 window statistics. A step is one whole join (window
 statistics, join kernel, finalisation with the exact distance of each pick).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--kernel plain|bf16x3|tf32|auto] [--serving-requests R]
+                    [--kernel plain|bf16x3|tf32|bf16|auto] [--serving-requests R]
 
 Prints one JSON line (rank 0). With N > 1 (launched by torchrun) the query has
 N times the headline's windows and is partitioned by query rows: every rank
@@ -233,12 +233,13 @@ def roofline(kname, pairs, m, join_ms, peaks, peak_src, full_size=False, sms=152
         src += " / 2 (nominal TF32:BF16 ratio)"
     achieved = pairs * 2 * m * mult / (join_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": tflops_peak, "unit": "TFLOP/s",
-            "frac": achieved / tflops_peak, "traffic": None, "kernel": f"k_tc<{0 if kname == 'bf16x3' else 1}>",
+            "frac": achieved / tflops_peak, "traffic": None,
+            "kernel": "k_tc<%d>" % {"bf16x3": 0, "tf32": 1, "bf16": 3}[kname],
             "peak_source": src, "flops_per_pair": 2 * m * mult}
 
 
 def seed_roofline(w, seeds_ms, peaks, peak_src):
-    """Tensor roofline of the plain join's seed kernel (K2s): one seed row per SEED_STRIDE
+    """Tensor roofline of the plain join's top-seed kernel (K2s): one seed row per SEED_STRIDE
     query windows against every dictionary window, K = m, three TF32 products per term."""
     if seeds_ms <= 0:
         return None
@@ -248,6 +249,20 @@ def seed_roofline(w, seeds_ms, peaks, peak_src):
     achieved = flops / (seeds_ms / 1e3) / 1e12
     return {"bound": "tensor", "kernel": "k_seed", "ms": seeds_ms, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_launch": flops,
+            "peak_source": f"{peak_src} bf16 burst / 2 (nominal TF32:BF16 ratio)"}
+
+
+def left_seed_roofline(w, spans, left_ms, peaks, peak_src):
+    """Tensor roofline of the plain join's left-seed kernel (K2l): every query window against
+    the first window of every dictionary span (spans from mp_plan_join), K = m, three TF32
+    products per term."""
+    if left_ms <= 0 or spans <= 0:
+        return None
+    flops = w.n_rows * spans * 2 * w.m * 3
+    peak = peaks.get("bf16_tflops", 1900.0) / 2.0
+    achieved = flops / (left_ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "k_left_seed", "ms": left_ms, "spans": spans, "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_launch": flops,
             "peak_source": f"{peak_src} bf16 burst / 2 (nominal TF32:BF16 ratio)"}
 
 
@@ -340,9 +355,10 @@ def _device_join_timed(mp, ctx, d, q, m, reps=3):
     s.synchronize()
     ms, n = mp.mp_profile_read(ctx, reset=True)
     mp.mp_profile(ctx, False)
-    per_call = (ms[mp.MP_PHASE_JOIN] + ms[mp.MP_PHASE_SEEDS]) / reps  # a large join runs in several row chunks
+    # a large join runs in several row chunks
+    per_call = (ms[mp.MP_PHASE_JOIN] + ms[mp.MP_PHASE_SEEDS] + ms[mp.MP_PHASE_LEFT_SEEDS]) / reps
     _device_join_timed.last_phases = {"stats": ms[0] / reps, "join": ms[1] / reps, "finalize": ms[2] / reps,
-                                      "seeds": ms[3] / reps}
+                                      "seeds": ms[3] / reps, "left_seeds": ms[4] / reps}
     return dd.cpu().numpy(), di.cpu().numpy(), float(per_call)
 
 
@@ -359,7 +375,7 @@ def study_precision(mp, rows=256):
            "(seed 5), m=512", "rows_checked": rows, "pairs": w.pairs, "forms": {}}
     try:
         d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
-        for kname in ("plain", "bf16x3", "tf32"):
+        for kname in ("plain", "bf16x3", "tf32", "bf16"):
             mp.mp_set_kernel(ctx, kernel_id(mp, kname))
             mp.mp_counters(ctx, reset=True)
             dist, idx, jm = _device_join_timed(mp, ctx, d, w.query, w.m, reps=2)
@@ -616,7 +632,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "auto"])
+    ap.add_argument("--kernel", default="plain", choices=["plain", "bf16x3", "tf32", "bf16", "auto"])
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", choices=["precision", "dict-vs-orig", "serving", "learn"], default=None,
@@ -671,6 +687,7 @@ def main():
         w.query = full[lo:hi]
     ctx = mp.mp_init(device=local_rank, kernel=kernel_id(mp, args.kernel))
     d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+    plan = mp.mp_plan_join(ctx, d, mp.MP_F32, len(w.query), w.m)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     if world > 1:
@@ -692,10 +709,13 @@ def main():
     join_ms = phase_ms[mp.MP_PHASE_JOIN] / max(1, phase_n[mp.MP_PHASE_JOIN])
     clock = clk.summary()
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    roof = roofline(args.kernel, pairs, w.m, join_ms, peaks, peak_src, full_size=args.scale == 1.0, sms=sms)
+    # the form the join ran (the autotuner's pick under --kernel auto)
+    ran = {mp.MP_KERNEL_PLAIN: "plain", mp.MP_KERNEL_TC_BF16X3: "bf16x3", mp.MP_KERNEL_TC_TF32: "tf32",
+           mp.MP_KERNEL_TC_BF16: "bf16"}[plan["kernel"]]
+    roof = roofline(ran, pairs, w.m, join_ms, peaks, peak_src, full_size=args.scale == 1.0, sms=sms)
     # the other join forms on the same workload (same timing method)
     kernels = {}
-    for kname in ("plain", "bf16x3", "tf32"):
+    for kname in ("plain", "bf16x3", "tf32", "bf16"):
         if kname == args.kernel:
             sm, pm, pn = step_ms, phase_ms, phase_n
         else:
@@ -718,9 +738,13 @@ def main():
                    "parallelism": (f"one query of {world} x the windows, sharded by query rows over {world} GPUs "
                                    "(weak scaling, no data-path collective)") if world > 1 else "1 GPU"},
         "phases_ms": {"stats": phase_ms[0] / max(1, phase_n[0]), "seeds": phase_ms[3] / max(1, phase_n[3]),
-                      "join": join_ms, "finalize": phase_ms[2] / max(1, phase_n[2])},
+                      "left_seeds": phase_ms[4] / max(1, phase_n[4]), "join": join_ms,
+                      "finalize": phase_ms[2] / max(1, phase_n[2])},
         "roofline": roof,
         "seed_roofline": seed_roofline(w, phase_ms[3] / max(1, phase_n[3]), peaks, peak_src),
+        "left_seed_roofline": left_seed_roofline(w, plan["spans"], phase_ms[4] / max(1, phase_n[4]), peaks,
+                                                 peak_src),
+        "plan": plan,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(np.sum(phase_n)),

@@ -267,7 +267,7 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
  * latency jitter, and applications that own the device allocator (a caching
  * allocator or pool whose accounting a foreign cudaMalloc would break).
  *
- * Its scratch is one fixed array of about 46 MB inside this library, held by
+ * Its scratch is one fixed array of about 56 MB inside this library, held by
  * every GPU that loads the library until the process exits. Limits: float32
  * samples only, at most 2^19 query windows (n - m + 1), and a dictionary cut
  * into at most 2^16 runs of windows; larger calls return MP_E_ARG with a
@@ -361,12 +361,36 @@ int mp_top_discords(const double *profile, int64_t n, int32_t k, int64_t excl, d
 int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t n, double tolerance, int32_t *kernel,
                 int32_t *groups, double *ms);
 
+/*
+ * The plan of a join (Algorithm 2) of n query samples at window length m on
+ * this context, as mp_ab_join_device would run it now: the form (after the
+ * kernel setting, the autotuner's cache and the form's m limits), the plain
+ * form's column groups, the dictionary spans those groups cut (a span is one
+ * segment's run of windows inside one group; the left seeds hold one value per
+ * span and query window), the plain launches the query's windows take (row
+ * chunks), whether the FP32 plain join takes its seeds from the tensor cores,
+ * and the workspace bytes the context reserves for the join. It computes the
+ * dictionary's statistics for m if they are not resident (that allocates) and
+ * launches nothing else. Errors: MP_E_ARG as for mp_ab_join_device.
+ */
+typedef struct mp_join_plan {
+    int32_t kernel;          /* MP_KERNEL_* the join runs */
+    int32_t column_groups;   /* column groups of the plain form */
+    int64_t spans;           /* dictionary spans of those groups */
+    int64_t row_chunks;      /* plain launches over the query's windows */
+    int32_t tc_seeds;        /* 1: top and left seeds on the tensor cores (FP32 plain form) */
+    int32_t pad;
+    int64_t workspace_bytes; /* device workspace the join reserves (every form) */
+} mp_join_plan;
+int mp_plan_join(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int64_t n, int32_t m, mp_join_plan *plan);
+
 /* Phases of a join, for mp_profile_read. */
 #define MP_PHASE_STATS 0    /* window statistics of the query (K1) */
 #define MP_PHASE_JOIN 1     /* the join kernel: plain (K2) or tensor-core (K3) */
 #define MP_PHASE_FINALIZE 2 /* reduction, constant-window rule and exact distance of the pick (K4) */
 #define MP_PHASE_SEEDS 3    /* the plain join's top seeds on the tensor cores (K2s; FP32 plain joins) */
-#define MP_PHASE_COUNT 4
+#define MP_PHASE_LEFT_SEEDS 4 /* the plain join's left seeds on the tensor cores (K2l; FP32 plain joins) */
+#define MP_PHASE_COUNT 5
 
 /*
  * Tracing: with enable = 1, synchronous and device joins on this context

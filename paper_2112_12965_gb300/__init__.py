@@ -42,7 +42,8 @@ MP_PHASE_STATS = 0
 MP_PHASE_JOIN = 1
 MP_PHASE_FINALIZE = 2
 MP_PHASE_SEEDS = 3
-MP_PHASE_COUNT = 4
+MP_PHASE_LEFT_SEEDS = 4
+MP_PHASE_COUNT = 5
 
 MP_COUNTER_NEAR_ROWS = 0
 MP_COUNTER_NEAR_CHUNKS = 1
@@ -86,6 +87,18 @@ class mp_config(ctypes.Structure):
         ("mem_budget", ctypes.c_size_t),
         ("tune_cache", ctypes.c_char_p),
         ("max_pending", ctypes.c_int32),
+    ]
+
+
+class mp_join_plan(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_int32),
+        ("column_groups", ctypes.c_int32),
+        ("spans", ctypes.c_int64),
+        ("row_chunks", ctypes.c_int64),
+        ("tc_seeds", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("workspace_bytes", ctypes.c_int64),
     ]
 
 
@@ -133,6 +146,7 @@ def _load():
         "mp_profile_read": ([P, P, P, i32], ctypes.c_int),
         "mp_counters": ([P, P, i32], ctypes.c_int),
         "mp_test_hook": ([P, i32, i64], ctypes.c_int),
+        "mp_plan_join": ([P, P, i32, i64, i32, ctypes.POINTER(mp_join_plan)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -348,6 +362,13 @@ def mp_profile_read(ctx, reset: bool = False) -> Tuple[np.ndarray, np.ndarray]:
     n = np.zeros(MP_PHASE_COUNT, dtype=np.int64)
     _check(lib.mp_profile_read(ctx, _ptr(ms), _ptr(n), 1 if reset else 0))
     return ms, n
+
+
+def mp_plan_join(ctx, d, dtype: int, n: int, m: int) -> dict:
+    """The plan mp_ab_join_device would run for n query samples at window length m."""
+    p = mp_join_plan()
+    _check(lib.mp_plan_join(ctx, d, dtype, n, m, ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in mp_join_plan._fields_ if k != "pad"}
 
 
 def mp_counters(ctx, reset: bool = False) -> np.ndarray:

@@ -838,13 +838,16 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         for (int64_t r0 = 0; r0 < nq; r0 += crow) {
             const int64_t rows = std::min<int64_t>(crow, nq - r0);
             if (seeds) {
-                PhaseTimer t(ctx, MP_PHASE_SEEDS, st);
-                int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb, s->seg_spans.data(),
-                                  (int32_t)s->seg_spans.size(), s->ms, a + r0, rows + m - 1, m, ms_a + r0,
-                                  32 * kPlainRowsPerLane, seed_top, sg.ld, err, st, fail);
-                if (rc) return rc;
-                rc = tc_left_seeds(a + r0, rows + m - 1, m, ms_a + r0, s->ms, gr->spans, gr->n_spans, gr->left_ops,
-                                   left, left_ld, err, st, fail);
+                {
+                    PhaseTimer t(ctx, MP_PHASE_SEEDS, st);
+                    int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb,
+                                      s->seg_spans.data(), (int32_t)s->seg_spans.size(), s->ms, a + r0, rows + m - 1,
+                                      m, ms_a + r0, 32 * kPlainRowsPerLane, seed_top, sg.ld, err, st, fail);
+                    if (rc) return rc;
+                }
+                PhaseTimer t(ctx, MP_PHASE_LEFT_SEEDS, st);
+                int rc = tc_left_seeds(a + r0, rows + m - 1, m, ms_a + r0, s->ms, gr->spans, gr->n_spans, gr->left_ops,
+                                       left, left_ld, err, st, fail);
                 if (rc) return rc;
             }
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
@@ -1577,6 +1580,33 @@ int mp_poll(mp_ctx *ctx, uint64_t ticket, int32_t *state, double *latency_s)
     return MP_OK;
 }
 
+int mp_plan_join(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int64_t n, int32_t m, mp_join_plan *plan)
+{
+    g_err.clear();
+    if (!plan) return fail(MP_E_ARG, "null argument");
+    const char dummy = 0;  // the plan reads no query
+    int rc = check_join_args(ctx, dict, &dummy, dtype, n, m);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    mp_dict *d = const_cast<mp_dict *>(dict);
+    DictStats *s;
+    rc = get_stats(ctx, d, m, &s);
+    if (rc) return rc;
+    const int64_t nq = n - m + 1;
+    *plan = mp_join_plan{};
+    plan->kernel = s->n_windows > 0 ? resolve_kernel(ctx, dtype, m, s, nq) : MP_KERNEL_PLAIN;
+    if (s->n_windows == 0) return MP_OK;  // nothing runs: +inf and -1 are written directly
+    const Geometry geo = join_plain_geometry(ctx, d, s, dtype, nq, m, true);
+    const int64_t crow = plain_chunk_rows(d, dtype, nq, m, true);
+    plan->column_groups = geo.n_groups;
+    plan->spans = grouping_spans(s, geo.n_groups);
+    plan->row_chunks = (nq + crow - 1) / crow;
+    plan->tc_seeds = dtype == MP_F32 && plan->kernel == MP_KERNEL_PLAIN ? 1 : 0;
+    plan->workspace_bytes = (int64_t)join_ws_bytes(ctx, d, s, dtype, n, m);
+    return MP_OK;
+}
+
 int mp_profile(mp_ctx *ctx, int32_t enable)
 {
     g_err.clear();
@@ -2155,7 +2185,7 @@ constexpr size_t kNoAllocBytes = kNoAllocGroupOff + (kNoAllocMaxSpans + 1) * siz
 constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
-// About 54 MB: statistics of 2^19 query windows, 2^20 partial results with
+// About 56 MB: statistics of 2^19 query windows, 2^20 partial results with
 // their near-tie records, and 2^16 spans. Host code must not use this name as
 // an address: it is a host-side stand-in; the device address comes from
 // cudaGetSymbolAddress.

@@ -275,6 +275,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Two bulk asynchronous copies of `bytes` each (a multiple of 16; every
+// address 16-byte aligned) from global to this CTA's shared memory, both
+// completing on `bar`, which this call arms with their byte count.
+__device__ __forceinline__ void bulk_copy2_g2s(void *dst0, const void *src0, void *dst1, const void *src1,
+                                               uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(2u * bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst0)),
+                 "l"(src0), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst1)),
+                 "l"(src1), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte
 // aligned) from global to this CTA's shared memory, completing on `bar`,
 // which this call arms with the expected byte count (one arrival).
@@ -906,9 +924,9 @@ __global__ void __launch_bounds__(kSeedThreads, 2) k_seed(SeedArgs p)
 // mean's hi part, zero past m, TF32 hi and lo), one 32 KB block per span tile
 // and K-block (32 values of k). A CTA stages its windows' samples for every
 // K-block once (shifted by its first window's mean, hi part). Per K-block it
-// copies the span block into shared memory with one bulk asynchronous copy
-// (the next block's copy overlaps the current MMAs) and builds the query's
-// row-shifted Hankel operand from the staged samples. The products
+// copies the span block's rows in use (hi and lo) into shared memory with bulk
+// asynchronous copies (the next block's copies overlap the current MMAs) and
+// builds the query's row-shifted Hankel operand from the staged samples. The products
 // are TF32 hi/lo as in K2s, so a left seed carries about FP32's error. The
 // epilogue removes the shifts and stores L[s][r]: for one span, consecutive
 // threads hold consecutive query windows, so the stores are coalesced as they
@@ -1002,7 +1020,13 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = *tmem_slot;
-    if (tid == 0) bulk_copy_g2s(bst[0], ops, kLeftBlock, &cbar[0]);
+    // a span block's hi and lo rows [0, nmma): two bulk copies on one mbarrier
+    const uint32_t cbytes = (uint32_t)nmma * 128u;
+    auto copy_block = [&](int q, int buf) {
+        const unsigned char *src = ops + (size_t)q * kLeftBlock;
+        bulk_copy2_g2s(bst[buf], src, bst[buf] + kLeftHalf, src + kLeftHalf, cbytes, &cbar[buf]);
+    };
+    if (tid == 0) copy_block(0, 0);
 
     // the CTA's query samples for every K-block, shifted (zeros past the
     // series), while the first span block is in flight
@@ -1039,7 +1063,7 @@ __global__ void __launch_bounds__(kLeftThreads, 2) k_left_seed(LeftArgs p)
             // the other block's last MMAs (K-block q - 1) are done: it takes K-block q + 1
             if (q + 1 < nkb) {
                 fence_async_smem();
-                bulk_copy_g2s(bst[(q + 1) & 1], ops + (size_t)(q + 1) * kLeftBlock, kLeftBlock, &cbar[(q + 1) & 1]);
+                copy_block(q + 1, (q + 1) & 1);
                 ++copies;
             }
         }

@@ -41,6 +41,24 @@ def test_roofline_objects():
     assert tc["bound"] == "tensor" and tc["flops_per_pair"] == 2 * m * 3 and tc["traffic"] is None
     tf = bench.roofline("tf32", pairs, m, 1.0, peaks, "test")
     assert tf["peak"] == pytest.approx(1000.0) and tf["flops_per_pair"] == 2 * m
+    b1 = bench.roofline("bf16", pairs, m, 1.0, peaks, "test")
+    assert b1["peak"] == pytest.approx(2000.0) and b1["flops_per_pair"] == 2 * m and b1["kernel"] == "k_tc<3>"
+    assert tc["kernel"] == "k_tc<0>" and tf["kernel"] == "k_tc<1>"
+
+
+def test_seed_rooflines():
+    peaks = {"bf16_tflops": 2000.0}
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 64)
+    top = bench.seed_roofline(w, 1.0, peaks, "test")
+    # one seed row per 640 query windows against every dictionary window, three TF32 products
+    assert top["flops_per_launch"] == -(-w.n_rows // 640) * w.n_dict_windows * 2 * w.m * 3
+    assert top["peak"] == pytest.approx(1000.0)
+    left = bench.left_seed_roofline(w, 160, 0.5, peaks, "test")
+    # every query window against the first window of each of 160 spans
+    assert left["flops_per_launch"] == w.n_rows * 160 * 2 * w.m * 3
+    assert left["achieved"] == pytest.approx(left["flops_per_launch"] / 0.5e-3 / 1e12)
+    assert bench.left_seed_roofline(w, 0, 0.5, peaks, "test") is None
+    assert bench.seed_roofline(w, 0.0, peaks, "test") is None
 
 
 @pytest.mark.slow

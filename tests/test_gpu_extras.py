@@ -23,7 +23,7 @@ def test_autotune_picks_and_persists_a_plain_grouping(mp, tmp_path):
         assert kern == mp.MP_KERNEL_PLAIN and groups >= 1 and ms > 0
         # every form picks exactly, so any may win; the choice records the tolerance
         kern3, _, _ = mp.mp_autotune(ctx, d, w.m, len(w.query), 1e-3)
-        assert kern3 in (mp.MP_KERNEL_PLAIN, mp.MP_KERNEL_TC_BF16X3, mp.MP_KERNEL_TC_TF32)
+        assert kern3 in (mp.MP_KERNEL_PLAIN, mp.MP_KERNEL_TC_BF16X3, mp.MP_KERNEL_TC_TF32, mp.MP_KERNEL_TC_BF16)
         lines = [json.loads(x) for x in cache.read_text().splitlines()]
         assert len(lines) == 2 and lines[0]["m"] == w.m and lines[0]["kernel"] == kern
         assert lines[0]["tolerance"] == 1e-4 and lines[1]["tolerance"] == 1e-3
@@ -34,10 +34,41 @@ def test_autotune_picks_and_persists_a_plain_grouping(mp, tmp_path):
     ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_AUTO, tune_cache=str(cache))
     try:
         d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+        assert mp.mp_plan_join(ctx, d, mp.MP_F32, len(w.query), w.m)["kernel"] == kern3
         dist, idx = mp.mp_ab_join(ctx, d, w.query, w.m)
         rows = np.random.default_rng(5).choice(len(dist), 96, replace=False)
         parity.check(dist, idx, w.query, w.dict_samples, w.offsets, w.m, rows=rows, atol=1e-4)
         mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)
+
+
+def test_plan_join(mp):
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 8)
+    ctx = mp.mp_init(device=0)
+    try:
+        d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+        p = mp.mp_plan_join(ctx, d, mp.MP_F32, len(w.query), w.m)
+        assert p["kernel"] == mp.MP_KERNEL_PLAIN and p["tc_seeds"] == 1 and p["row_chunks"] >= 1
+        # a span is one segment's run of windows in one group: each segment gives at least one, and
+        # each segment boundary inside a group adds one to the groups
+        n_seg = len(w.offsets) - 1
+        assert n_seg <= p["spans"] <= p["column_groups"] + n_seg - 1
+        assert p["workspace_bytes"] > 0
+        mp.mp_set_kernel(ctx, mp.MP_KERNEL_TC_BF16)
+        p1 = mp.mp_plan_join(ctx, d, mp.MP_F32, len(w.query), w.m)
+        assert p1["kernel"] == mp.MP_KERNEL_TC_BF16 and p1["tc_seeds"] == 0
+        assert p1["workspace_bytes"] == p["workspace_bytes"]  # reserved for every form
+        with pytest.raises(mp.MPError):
+            mp.mp_plan_join(ctx, d, mp.MP_F32, len(w.query), 3)
+        with pytest.raises(mp.MPError):
+            mp.mp_plan_join(ctx, d, mp.MP_F64, len(w.query), w.m)  # the dictionary holds float32
+        mp.mp_dict_free(ctx, d)
+        # FP64: the plain form, no tensor-core seeds
+        d64 = mp.mp_dict_load(ctx, w.dict_samples.astype(np.float64), w.offsets, [w.m])
+        p2 = mp.mp_plan_join(ctx, d64, mp.MP_F64, 4096, w.m)
+        assert p2["kernel"] == mp.MP_KERNEL_PLAIN and p2["tc_seeds"] == 0
+        mp.mp_dict_free(ctx, d64)
     finally:
         mp.mp_shutdown(ctx)
 

@@ -250,7 +250,7 @@ def test_profile_phases(mp, ctx):
             mp.mp_ab_join(ctx, d, w.query, w.m)
         ms, n = mp.mp_profile_read(ctx, reset=True)
         # stats, join, finalisation, and the FP32 plain join's tensor-core seeds
-        assert list(n) == [3, 3, 3, 3] and np.all(ms > 0)
+        assert list(n) == [3, 3, 3, 3, 3] and np.all(ms > 0)
     finally:
         mp.mp_profile(ctx, False)
         mp.mp_dict_free(ctx, d)
