@@ -186,17 +186,20 @@ template <int kRows> struct Rows<float, kRows, true> {
         }
     }
     // Two columns share one 3-input maximum per row: score() keeps the first
-    // column's scores in q, score_max2() folds them with the second's.
-    __device__ __forceinline__ void score(float2 Z, float2 W, float2 *q) const
+    // column's scores in q, score_max2() folds them with the second's. Here Z
+    // is NaN on a column that may not be selected (constant window or
+    // padding): the score C * Z is then NaN, which the maximum ignores, so a
+    // packed multiply replaces the multiply-add with the penalty.
+    __device__ __forceinline__ void score(float2 Z, float2 *q) const
     {
 #pragma unroll
-        for (int k = 0; k < H; ++k) q[k] = __ffma2_rn(C[k], Z, W);
+        for (int k = 0; k < H; ++k) q[k] = __fmul2_rn(C[k], Z);
     }
-    __device__ __forceinline__ void score_max2(float2 Z, float2 W, const float2 *q0, float *cm) const
+    __device__ __forceinline__ void score_max2(float2 Z, const float2 *q0, float *cm) const
     {
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-            const float2 q = __ffma2_rn(C[k], Z, W);
+            const float2 q = __fmul2_rn(C[k], Z);
             cm[k] = fmaxf(cm[k], fmaxf(q0[k].x, q.x));
             cm[k + H] = fmaxf(cm[k + H], fmaxf(q0[k].y, q.y));
         }
@@ -328,7 +331,8 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                     v.w = T(-INFINITY);
                 }
                 if constexpr (kPack) {
-                    scs2[c] = make_float4(v.x, v.y, v.z, v.w);
+                    // z = NaN where the penalty is -inf (the packed scores are C * z)
+                    scs2[c] = make_float4(v.x, v.y, v.w < T(0) ? __int_as_float(0x7fc00000) : v.z, v.w);
                 } else {
                     scs[c] = v;
                 }
@@ -440,9 +444,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
                             R.step(make_float2(cv.x, cv.x), make_float2(cv.y, cv.y), up, lane == 0, stop_w[c]);
                         }
                         if ((u & 1) == 0)
-                            R.score(make_float2(cv.z, cv.z), make_float2(cv.w, cv.w), q0);
+                            R.score(make_float2(cv.z, cv.z), q0);
                         else
-                            R.score_max2(make_float2(cv.z, cv.z), make_float2(cv.w, cv.w), q0, cm);
+                            R.score_max2(make_float2(cv.z, cv.z), q0, cm);
                     }
                 } else if constexpr (!kPack && !kSelf && sizeof(T) == 4) {
                     // scalar FP32 form (serving): the same pairing of columns

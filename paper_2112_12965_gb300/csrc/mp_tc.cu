@@ -1132,7 +1132,11 @@ size_t plan_smem(const TcPlan &P)
 
 // Estimated SM clocks per tile: the MMAs (or the shared-memory traffic they
 // and the builders cause, if larger) plus, with one stage, the builders'
-// time that cannot overlap the MMAs.
+// time that cannot overlap the MMAs. The traffic term takes 64 bytes per
+// clock: measured kernels whose MMAs (M = 128, one SM) read 12 KB of operands
+// each ran at 60-68 bytes per clock of operand reads plus operand writes, not
+// at the 128 of ordinary shared-memory loads.
+constexpr double kTcSmemBytesPerClk = 64.0;
 double plan_clocks(const TcPlan &P, int m)
 {
     const double ksteps = (double)m / P.kstep;
@@ -1141,7 +1145,7 @@ double plan_clocks(const TcPlan &P, int m)
     const int groups = (P.nkb + P.qg - 1) / P.qg;
     const double writes = (double)groups * P.rb_rows * 128.0 * P.nhl;
     const double build = (double)groups * P.rb_rows * 8.0 / kBuildThreads * (P.variant == 1 ? 10.0 : 16.0);
-    const double smem = (reads + writes) / 128.0;
+    const double smem = (reads + writes) / kTcSmemBytesPerClk;
     return std::max(mma, smem) + (P.n_stages == 1 ? build : 0.0);
 }
 
