@@ -195,6 +195,10 @@ struct mp_ctx {
     bool stop = false;
     std::thread worker;
     cudaStream_t sstreams[2] = {nullptr, nullptr};
+    // the serving path's stream-ordered allocations; it keeps freed memory
+    // for reuse (bounded by the admission budget) instead of returning it to
+    // the driver at every synchronisation
+    cudaMemPool_t pool = nullptr;
     int next_stream = 0;
 
     // tracing
@@ -407,6 +411,33 @@ static int get_stats(mp_ctx *ctx, mp_dict *d, int32_t m, DictStats **out)
 
 // Cut the dictionary's valid windows into n_groups column groups of nearly
 // equal size; a span never crosses a segment. Cached per n_groups.
+// Column groups cut the dictionary's windows at chunk starts. A segment's
+// windows form chunks of kChunk windows from its first window on (the plain
+// and tensor-core kernels keep one approximate score per chunk, and the
+// finalisation re-scores a chunk with its first window's mean as the shift),
+// and a chunk belongs to group floor(p / T), p the position of its first
+// window among all the dictionary's windows and T = ceil(windows / groups).
+// So a window lies in the same chunk, scored with the same shift, whatever
+// the number of groups, and the join's results do not depend on it. With
+// T >= kChunk every group meets at least one chunk.
+static int64_t group_target(int64_t n_windows, int n_groups)
+{
+    return (std::max<int64_t>(1, n_windows) + n_groups - 1) / n_groups;
+}
+// groups that a segment's chunks meet (cum: windows before the segment)
+__host__ __device__ static inline int64_t segment_pieces(int64_t cum, int64_t ncols, int64_t T)
+{
+    if (ncols <= 0) return 0;
+    const int64_t last = cum + (ncols - 1) / kChunk * kChunk;  // position of the last chunk's first window
+    return last / T - cum / T + 1;
+}
+// the first chunk index (within the segment) whose start lies at or past
+// position p, for chunk starts cum, cum + kChunk, ...
+__host__ __device__ static inline int64_t chunk_at_or_after(int64_t cum, int64_t p)
+{
+    return p <= cum ? 0 : (p - cum + kChunk - 1) / kChunk;
+}
+
 static int get_grouping(mp_ctx *ctx, DictStats *s, int n_groups, DictStats::Grouping **out)
 {
     auto it = s->groupings.find(n_groups);
@@ -416,26 +447,23 @@ static int get_grouping(mp_ctx *ctx, DictStats *s, int n_groups, DictStats::Grou
     }
     std::vector<Span> spans;
     std::vector<int32_t> gstart(1, 0);
-    const int64_t target = (s->n_windows + n_groups - 1) / n_groups;
-    int64_t fill = 0;
+    const int64_t T = group_target(s->n_windows, n_groups);
+    int64_t cum = 0;
     for (const Span &seg : s->seg_spans) {
-        int64_t off = 0;
-        while (off < seg.ncols) {
-            const int64_t take = std::min<int64_t>(seg.ncols - off, target - fill);
+        const int64_t nch = (seg.ncols + kChunk - 1) / kChunk;
+        for (int64_t j = 0; j < nch;) {
+            const int64_t k = (cum + j * kChunk) / T;                       // this chunk's group
+            const int64_t j_end = std::min(nch, chunk_at_or_after(cum, (k + 1) * T));  // first chunk of a later group
+            while ((int64_t)gstart.size() <= k) gstart.push_back((int32_t)spans.size());  // group k starts here
             Span sp;
-            sp.g0 = seg.g0 + off;
-            sp.ncols = (int32_t)take;
+            sp.g0 = seg.g0 + j * kChunk;
+            sp.ncols = (int32_t)(std::min<int64_t>(seg.ncols, j_end * kChunk) - j * kChunk);
             sp.pad = 0;
             spans.push_back(sp);
-            off += take;
-            fill += take;
-            if (fill == target) {
-                gstart.push_back((int32_t)spans.size());
-                fill = 0;
-            }
+            j = j_end;
         }
+        cum += seg.ncols;
     }
-    if (fill > 0) gstart.push_back((int32_t)spans.size());
     while ((int)gstart.size() < n_groups + 1) gstart.push_back((int32_t)spans.size());
     DictStats::Grouping g;
     g.n_spans = (int32_t)spans.size();
@@ -523,26 +551,39 @@ static int plain_ctas_cached(bool f64, int warps, int m)
     return n;
 }
 
+// tc_seeds: the FP32 plain kernel loads its left seeds (computed on the
+// tensor cores) instead of computing them; batched: the serving kernel, where
+// a request's column groups share the GPU with other requests' work.
 static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int rows_per_lane, int dtype = -1,
-                               int m = 0, int64_t n_segments = 1)
+                               int m = 0, int64_t n_segments = 1, bool tc_seeds = false, bool batched = false)
 {
     Geometry g;
     const int64_t rows_warp = 32 * rows_per_lane;
     g.warps = nq <= rows_warp ? 1 : (nq <= 2 * rows_warp ? 2 : 4);
     const int64_t rows_cta = rows_warp * g.warps;
     g.n_row_blocks = (int)((nq + rows_cta - 1) / rows_cta);
-    // Column groups: each keeps >= 4096 windows (to amortise its left seeds),
-    // and the count is chosen by a cost model of whole waves: a launch of
+    // Column groups, chosen by a cost model of whole waves: a launch of
     // n_row_blocks * ng CTAs takes ceil(CTAs / resident CTAs) waves, each as
-    // long as one CTA's columns plus its left seeds (about m/4 columns' work
-    // per span). The smallest ng within 2 % of the cheapest wins.
-    const int64_t max_g = std::max<int64_t>(1, std::min<int64_t>(64, W / 4096));
+    // long as one CTA's columns plus its fixed work (staging the query rows
+    // and a first column block, about (m + 64) / 4 columns' worth) plus its
+    // left seeds per span (about m/4 columns' work when computed in the
+    // kernel, 8 when loaded), plus the finalisation's walk over the groups'
+    // partial results (about 5 columns' worth per group: its loads of a row's
+    // groups follow one another). The smallest ng within 2 % of the cheapest
+    // wins. A group keeps at least 16 columns (one chunk of the lazy argmax);
+    // a batched request's groups keep enough columns that their fixed work
+    // stays within a quarter of the request's, since other requests fill the
+    // GPU.
+    const double fixed = (double)(std::max(m, 16) + 64) / 4.0;
+    const double span_cost = tc_seeds ? 8.0 : (double)std::max(m, 16) / 4.0;
+    const int64_t min_cols = batched ? (int64_t)(4.0 * (fixed + span_cost)) : 16;
+    const int64_t max_g = std::max<int64_t>(1, std::min<int64_t>(1024, W / min_cols));
     const int per_sm = m > 0 ? plain_ctas_cached(dtype == MP_F64, g.warps, m) : 4;
     const double slots = (double)ctx->sm_count * per_sm;
     const double nseg = std::max<double>(1.0, (double)n_segments);
     auto cost = [&](int64_t k) {
         const double waves = std::ceil((double)g.n_row_blocks * (double)k / slots);
-        return waves * ((double)W / (double)k + (double)std::max(m, 16) / 4.0 * (nseg / (double)k + 1.0));
+        return waves * ((double)W / (double)k + fixed + span_cost * (nseg / (double)k + 1.0)) + 5.0 * (double)k;
     };
     double best_c = 1e300;
     for (int64_t k = 1; k <= max_g; ++k) best_c = std::min(best_c, cost(k));
@@ -554,7 +595,9 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
         auto it = ctx->tune.find(TuneKey{dtype, m, ilog2(W), ilog2(nq)});
         if (it != ctx->tune.end() && it->second.kernel == MP_KERNEL_PLAIN) ng = it->second.groups;
     }
-    g.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(ng, W));
+    // at most one group per chunk's worth of windows (T >= kChunk: no group
+    // without a chunk), also for a grouping taken from the tuning cache
+    g.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(ng, W / kChunk));
     return g;
 }
 
@@ -674,10 +717,10 @@ static size_t join_seed_bytes(const mp_dict *d, int32_t dtype, int64_t nq, int32
 // groups (a segment contributes one span per group it meets).
 static int64_t grouping_spans(const DictStats *s, int n_groups)
 {
-    const int64_t target = (std::max<int64_t>(1, s->n_windows) + n_groups - 1) / n_groups;
+    const int64_t T = group_target(s->n_windows, n_groups);
     int64_t n = 0, cum = 0;
     for (const Span &seg : s->seg_spans) {
-        n += (cum + seg.ncols - 1) / target - cum / target + 1;
+        n += segment_pieces(cum, seg.ncols, T);
         cum += seg.ncols;
     }
     return n;
@@ -693,7 +736,7 @@ static Geometry join_plain_geometry(const mp_ctx *ctx, const mp_dict *d, const D
 {
     const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
     return plain_geometry(ctx, plain_chunk_rows(d, dtype, nq, m, seeds), std::max<int64_t>(1, s->n_windows), rpl,
-                          dtype, m, (int64_t)s->seg_spans.size());
+                          dtype, m, (int64_t)s->seg_spans.size(), seeds && dtype == MP_F32);
 }
 
 // The workspace layout join_device uses for this form: the plain form's column
@@ -710,6 +753,19 @@ static JoinWs join_layout(const mp_ctx *ctx, const mp_dict *d, const DictStats *
         left = (size_t)grouping_spans(s, groups) * left_ld_for(plain_chunk_rows(d, dtype, nq, m, seeds)) * 4;
     return join_ws_layout(nq, dtype, groups, 0, join_seed_bytes(d, dtype, nq, m, seeds), near_slots_for(kernel),
                           left);
+}
+
+// Whether an FP32 plain join of nq query windows takes its top and left seeds
+// from the tensor-core kernels (K2s, K2l) rather than computing them in the
+// plain kernel. The two seed kernels cost a few tens of microseconds whatever
+// the size (their tiles run one after another inside a CTA); computing the
+// seeds in the plain kernel costs about a seventh of its column work plus
+// m/4 columns per span and CTA. Below about 2^31 pairs the in-kernel seeds
+// are cheaper.
+constexpr double kTcSeedMinPairs = 2147483648.0;
+static bool tc_seeds_pay(const DictStats *s, int32_t dtype, int64_t nq)
+{
+    return dtype == MP_F32 && (double)nq * (double)std::max<int64_t>(1, s->n_windows) >= kTcSeedMinPairs;
 }
 
 // The join on device buffers; `base` is a device workspace of at least
@@ -729,6 +785,8 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
         return fail(MP_E_INTERNAL, "the self-join runs the FP32 plain kernel with tensor-core seeds");
     const int64_t nq = n - m + 1;
     if (s->n_windows == 0) return fail(MP_E_INTERNAL, "empty dictionary must be handled by the caller");
+    // a small join computes its seeds in the plain kernel (the self-join's kernel needs the tensor-core seeds)
+    if (excl == 0) seeds = seeds && tc_seeds_pay(s, dtype, nq);
     const int64_t crow = plain_chunk_rows(d, dtype, nq, m, seeds);  // query windows per plain launch
     const Geometry geo = join_plain_geometry(ctx, d, s, dtype, nq, m, seeds);
     const bool tc = is_tc(kernel);
@@ -886,7 +944,10 @@ static size_t join_ws_bytes(const mp_ctx *ctx, const mp_dict *d, const DictStats
                             int32_t m, bool seeds = true)
 {
     const int64_t nq = n - m + 1;
-    size_t b = join_layout(ctx, d, s, dtype, nq, m, MP_KERNEL_PLAIN, seeds).total;
+    // the plain form with the seeds the join may take (join_device leaves out
+    // the tensor-core seeds of a small join), or a tensor-core form
+    size_t b = join_layout(ctx, d, s, dtype, nq, m, MP_KERNEL_PLAIN, false).total;
+    if (seeds) b = std::max(b, join_layout(ctx, d, s, dtype, nq, m, MP_KERNEL_PLAIN, true).total);
     if (dtype == MP_F32) b = std::max(b, join_layout(ctx, d, s, dtype, nq, m, MP_KERNEL_TC_BF16X3, seeds).total);
     return b;
 }
@@ -918,7 +979,7 @@ static Geometry serve_geometry(const mp_ctx *ctx, int64_t nq, const DictStats *s
 {
     Geometry geo =
         plain_geometry(ctx, nq, std::max<int64_t>(1, s->n_windows), kServeRowsPerLane, dtype, m,
-                       (int64_t)s->seg_spans.size());
+                       (int64_t)s->seg_spans.size(), false, true);
     geo.warps = 4;
     geo.n_row_blocks = (int)((nq + 4 * 32 * kServeRowsPerLane - 1) / (4 * 32 * kServeRowsPerLane));
     return geo;
@@ -1098,7 +1159,7 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
     if (!preqs.empty()) {
         const size_t sz_req = align_up(preqs.size() * sizeof(PlainRequest), 256);
         const size_t sz_items = align_up(items.size() * sizeof(BatchItem), 256);
-        if (cudaMallocAsync(&bt.dmem, sz_req + sz_items + 256, st) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&bt.dmem, sz_req + sz_items + 256, ctx->pool, st) != cudaSuccess) {
             cudaGetLastError();
             return fail(MP_E_NOMEM, "batch tables");
         }
@@ -1161,7 +1222,7 @@ static void scheduler_loop(mp_ctx *ctx)
             ctx->pending.pop_front();
             const bool injected = ctx->hook_fail_alloc > 0;  // a testing hook: fail as if out of memory
             if (injected) --ctx->hook_fail_alloc;
-            if (injected || cudaMallocAsync(&r->dmem, r->bytes, bt.stream) != cudaSuccess) {
+            if (injected || cudaMallocFromPoolAsync(&r->dmem, r->bytes, ctx->pool, bt.stream) != cudaSuccess) {
                 cudaGetLastError();
                 pinned_give(ctx, r->h_stage, r->stage_bytes);
                 r->h_stage = nullptr;
@@ -1248,6 +1309,16 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
     CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[0], cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[1], cudaStreamNonBlocking));
+    {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = cfg.device;
+        CUDA_TRY(cudaMemPoolCreate(&c->pool, &props));
+        uint64_t keep = UINT64_MAX;
+        CUDA_TRY(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     CUDA_TRY(cudaMalloc(&c->d_counters, kFinCounters * sizeof(unsigned long long)));
     CUDA_TRY(cudaMemset(c->d_counters, 0, kFinCounters * sizeof(unsigned long long)));
     size_t fr = 0, tot = 0;
@@ -1287,6 +1358,9 @@ int mp_shutdown(mp_ctx *ctx)
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (auto &kv : ctx->pinned_free)
         for (void *p : kv.second) cudaFreeHost(p);
+    cudaStreamSynchronize(ctx->sstreams[0]);
+    cudaStreamSynchronize(ctx->sstreams[1]);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     cudaStreamDestroy(ctx->stream);
     cudaStreamDestroy(ctx->sstreams[0]);
     cudaStreamDestroy(ctx->sstreams[1]);
@@ -1597,12 +1671,13 @@ int mp_plan_join(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int64_t n, int
     *plan = mp_join_plan{};
     plan->kernel = s->n_windows > 0 ? resolve_kernel(ctx, dtype, m, s, nq) : MP_KERNEL_PLAIN;
     if (s->n_windows == 0) return MP_OK;  // nothing runs: +inf and -1 are written directly
-    const Geometry geo = join_plain_geometry(ctx, d, s, dtype, nq, m, true);
-    const int64_t crow = plain_chunk_rows(d, dtype, nq, m, true);
+    const bool seeds = tc_seeds_pay(s, dtype, nq);  // as join_device decides for the plain form
+    const Geometry geo = join_plain_geometry(ctx, d, s, dtype, nq, m, seeds);
+    const int64_t crow = plain_chunk_rows(d, dtype, nq, m, seeds);
     plan->column_groups = geo.n_groups;
     plan->spans = grouping_spans(s, geo.n_groups);
     plan->row_chunks = (nq + crow - 1) / crow;
-    plan->tc_seeds = dtype == MP_F32 && plan->kernel == MP_KERNEL_PLAIN ? 1 : 0;
+    plan->tc_seeds = seeds && plan->kernel == MP_KERNEL_PLAIN ? 1 : 0;
     plan->workspace_bytes = (int64_t)join_ws_bytes(ctx, d, s, dtype, n, m);
     return MP_OK;
 }
@@ -2254,25 +2329,33 @@ __global__ void __launch_bounds__(1024) k_noalloc_groups(const Span *seg, int32_
     for (int s = s0; s < s1; ++s) cols += seg[s].ncols;
     int64_t tot;
     const int64_t cum0 = block_excl_scan(cols, tmp, &tot);
-    // spans of each segment: one per group it meets
+    // spans of each segment: one per group its chunks meet (the cut of get_grouping)
     int64_t pieces = 0, cum = cum0;
     for (int s = s0; s < s1; ++s) {
-        const int64_t n = seg[s].ncols;
-        pieces += (cum + n - 1) / T - cum / T + 1;
-        cum += n;
+        pieces += segment_pieces(cum, seg[s].ncols, T);
+        cum += seg[s].ncols;
     }
     int64_t idx = block_excl_scan(pieces, tmp, &tot);  // also orders the gstart initialisation before the writes
     cum = cum0;
+    // the group of the previous segment's last chunk (-1 before the first segment)
+    int64_t prev_k = -1;
+    if (s0 > 0 && s0 < s1) {
+        const int64_t n = seg[s0 - 1].ncols, c = cum0 - n;
+        prev_k = n > 0 ? (c + (n - 1) / kChunk * kChunk) / T : -1;
+    }
     for (int s = s0; s < s1; ++s) {
         const Span sg = seg[s];
-        const int64_t end = cum + sg.ncols;
-        for (int64_t k = cum / T; k * T < end; ++k) {
-            const int64_t a = max(cum, k * T), b = min(end, (k + 1) * T);
-            spans[idx] = Span{sg.g0 + (a - cum), (int32_t)(b - a), 0};
-            if (a == k * T) gstart[k] = (int32_t)idx;  // group k starts here
+        const int64_t nch = (sg.ncols + kChunk - 1) / kChunk;
+        for (int64_t j = 0; j < nch;) {
+            const int64_t k = (cum + j * kChunk) / T;
+            const int64_t j_end = min(nch, chunk_at_or_after(cum, (k + 1) * T));
+            spans[idx] = Span{sg.g0 + j * kChunk, (int32_t)(min((int64_t)sg.ncols, j_end * kChunk) - j * kChunk), 0};
+            if (j > 0 || prev_k < k) gstart[k] = (int32_t)idx;  // group k's first chunk
+            prev_k = k;
             ++idx;
+            j = j_end;
         }
-        cum = end;
+        cum += sg.ncols;
     }
 }
 
@@ -2318,12 +2401,8 @@ extern "C" int mp_ab_join_noalloc(mp_ctx *ctx, const mp_dict *dict, const void *
         geo.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(geo.n_groups, kNoAllocMaxPartials / nq));
         // the cut into column groups of get_grouping, built on the device from
         // the dictionary's resident segment table (no host copy per call)
-        const int64_t target = (s->n_windows + geo.n_groups - 1) / geo.n_groups;
-        int64_t n_spans = 0, cum = 0;
-        for (const Span &seg : s->seg_spans) {
-            n_spans += (cum + seg.ncols - 1) / target - cum / target + 1;
-            cum += seg.ncols;
-        }
+        const int64_t target = group_target(s->n_windows, geo.n_groups);
+        const int64_t n_spans = grouping_spans(s, geo.n_groups);
         if (n_spans > kNoAllocMaxSpans)
             return fail(MP_E_ARG, "dictionary needs %lld spans, above the no-allocation limit of %lld",
                         (long long)n_spans, (long long)kNoAllocMaxSpans);

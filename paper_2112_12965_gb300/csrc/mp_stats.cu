@@ -24,7 +24,7 @@ namespace mpd {
 namespace {
 
 constexpr int kStatsThreads = 256;
-constexpr int kStatsTile = 1024;  // windows per CTA
+constexpr int kStatsTile = 1024;  // windows per CTA (halved down to 128 while the grid is small)
 
 __device__ __forceinline__ double block_exclusive_scan(double v, double *warp_tot, double *total)
 {
@@ -94,12 +94,12 @@ __global__ void __launch_bounds__(kStatsThreads) k_window_stats(const T *__restr
                                                                  double *__restrict__ invstd,
                                                                  uint8_t *__restrict__ cflag,
                                                                  vec4_t<T> *__restrict__ rs,
-                                                                 Split<T> *__restrict__ ms)
+                                                                 Split<T> *__restrict__ ms, int32_t tile)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t nw = n - m + 1;
-    const int64_t w0 = (int64_t)blockIdx.x * kStatsTile;
-    const int tw = (nw - w0 < kStatsTile) ? (int)(nw - w0) : kStatsTile;
+    const int64_t w0 = (int64_t)blockIdx.x * tile;
+    const int tw = (nw - w0 < tile) ? (int)(nw - w0) : tile;
     // Samples e = 0 .. E-1 hold x[w0 - 1 + e]; e = 0 is the sample before the
     // tile (needed for the previous window's mean), absent for the first tile.
     const int E = tw + m;
@@ -287,14 +287,18 @@ cudaError_t launch_window_stats(const T *x, int64_t n, int32_t m, double *mean, 
 {
     const int64_t nw = n - m + 1;
     if (nw <= 0) return cudaSuccess;
-    const int64_t grid = (nw + kStatsTile - 1) / kStatsTile;
-    const int E = kStatsTile + m;
+    // smaller tiles for short series, so that a short query's statistics
+    // spread over many SMs instead of running in one CTA
+    int tile = kStatsTile;
+    while (tile > 128 && (nw + tile - 1) / tile < 512) tile >>= 1;
+    const int64_t grid = (nw + tile - 1) / tile;
+    const int E = tile + m;
     const size_t smem = (size_t)(E + 1) * (2 * sizeof(double) + sizeof(int));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_window_stats<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_window_stats<T><<<(unsigned)grid, kStatsThreads, smem, st>>>(x, n, m, mean, invstd, cflag, rs, ms);
+    k_window_stats<T><<<(unsigned)grid, kStatsThreads, smem, st>>>(x, n, m, mean, invstd, cflag, rs, ms, tile);
     return cudaGetLastError();
 }
 

@@ -241,7 +241,7 @@ def test_argument_errors(mp, ctx):
 
 
 def test_profile_phases(mp, ctx):
-    w = synthetic.workload("ecg_1m_m256", scale=1 / 64)
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 16)
     d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
     try:
         mp.mp_profile(ctx, True)
@@ -249,8 +249,16 @@ def test_profile_phases(mp, ctx):
         for _ in range(3):
             mp.mp_ab_join(ctx, d, w.query, w.m)
         ms, n = mp.mp_profile_read(ctx, reset=True)
-        # stats, join, finalisation, and the FP32 plain join's tensor-core seeds
+        # stats, join, finalisation, and the FP32 plain join's tensor-core seeds (3.2e9 pairs)
+        assert mp.mp_plan_join(ctx, d, mp.MP_F32, len(w.query), w.m)["tc_seeds"] == 1
         assert list(n) == [3, 3, 3, 3, 3] and np.all(ms > 0)
+        # a join below 2^31 pairs computes its seeds in the plain kernel
+        q = w.query[: 8192 + w.m - 1]
+        assert mp.mp_plan_join(ctx, d, mp.MP_F32, len(q), w.m)["tc_seeds"] == 0
+        for _ in range(3):
+            mp.mp_ab_join(ctx, d, q, w.m)
+        ms, n = mp.mp_profile_read(ctx, reset=True)
+        assert list(n) == [3, 3, 3, 0, 0] and np.all(ms[:3] > 0)
     finally:
         mp.mp_profile(ctx, False)
         mp.mp_dict_free(ctx, d)
@@ -358,17 +366,60 @@ def _near_copies_case():
     return q.astype(np.float32), b, offs, m
 
 
-def test_near_tie_records_overflow_rescans_the_group(mp):
+def _ilog2(x):
+    return int(x).bit_length() - 1
+
+
+@pytest.mark.parametrize("groups", [1, 3, 7, 40])
+def test_results_do_not_depend_on_the_column_grouping(mp, tmp_path, groups):
+    """Column groups are cut at chunk starts (every 16 windows from a segment's first window), so a window is
+    scored in the same chunk with the same shift under any grouping: a tuning-cache line that forces the
+    plain form to `groups` column groups gives the default join's results bit for bit."""
+    b = synthetic.ecg_like(9000, 71).astype(np.float32)
+    offs = np.array([0, 1234, 4321, 4999, 9000], dtype=np.int64)  # ragged segments
+    q = synthetic.ecg_like(6000, 72).astype(np.float32)
+    m = 96
+    n_w = sum(int(offs[i + 1] - offs[i]) - m + 1 for i in range(len(offs) - 1))
+    nq = len(q) - m + 1
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        ref_d, ref_i = join(mp, ctx, q, b, offs, m)
+    finally:
+        mp.mp_shutdown(ctx)
+    cache = tmp_path / "groups.jsonl"
+    cache.write_text('{"dtype": %d, "m": %d, "wlog": %d, "qlog": %d, "kernel": %d, "groups": %d, "ms": 0}\n'
+                     % (mp.MP_F32, m, _ilog2(n_w), _ilog2(nq), mp.MP_KERNEL_PLAIN, groups))
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_AUTO, tune_cache=str(cache))
+    try:
+        d = mp.mp_dict_load(ctx, b, offs, [m])
+        assert mp.mp_plan_join(ctx, d, mp.MP_F32, len(q), m)["column_groups"] == groups
+        dist, idx = mp.mp_ab_join(ctx, d, q, m)
+        mp.mp_dict_free(ctx, d)
+    finally:
+        mp.mp_shutdown(ctx)
+    assert np.array_equal(dist, ref_d) and np.array_equal(idx, ref_i)
+    parity.check(dist, idx, q, b, offs, m, rows=np.arange(0, nq, 41), atol=1e-4)
+
+
+def test_near_tie_records_overflow_rescans_the_group(mp, tmp_path):
     """Seven near-tied chunks per query window in one column group: more than the plain kernel's record slots.
     The records overflow, the finalisation re-scores the whole column group for those windows, and every
     row still matches the oracle (1e-4, the plain path's tolerance). The context's counters show that the
-    overflow path ran."""
+    overflow path ran. A tuning-cache line pins the plain form to one column group for this shape (the
+    default cost model spreads a join this small over many narrow groups, each holding one copy)."""
     q, b, offs, m = _near_copies_case()
-    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    n_w, nq = len(b) - m + 1, len(q) - m + 1
+    cache = tmp_path / "one_group.jsonl"
+    cache.write_text('{"dtype": %d, "m": %d, "wlog": %d, "qlog": %d, "kernel": %d, "groups": 1, "ms": 0}\n'
+                     % (mp.MP_F32, m, _ilog2(n_w), _ilog2(nq), mp.MP_KERNEL_PLAIN))
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_AUTO, tune_cache=str(cache))
     try:
         mp.mp_counters(ctx, reset=True)
-        dist, idx = join(mp, ctx, q, b, offs, m)
+        d = mp.mp_dict_load(ctx, b, offs, [m])
+        assert mp.mp_plan_join(ctx, d, mp.MP_F32, len(q), m)["column_groups"] == 1
+        dist, idx = mp.mp_ab_join(ctx, d, q, m)
         c = mp.mp_counters(ctx)
+        mp.mp_dict_free(ctx, d)
     finally:
         mp.mp_shutdown(ctx)
     od, oi, od2 = oracle.ab_join(q, b, offs, m)
