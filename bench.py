@@ -473,7 +473,8 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
         t_stream = time.perf_counter() - t0
         mp.mp_stream_close(st)
         # the same appends without waiting (mp_stream_submit: each append a serving request), up to
-        # 256 outstanding; equal to the synchronous appends' results
+        # 1024 outstanding (the library admits 256 at once, 128 per batched launch); equal to the
+        # synchronous appends' results
         st = mp.mp_stream_open(ctx, d, mp.MP_F32, m)
         t0 = time.perf_counter()
         live, outs, n_win_async = collections.OrderedDict(), [], 0
@@ -492,11 +493,11 @@ def study_learn(mp, n_b=1 << 20, m=256, budget_frac=0.01, seed=6):
             n_win_async += k
             if t:
                 live[t] = True
-            while len(live) >= 256:  # oldest first: appends finish roughly in order
+            while len(live) >= 1024:  # oldest first: appends finish roughly in order
                 tk = next(iter(live))
                 stt, _ = mp.mp_poll(ctx, tk)
                 if stt == mp.MP_PENDING:
-                    time.sleep(0.00005)
+                    time.sleep(0)  # yield to the library's scheduler thread
                     continue
                 if stt != mp.MP_DONE:
                     raise RuntimeError("stream append failed")

@@ -213,7 +213,8 @@ struct mp_ctx {
     int64_t prof_n[MP_PHASE_COUNT] = {};
 
     // pinned staging buffers, free lists by power-of-two size class
-    std::map<size_t, std::vector<void *>> pinned_free;
+    std::map<size_t, std::vector<void *>> pinned_free;  // staging buffers by size class
+    std::vector<void *> pinned_slabs;                   // the pinned allocations they are cut from
 
     // autotuner
     std::map<TuneKey, TuneVal> tune;
@@ -1020,20 +1021,24 @@ static size_t pinned_class(size_t bytes)
     return c;
 }
 
+// A pinned allocation costs tens of microseconds whatever its size, so
+// staging buffers of one class are cut from slabs of at least 4 MB.
 static void *pinned_take(mp_ctx *ctx, size_t bytes)
 {
     const size_t c = pinned_class(bytes);
     auto &fl = ctx->pinned_free[c];
-    if (!fl.empty()) {
-        void *p = fl.back();
-        fl.pop_back();
-        return p;
+    if (fl.empty()) {
+        const size_t slab = std::max(c, (size_t)4 << 20);
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, slab, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ctx->pinned_slabs.push_back(p);
+        for (size_t o = 0; o + c <= slab; o += c) fl.push_back((unsigned char *)p + o);
     }
-    void *p = nullptr;
-    if (cudaHostAlloc(&p, c, cudaHostAllocPortable) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
+    void *p = fl.back();
+    fl.pop_back();
     return p;
 }
 
@@ -1069,8 +1074,12 @@ static void finish_request(mp_ctx *ctx, Request &r, int32_t state, cudaStream_t 
     r.dict->refs.fetch_sub(1);
 }
 
-// Stage and launch one batch of admitted requests on stream `st`. Called by
-// the scheduler thread with ctx->mu held (dictionary statistics may be built).
+// Stage and launch one batch of admitted requests on stream `st`, from the
+// scheduler thread. The context lock (ctx->mu) is held only while the
+// requests' dictionary statistics and column groupings are resolved (they may
+// be built then) and while requests that run alone are enqueued; the batched
+// requests' copies and launches follow without it, so that submissions and
+// synchronous joins on the context do not wait for them.
 static int launch_batch(mp_ctx *ctx, Batch &bt)
 {
     cudaStream_t st = bt.stream;
@@ -1088,75 +1097,81 @@ static int launch_batch(mp_ctx *ctx, Batch &bt)
         int64_t *idx;
     };
     std::vector<Post> post;
-    for (auto &rp : bt.reqs) {
-        Request &r = *rp;
-        DictStats *s = nullptr;
-        int rc = get_stats(ctx, r.dict, r.m, &s);
-        if (rc) return rc;
-        const int64_t nq = r.n - r.m + 1;
-        unsigned char *p = (unsigned char *)r.dmem;
-        unsigned char *q = p;
-        p += align_up((size_t)r.n * dtype_size(r.dtype), 256);
-        double *dist = (double *)p;
-        int64_t *idx = (int64_t *)(p + nq * 8);
-        p += align_up(nq * 16, 256);
-        CUDA_TRY(cudaMemcpyAsync(q, r.h_stage, (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
-        const int kern = s->n_windows > 0 ? resolve_kernel(ctx, r.dtype, r.m, s, nq) : MP_KERNEL_PLAIN;
-        if (s->n_windows == 0 || r.dtype == MP_F64 || kern != MP_KERNEL_PLAIN || serve_alone(r)) {
-            // Requests that do not fit the batched FP32 plain kernel, and
-            // large ones, run alone on the batch's stream.
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (auto &rp : bt.reqs) {
+            Request &r = *rp;
+            DictStats *s = nullptr;
+            int rc = get_stats(ctx, r.dict, r.m, &s);
+            if (rc) return rc;
+            const int64_t nq = r.n - r.m + 1;
+            unsigned char *p = (unsigned char *)r.dmem;
+            unsigned char *q = p;
+            p += align_up((size_t)r.n * dtype_size(r.dtype), 256);
+            double *dist = (double *)p;
+            int64_t *idx = (int64_t *)(p + nq * 8);
+            p += align_up(nq * 16, 256);
+            const int kern = s->n_windows > 0 ? resolve_kernel(ctx, r.dtype, r.m, s, nq) : MP_KERNEL_PLAIN;
             if (s->n_windows == 0) {
                 r.no_windows = true;  // +inf / -1, written at completion
                 continue;
             }
-            rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p, kern,
-                             r.dtype == MP_F32 && serve_alone(r));
+            if (r.dtype == MP_F64 || kern != MP_KERNEL_PLAIN || serve_alone(r)) {
+                // Requests that do not fit the batched FP32 plain kernel, and
+                // large ones, run alone on the batch's stream.
+                CUDA_TRY(cudaMemcpyAsync(q, r.h_stage, (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
+                rc = join_device(ctx, r.dict, s, q, r.dtype, r.n, r.m, dist, idx, st, p, kern,
+                                 r.dtype == MP_F32 && serve_alone(r));
+                if (rc) return rc;
+                CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
+                continue;
+            }
+            const Geometry geo = serve_geometry(ctx, nq, s, r.dtype, r.m);
+            DictStats::Grouping *gr = nullptr;
+            rc = get_grouping(ctx, s, geo.n_groups, &gr);
             if (rc) return rc;
-            CUDA_TRY(cudaMemcpyAsync(r.h_stage, dist, (size_t)nq * 16, cudaMemcpyDeviceToHost, st));
-            continue;
+            JoinWs w = join_ws_layout(nq, r.dtype, geo.n_groups, 0);
+            // the layout must lie inside the request's memory (sized by request_bytes)
+            if ((size_t)(p - (unsigned char *)r.dmem) + w.total > r.bytes)
+                return fail(MP_E_INTERNAL, "serving workspace of %zu bytes exceeds the request's %zu", w.total,
+                            r.bytes);
+            PlainRequest pr{};  // seed_top null: the batched kernel computes its seeds
+            pr.a = (const float *)q;
+            pr.na = r.n;
+            pr.nq = nq;
+            pr.m = r.m;
+            pr.n_groups = geo.n_groups;
+            pr.rs_a = (float4 *)(p + w.off_rs);
+            pr.ms_a = (Split<float> *)(p + w.off_ms);
+            pr.b = (const float *)r.dict->d_samples;
+            pr.nb = r.dict->nb;
+            pr.rs_b = (const float4 *)s->rs;
+            pr.ms_b = (const Split<float> *)s->ms;
+            pr.spans = gr->spans;
+            pr.group_start = gr->group_start;
+            pr.part = (Partial<float> *)(p + w.off_part);
+            pr.near = near_rec(p, w, nq);
+            pr.ld_part = nq;
+            const int ridx = (int)preqs.size();
+            preqs.push_back(pr);
+            for (int64_t rb = 0; rb < geo.n_row_blocks; ++rb)
+                for (int g2 = 0; g2 < geo.n_groups; ++g2) items.push_back(BatchItem{ridx, g2, rb});
+            max_m = std::max(max_m, (int)r.m);
+            post.push_back(Post{&r, s, gr, geo.n_groups, p, (float *)q, dist, idx});
         }
-        const Geometry geo = serve_geometry(ctx, nq, s, r.dtype, r.m);
-        DictStats::Grouping *gr = nullptr;
-        rc = get_grouping(ctx, s, geo.n_groups, &gr);
-        if (rc) return rc;
-        JoinWs w = join_ws_layout(nq, r.dtype, geo.n_groups, 0);
-        // the layout must lie inside the request's memory (sized by request_bytes)
-        if ((size_t)(p - (unsigned char *)r.dmem) + w.total > r.bytes)
-            return fail(MP_E_INTERNAL, "serving workspace of %zu bytes exceeds the request's %zu", w.total, r.bytes);
-        const float *a = (const float *)q;
-        double *mean_a = (double *)(p + w.off_mean);
-        double *inv_a = (double *)(p + w.off_inv);
-        uint8_t *cf_a = (uint8_t *)(p + w.off_cflag);
-        float4 *rs_a = (float4 *)(p + w.off_rs);
-        Split<float> *ms_a = (Split<float> *)(p + w.off_ms);
-        Partial<float> *part = (Partial<float> *)(p + w.off_part);
-        const NearRec near = near_rec(p, w, nq);
-        CUDA_TRY(launch_window_stats<float>(a, r.n, r.m, mean_a, inv_a, cf_a, rs_a, ms_a, st));
-        PlainRequest pr{};  // seed_top null: the batched kernel computes its seeds
-        pr.a = a;
-        pr.na = r.n;
-        pr.nq = nq;
-        pr.m = r.m;
-        pr.n_groups = geo.n_groups;
-        pr.rs_a = rs_a;
-        pr.ms_a = ms_a;
-        pr.b = (const float *)r.dict->d_samples;
-        pr.nb = r.dict->nb;
-        pr.rs_b = (const float4 *)s->rs;
-        pr.ms_b = (const Split<float> *)s->ms;
-        pr.spans = gr->spans;
-        pr.group_start = gr->group_start;
-        pr.part = part;
-        pr.near = near;
-        pr.ld_part = nq;
-        const int ridx = (int)preqs.size();
-        preqs.push_back(pr);
-        for (int64_t rb = 0; rb < geo.n_row_blocks; ++rb)
-            for (int g = 0; g < geo.n_groups; ++g) items.push_back(BatchItem{ridx, g, rb});
-        max_m = std::max(max_m, (int)r.m);
-        post.push_back(Post{&r, s, gr, geo.n_groups, p, (float *)a, dist, idx});
     }
     if (!preqs.empty()) {
+        // each batched request's query and statistics (K1)
+        for (Post &ps : post) {
+            Request &r = *ps.r;
+            const int64_t nq = r.n - r.m + 1;
+            JoinWs w = join_ws_layout(nq, r.dtype, ps.n_groups, 0);
+            CUDA_TRY(cudaMemcpyAsync(ps.a, r.h_stage, (size_t)r.n * dtype_size(r.dtype), cudaMemcpyHostToDevice, st));
+            CUDA_TRY(launch_window_stats<float>(ps.a, r.n, r.m, (double *)(ps.base + w.off_mean),
+                                                (double *)(ps.base + w.off_inv), (uint8_t *)(ps.base + w.off_cflag),
+                                                (float4 *)(ps.base + w.off_rs), (Split<float> *)(ps.base + w.off_ms),
+                                                st));
+        }
         const size_t sz_req = align_up(preqs.size() * sizeof(PlainRequest), 256);
         const size_t sz_items = align_up(items.size() * sizeof(BatchItem), 256);
         if (cudaMallocFromPoolAsync(&bt.dmem, sz_req + sz_items + 256, ctx->pool, st) != cudaSuccess) {
@@ -1239,11 +1254,7 @@ static void scheduler_loop(mp_ctx *ctx)
             ctx->next_stream ^= 1;
             cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
             lk.unlock();
-            int rc;
-            {
-                std::lock_guard<std::mutex> g(ctx->mu);
-                rc = launch_batch(ctx, bt);
-            }
+            const int rc = launch_batch(ctx, bt);  // takes ctx->mu itself, for what needs it
             lk.lock();
             if (rc != MP_OK) {
                 cudaStreamSynchronize(bt.stream);
@@ -1356,8 +1367,7 @@ int mp_shutdown(mp_ctx *ctx)
         cudaEventDestroy(mk.t1);
     }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    for (auto &kv : ctx->pinned_free)
-        for (void *p : kv.second) cudaFreeHost(p);
+    for (void *p : ctx->pinned_slabs) cudaFreeHost(p);
     cudaStreamSynchronize(ctx->sstreams[0]);
     cudaStreamSynchronize(ctx->sstreams[1]);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
