@@ -140,3 +140,31 @@ def test_drain_returns_only_after_every_result_is_written(mp):
         mp.mp_dict_free(ctx, h)
     finally:
         mp.mp_shutdown(ctx)
+
+
+def test_sync_joins_while_batches_launch(mp):
+    """The scheduler enqueues a batch's copies and launches without the context lock, so synchronous joins
+    (which hold it) run while batches are being launched and executed. Both must give the results each gives
+    alone: the serving results equal the synchronous join of the same query, bit for bit."""
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN, max_inflight=16, max_batch=8)
+    try:
+        dicts, reqs = make_mix(n_req=48, seed=3)
+        handles = [mp.mp_dict_load(ctx, b, offs, [64, 128, 256]) for b, offs in dicts]
+        ref = [mp.mp_ab_join(ctx, handles[di], q, m) for di, q, m in reqs]
+        outs, tickets = [], []
+        for k, (di, q, m) in enumerate(reqs):
+            nq = len(q) - m + 1
+            od, oi = np.empty(nq), np.empty(nq, dtype=np.int64)
+            tickets.append(mp.mp_submit(ctx, handles[di], q, m, od, oi))
+            outs.append((od, oi))
+            if k % 4 == 0:  # a synchronous join between submissions, while earlier batches run
+                j = (k * 7) % len(reqs)
+                d2, i2 = mp.mp_ab_join(ctx, handles[reqs[j][0]], reqs[j][1], reqs[j][2])
+                assert np.array_equal(d2, ref[j][0]) and np.array_equal(i2, ref[j][1])
+        wait(mp, ctx, tickets)
+        for (od, oi), (rd, ri) in zip(outs, ref):
+            assert np.array_equal(od, rd) and np.array_equal(oi, ri)
+        for h in handles:
+            mp.mp_dict_free(ctx, h)
+    finally:
+        mp.mp_shutdown(ctx)
