@@ -368,7 +368,8 @@ int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t n, double t
  * form's column groups, the dictionary spans those groups cut (a span is one
  * segment's run of windows inside one group; the left seeds hold one value per
  * span and query window), the plain launches the query's windows take (row
- * chunks), whether the FP32 plain join takes its seeds from the tensor cores,
+ * chunks), whether the FP32 plain join takes its seeds from the tensor cores
+ * (joins of at least 2^31 pairs; smaller ones compute them in the plain kernel),
  * and the workspace bytes the context reserves for the join. It computes the
  * dictionary's statistics for m if they are not resident (that allocates) and
  * launches nothing else. Errors: MP_E_ARG as for mp_ab_join_device.
@@ -388,8 +389,8 @@ int mp_plan_join(mp_ctx *ctx, const mp_dict *dict, int32_t dtype, int64_t n, int
 #define MP_PHASE_STATS 0    /* window statistics of the query (K1) */
 #define MP_PHASE_JOIN 1     /* the join kernel: plain (K2) or tensor-core (K3) */
 #define MP_PHASE_FINALIZE 2 /* reduction, constant-window rule and exact distance of the pick (K4) */
-#define MP_PHASE_SEEDS 3    /* the plain join's top seeds on the tensor cores (K2s; FP32 plain joins) */
-#define MP_PHASE_LEFT_SEEDS 4 /* the plain join's left seeds on the tensor cores (K2l; FP32 plain joins) */
+#define MP_PHASE_SEEDS 3    /* the plain join's top seeds on the tensor cores (K2s; FP32 plain joins of >= 2^31 pairs) */
+#define MP_PHASE_LEFT_SEEDS 4 /* the plain join's left seeds on the tensor cores (K2l; the same joins) */
 #define MP_PHASE_COUNT 5
 
 /*
