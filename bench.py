@@ -42,11 +42,12 @@ L2_BYTES = 129 * 2**20
 PLAIN_OPS_PER_PAIR = 4
 # DRAM bytes of one k_plain launch on the full-size ECG workload (2^20 query
 # samples, 64 x 1024 dictionary, m = 256), from one single-pass ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum: 672.54 MB read (the top seeds
-# and the left seeds of the tensor cores) and 159.99 MB written (partial
+# dram__bytes_read.sum + dram__bytes_write.sum: 672.09 MB read (the top seeds
+# and the left seeds of the tensor cores) and 160.11 MB written (partial
 # results and near-tie record headers). Valid for this kernel build (seeds from
-# K2s and K2l, four-slot records, packed-multiply score) and workload only.
-PLAIN_DRAM_BYTES_FULL = 672.54e6 + 159.99e6
+# K2s and K2l, four-slot records, packed-multiply score fused with the
+# recurrence step) and workload only.
+PLAIN_DRAM_BYTES_FULL = 672.09e6 + 160.11e6
 LANES_PER_SM = 128  # FP32 lanes per SM
 # query windows per top seed of the FP32 plain kernel: one per warp, 32 lanes x 20 rows
 SEED_STRIDE = 32 * 20
