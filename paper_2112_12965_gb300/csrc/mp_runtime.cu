@@ -227,6 +227,26 @@ struct mp_ctx {
     // testing hooks (mp_test_hook)
     int64_t hook_fail_alloc = 0;  // serving allocations still to fail (under smu)
     long long hook_tc_wait = 0;   // tensor-core role-wait bound in clocks (0: the default)
+
+    // CUDA graphs of repeated small synchronous joins (under mu; see ab_join_host)
+    struct GraphKey {
+        const mp_dict *d;
+        int32_t dtype, m, kernel, corr;
+        int64_t n;
+        bool operator<(const GraphKey &o) const
+        {
+            return std::tie(d, dtype, m, kernel, corr, n) < std::tie(o.d, o.dtype, o.m, o.kernel, o.corr, o.n);
+        }
+    };
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        unsigned char *h_io = nullptr;  // pinned: the query, then dist, idx and the error word
+        size_t out_off = 0;
+        void *ws = nullptr;  // the workspace the graph was captured with
+        int calls = 0;
+        bool failed = false;  // capture did not work for this shape: never again
+    };
+    std::map<GraphKey, GraphEntry> graphs;
 };
 
 static void tune_load(mp_ctx *ctx, const char *path);
@@ -309,11 +329,35 @@ static int check_join_args(mp_ctx *ctx, const mp_dict *dict, const void *q, int3
     return MP_OK;
 }
 
+static void graph_entry_free(mp_ctx::GraphEntry &e)
+{
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.h_io) cudaFreeHost(e.h_io);
+    e.exec = nullptr;
+    e.h_io = nullptr;
+}
+
+// Drop the cached graphs (of one dictionary, or all when d is null): they hold
+// its device pointers, the workspace's, and the launch geometry of the kernel
+// setting and tuning they were captured under. Caller holds ctx->mu.
+static void graphs_clear(mp_ctx *ctx, const mp_dict *d = nullptr)
+{
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+        if (d == nullptr || it->first.d == d) {
+            graph_entry_free(it->second);
+            it = ctx->graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 // Grow the context workspace to at least `bytes` (synchronises the stream).
 static int ensure_ws(mp_ctx *ctx, size_t bytes)
 {
     if (ctx->ws_size >= bytes) return MP_OK;
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    graphs_clear(ctx);  // they point into the old workspace
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_size = 0;
@@ -1355,6 +1399,7 @@ int mp_shutdown(mp_ctx *ctx)
     if (ctx->worker.joinable()) ctx->worker.join();
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    graphs_clear(ctx);
     for (mp_dict *d : ctx->dicts) {
         for (auto &kv : d->stats) free_stats(kv.second.get());
         cudaFree(d->d_samples);
@@ -1385,6 +1430,7 @@ int mp_set_kernel(mp_ctx *ctx, int32_t kernel)
     if (kernel < MP_KERNEL_AUTO || kernel > MP_KERNEL_TC_BF16) return fail(MP_E_ARG, "unknown kernel %d", kernel);
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->kernel = kernel;
+    graphs_clear(ctx);
     return MP_OK;
 }
 
@@ -1443,6 +1489,7 @@ int mp_dict_free(mp_ctx *ctx, mp_dict *d)
     if (d->refs.load() > 0) return fail(MP_E_BUSY, "dictionary referenced by %d requests in flight", d->refs.load());
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    graphs_clear(ctx, d);
     for (auto &kv : d->stats) free_stats(kv.second.get());
     cudaFree(d->d_samples);
     ctx->dicts.erase(d);
@@ -1507,6 +1554,12 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
     return MP_OK;
 }
 
+// CUDA graphs of repeated synchronous joins: joins of at most this many query
+// windows (larger ones are bound by their kernels), at most this many cached
+// shapes per context (the cache is emptied when it is full).
+constexpr int64_t kGraphMaxWindows = (int64_t)1 << 18;
+constexpr size_t kGraphMaxEntries = 16;
+
 // The synchronous join with host buffers; corr: report rho = 1 - d^2 / (2m)
 // (-inf where the dictionary has no window) instead of d.
 static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
@@ -1540,10 +1593,79 @@ static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int
     void *dq = base;
     double *dd = (double *)(base + qbytes);
     int64_t *di = (int64_t *)(base + qbytes + obytes);
+    int32_t *d_err = (int32_t *)(base + qbytes + 2 * obytes);  // the tensor-core kernels' error word (join_device)
     cudaStream_t st = ctx->stream;
-    CUDA_TRY(cudaMemcpyAsync(dq, query, (size_t)n * dtype_size(dtype), cudaMemcpyHostToDevice, st));
-    rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes,
-                     resolve_kernel(ctx, dtype, m, s, nq), true, corr);
+    const int kern = resolve_kernel(ctx, dtype, m, s, nq);
+    const size_t es = dtype_size(dtype);
+
+    // A small join repeated with the same shape (a streaming append, a loop of
+    // short queries) is bound by its launches, not its kernels: from its second
+    // call on it runs as one CUDA graph captured from the same enqueue sequence
+    // (copy in from a pinned staging buffer, the join, copies out), replayed
+    // with one launch. Off while tracing (the phase events are not captured).
+    mp_ctx::GraphEntry *ge = nullptr;
+    if (!ctx->profiling && nq <= kGraphMaxWindows) {
+        const mp_ctx::GraphKey key{d, dtype, m, kern, corr ? 1 : 0, n};
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end() && ctx->graphs.size() >= kGraphMaxEntries) graphs_clear(ctx);
+        ge = &ctx->graphs[key];
+        if (ge->failed || (ge->exec == nullptr && ++ge->calls < 2)) ge = nullptr;  // first call: the normal path
+    }
+    if (ge && ge->exec && ge->ws != ctx->ws) {  // (graphs_clear runs when the workspace moves; kept as a guard)
+        graph_entry_free(*ge);
+    }
+    if (ge && ge->exec == nullptr) {
+        // capture this call's enqueue sequence
+        ge->out_off = align_up((size_t)n * es, 256);
+        const size_t io = ge->out_off + (size_t)nq * 16 + 16;
+        bool ok = cudaHostAlloc((void **)&ge->h_io, io, cudaHostAllocPortable) == cudaSuccess;
+        cudaGraph_t graph = nullptr;
+        if (ok) ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            bool enq = cudaMemcpyAsync(dq, ge->h_io, (size_t)n * es, cudaMemcpyHostToDevice, st) == cudaSuccess;
+            enq = enq && join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes, kern, true,
+                                     corr) == MP_OK;
+            unsigned char *ho = ge->h_io + ge->out_off;
+            enq = enq && cudaMemcpyAsync(ho, dd, (size_t)nq * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+            enq = enq && cudaMemcpyAsync(ho + (size_t)nq * 8, di, (size_t)nq * 8, cudaMemcpyDeviceToHost, st) ==
+                             cudaSuccess;
+            enq = enq && cudaMemcpyAsync(ho + (size_t)nq * 16, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ==
+                             cudaSuccess;
+            const bool ended = cudaStreamEndCapture(st, &graph) == cudaSuccess;
+            ok = enq && ended && graph != nullptr &&
+                 cudaGraphInstantiate(&ge->exec, graph, 0) == cudaSuccess;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            // this shape cannot be captured (something in its path synchronises
+            // or allocates): join it the normal way from now on
+            cudaGetLastError();
+            g_err.clear();
+            graph_entry_free(*ge);
+            ge->failed = true;
+            ge = nullptr;
+        } else {
+            ge->ws = ctx->ws;
+        }
+    }
+    if (ge) {
+        memcpy(ge->h_io, query, (size_t)n * es);
+        CUDA_TRY(cudaGraphLaunch(ge->exec, st));
+        // the NaN/Inf check runs while the device joins; nothing is copied out unless it passes
+        const bool finite = host_all_finite(query, dtype, n);
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (!finite) return fail(MP_E_ARG, "query has NaN or Inf samples");
+        const unsigned char *ho = ge->h_io + ge->out_off;
+        int32_t err = 0;
+        memcpy(&err, ho + (size_t)nq * 16, sizeof err);
+        if (err) return fail(MP_E_TIMEOUT, "a tensor-core wait timed out on the device; results are invalid");
+        memcpy(out_dist, ho, (size_t)nq * 8);
+        memcpy(out_idx, ho + (size_t)nq * 8, (size_t)nq * 8);
+        return MP_OK;
+    }
+
+    CUDA_TRY(cudaMemcpyAsync(dq, query, (size_t)n * es, cudaMemcpyHostToDevice, st));
+    rc = join_device(ctx, d, s, dq, dtype, n, m, dd, di, st, base + qbytes + 2 * obytes, kern, true, corr);
     if (rc) return rc;
     // The query is checked for NaN and Inf here, while the device joins it.
     // A join of such samples is wasted but harmless: the kernels take every
@@ -1555,9 +1677,8 @@ static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int
     }
     CUDA_TRY(cudaMemcpyAsync(out_dist, dd, nq * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(out_idx, di, nq * 8, cudaMemcpyDeviceToHost, st));
-    // the error word of the tensor-core kernels (zeroed by join_device)
     int32_t err = 0;
-    CUDA_TRY(cudaMemcpyAsync(&err, base + qbytes + 2 * obytes, sizeof err, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     if (err) return fail(MP_E_TIMEOUT, "a tensor-core wait timed out on the device; results are invalid");
     return MP_OK;
@@ -1738,6 +1859,7 @@ int mp_test_hook(mp_ctx *ctx, int32_t hook, int64_t value)
     } else if (hook == MP_HOOK_TC_WAIT) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->hook_tc_wait = (long long)value;
+        graphs_clear(ctx);  // a captured join carries the wait bound it was launched with
     } else {
         return fail(MP_E_ARG, "unknown hook %d", hook);
     }
@@ -2233,6 +2355,7 @@ extern "C" int mp_autotune(mp_ctx *ctx, const mp_dict *dict, int32_t m, int64_t 
     const TuneKey key{dtype, m, ilog2(s->n_windows), ilog2(nq)};
     const TuneVal val{best.kernel, best.groups, best_ms, tolerance};
     ctx->tune[key] = val;
+    graphs_clear(ctx);  // cached graphs carry the launch geometry of the old choice
     tune_save(ctx, key, val);
     if (kernel_out) *kernel_out = best.kernel;
     if (groups_out) *groups_out = best.groups;

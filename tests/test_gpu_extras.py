@@ -268,3 +268,43 @@ def test_learn_dictionary_matches_oracle(mp):
         assert bound2 <= bound + 1e-6 and chosen2 == chosen[: len(chosen2)]
     finally:
         mp.mp_shutdown(ctx)
+
+
+def test_repeated_small_joins_replay_a_graph(mp):
+    """A synchronous join repeated with the same shape runs, from its second call on, as one captured CUDA graph.
+    Every call gives the first call's results bit for bit; a query with NaN at that shape is still refused with
+    the outputs untouched; after its dictionary is freed, a new dictionary of the same shape gets its own
+    results (the cached graph held the old one's pointers)."""
+    w = synthetic.workload("ecg_1m_m256", scale=1 / 256)
+    ctx = mp.mp_init(device=0, kernel=mp.MP_KERNEL_PLAIN)
+    try:
+        d = mp.mp_dict_load(ctx, w.dict_samples, w.offsets, [w.m])
+        ref_d, ref_i = mp.mp_ab_join(ctx, d, w.query, w.m)
+        for _ in range(4):
+            dist, idx = mp.mp_ab_join(ctx, d, w.query, w.m)
+            assert np.array_equal(dist, ref_d) and np.array_equal(idx, ref_i)
+        # another query of the same length through the cached graph
+        q2 = synthetic.ecg_like(len(w.query), 77).astype(np.float32)
+        d2, i2 = mp.mp_ab_join(ctx, d, q2, w.m)
+        rows = np.arange(0, len(d2), 53)
+        parity.check(d2, i2, q2, w.dict_samples, w.offsets, w.m, rows=rows, atol=1e-4)
+        # NaN at a cached shape: refused, nothing written
+        bad = w.query.copy()
+        bad[len(bad) // 2] = np.nan
+        out_d = np.full(len(ref_d), -5.0)
+        out_i = np.full(len(ref_d), -9, dtype=np.int64)
+        with pytest.raises(mp.MPError) as e:
+            mp._check(mp.lib.mp_ab_join(ctx, d, mp._ptr(bad), mp.MP_F32, len(bad), w.m, mp._ptr(out_d),
+                                        mp._ptr(out_i)))
+        assert e.value.code == mp.MP_E_ARG
+        assert np.all(out_d == -5.0) and np.all(out_i == -9)
+        mp.mp_dict_free(ctx, d)
+        # a different dictionary of the same shape
+        b2 = synthetic.ecg_like(len(w.dict_samples), 78).astype(np.float32)
+        dn = mp.mp_dict_load(ctx, b2, w.offsets, [w.m])
+        for _ in range(3):
+            d3, i3 = mp.mp_ab_join(ctx, dn, w.query, w.m)
+        parity.check(d3, i3, w.query, b2, w.offsets, w.m, rows=rows, atol=1e-4)
+        mp.mp_dict_free(ctx, dn)
+    finally:
+        mp.mp_shutdown(ctx)
