@@ -143,6 +143,11 @@ int mp_dict_windows(const mp_dict *dict, int32_t m, int64_t *n_windows);
  *   out_dist  host, n - m + 1 doubles: P_hat
  *   out_idx   host, n - m + 1 int64: global window index g, or -1
  * Copies the query to the device, joins, copies the result back and returns.
+ * From the second call with the same shape (dictionary, dtype, n, m, form)
+ * on, a join of at most 2^18 query windows runs as one captured CUDA graph
+ * through pinned staging memory that the context keeps (up to 16 shapes; a
+ * shape's graph is dropped when its dictionary is freed or the kernel setting
+ * changes). The results are the same either way.
  */
 int mp_ab_join(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
                double *out_dist, int64_t *out_idx);
