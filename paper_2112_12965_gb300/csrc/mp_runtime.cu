@@ -943,7 +943,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             if (seeds) {
                 {
                     PhaseTimer t(ctx, MP_PHASE_SEEDS, st);
-                    int rc = tc_seeds(ctx->sm_count, &s->tc_pack, (const float *)d->d_samples, d->nb,
+                    int rc = tc_seeds(&s->tc_pack, (const float *)d->d_samples, d->nb,
                                       s->seg_spans.data(), (int32_t)s->seg_spans.size(), s->ms, a + r0, rows + m - 1,
                                       m, ms_a + r0, 32 * kPlainRowsPerLane, seed_top, sg.ld, err, st, fail);
                     if (rc) return rc;

@@ -1404,7 +1404,7 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
     return MP_OK;
 }
 
-int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
+int tc_seeds(void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
              const void *ms_b, const float *a, int64_t n, int32_t m, const void *ms_a, int32_t stride, float *seeds,
              int64_t ld, int32_t *err, cudaStream_t st, fail_fn fail)
 {
@@ -1420,7 +1420,6 @@ int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *
     // one tile per CTA: short CTAs of equal work, which the hardware scheduler
     // packs without a tail (groups of 2-3 tiles, about four waves, took 5 %
     // longer on the 2^20-window ECG join)
-    (void)sm_count;
     const int ng = std::max(1, n_tiles);
     TcPack *use = get_pack(pk, tiles, kTcMaxN, ng, st);
     if (!use) return fail(MP_E_NOMEM, "tensor-core tile table");

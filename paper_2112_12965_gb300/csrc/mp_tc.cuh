@@ -45,7 +45,7 @@ int tc_join(int sm_count, int variant, void **pack, const float *b, int64_t nb, 
 // products of a hi/lo split). Positions g of windows that cross a segment end
 // are not written; ld >= nb - m + 1. *err is set to 1 on a device-side
 // timeout. Any m >= 1.
-int tc_seeds(int sm_count, void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
+int tc_seeds(void **pack, const float *b, int64_t nb, const Span *seg_spans, int32_t n_seg,
              const void *ms_b, const float *a, int64_t n, int32_t m, const void *ms_a, int32_t stride, float *seeds,
              int64_t ld, int32_t *err, cudaStream_t st, fail_fn fail);
 
