@@ -575,10 +575,16 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                 }
             } else {
                 // the column groups: largest q, then lowest chunk start
+                // (the record headers are read in the same pass, so that the
+                // near-tie pass below re-reads only what this one brought into
+                // L1 and walks the headers again only for windows with records)
                 T q = T(-INFINITY);
+                int32_t hdr = 0;  // OR of the groups' header words: any slot in use, any overflow
+                const bool rec = p.near.rec != nullptr;
 #pragma unroll 4
                 for (int k = 0; k < p.n_groups; ++k) {
                     const Partial<T> v = p.part[(int64_t)k * p.nq + i];
+                    if (rec) hdr |= p.near.head(k, i)->g;
                     if (better(v.q, v.g, q, g)) {
                         q = v.q;
                         g = v.g;
@@ -600,21 +606,25 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                         const T lim = q - near_width(p, i, isa, ma);
                         s_lim[tid] = lim;
                         const int S = p.near.S;
+                        ovf = (hdr & kNearOverflow) != 0;
+#pragma unroll 4
                         for (int k = 0; k < p.n_groups; ++k) {
                             const Partial<T> v = p.part[(int64_t)k * p.nq + i];
                             if (v.g >= 0 && v.g != g && v.q >= lim) {
                                 if (nc < kFinMaxCand) s_cand[nc][tid] = v.g;
                                 ++nc;
                             }
-                            const NearSlot *h = p.near.head(k, i);
-                            const int32_t f = h->g;
-                            ovf |= (f & kNearOverflow) != 0;
-                            const int n = f & kNearCountMask;
-                            for (int u = 1; u <= n && u <= S; ++u) {
-                                const NearSlot sl = h[(int64_t)u * p.near.ld];
-                                if (sl.g != g && T(sl.q) >= lim) {
-                                    if (nc < kFinMaxCand) s_cand[nc][tid] = sl.g;
-                                    ++nc;
+                        }
+                        if (hdr & kNearCountMask) {  // some group recorded near ties for this window
+                            for (int k = 0; k < p.n_groups; ++k) {
+                                const NearSlot *h = p.near.head(k, i);
+                                const int n = h->g & kNearCountMask;
+                                for (int u = 1; u <= n && u <= S; ++u) {
+                                    const NearSlot sl = h[(int64_t)u * p.near.ld];
+                                    if (sl.g != g && T(sl.q) >= lim) {
+                                        if (nc < kFinMaxCand) s_cand[nc][tid] = sl.g;
+                                        ++nc;
+                                    }
                                 }
                             }
                         }
