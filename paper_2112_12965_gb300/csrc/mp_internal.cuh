@@ -34,6 +34,11 @@ struct Span {
 
 // Launch geometry of the plain diagonal kernel.
 constexpr int kPlainRowsPerLane = 20;  // query windows owned by one lane (k_plain, FP32)
+// Short FP32 joins with seeds computed in the kernel (at most kPlainShortMaxRows
+// query windows) use kPlainRowsShort rows per lane instead: a CTA's time is
+// then its warps' seed dot products, which fall with the rows per lane.
+constexpr int kPlainRowsShort = 4;
+constexpr int64_t kPlainShortMaxRows = 4096;
 constexpr int kServeRowsPerLane = 16;  // the same in the batched serving kernel (two CTAs per SM)
 constexpr int kPlainColBlock = 256;    // dictionary windows staged per block
 constexpr int kChunk = 16;             // windows per chunk of the lazy argmax
@@ -197,7 +202,8 @@ struct PlainLaunch {
     int32_t m;
     int32_t n_row_blocks;
     int32_t n_groups;      // column groups
-    int32_t warps;         // warps per CTA (rows per CTA = warps * 32 * kPlainRowsPerLane)
+    int32_t warps;         // warps per CTA (rows per CTA = warps * 32 * rows per lane)
+    int32_t rows_per_lane = 0;  // 0: plain_rows_per_lane<T>(); kPlainRowsShort: the short form (FP32, no K2s seeds)
     int64_t ld_part = 0;   // row stride of the partial results and near-tie records (0: nq)
     int64_t row0 = 0;      // self-join: series position of query window 0
     int32_t excl = 0;      // self-join: exclusion zone half-width (0: an AB-join)
@@ -222,7 +228,7 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
 template <typename T> constexpr int plain_rows_per_lane() { return sizeof(T) == 4 ? kPlainRowsPerLane : 8; }
 template <typename T> size_t plain_smem_bytes(int warps, int m, int rows_per_lane = plain_rows_per_lane<T>());
 // Resident CTAs per SM of the plain kernel for this shape (occupancy API).
-template <typename T> int plain_ctas_per_sm(int warps, int m);
+template <typename T> int plain_ctas_per_sm(int warps, int m, int rows_per_lane = plain_rows_per_lane<T>());
 
 // Serving: one request of a persistent batched launch (FP32 data). The layout
 // mirrors the kernel's parameter block.

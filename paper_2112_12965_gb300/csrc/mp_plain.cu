@@ -572,8 +572,9 @@ __device__ __forceinline__ void plain_item(const PlainParams<T> &p, int64_t rb, 
 // (shuffle, column terms, seed select) and the per-chunk argmax over more
 // pairs, and mean fewer top seeds; that gained more than the 16 warps of 16
 // rows per lane at 128 registers hid.
+// The short form (kPlainRowsShort rows per lane) takes 6 CTAs per SM.
 template <typename T, int kRows, bool kSeeds, bool kNear, bool kSelf = false>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_plain(PlainParams<T> p)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (kRows <= kPlainRowsShort ? 6 : 3) : 1) k_plain(PlainParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     plain_item<T, kRows, kSeeds, kNear, true, kSelf>(p, blockIdx.x / p.n_groups, blockIdx.x % p.n_groups, smem_raw);
@@ -644,8 +645,10 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
     p.ld_part = L.ld_part > 0 ? L.ld_part : L.nq;
     p.row0 = L.row0;
     p.excl = L.excl;
-    const size_t smem = plain_smem_bytes<T>(L.warps, L.m);
     constexpr int R = plain_rows_per_lane<T>();
+    const bool short_form = sizeof(T) == 4 && L.rows_per_lane == kPlainRowsShort;
+    if (L.rows_per_lane != 0 && L.rows_per_lane != R && !short_form) return cudaErrorInvalidValue;
+    const size_t smem = plain_smem_bytes<T>(L.warps, L.m, short_form ? kPlainRowsShort : R);
     const int64_t grid = (int64_t)L.n_row_blocks * L.n_groups;
     auto launch = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -661,6 +664,12 @@ cudaError_t launch_plain(const PlainLaunch &L, const T *a, int64_t na, const vec
         if (near.rec != nullptr && (near.ld != p.ld_part || near.S < 1 || near.S > kNearMaxSlots))
             return cudaErrorInvalidValue;
         if ((seed_top == nullptr) != (left == nullptr)) return cudaErrorInvalidValue;  // both seeds, or neither
+        if (short_form) {
+            // short join: seeds computed in the kernel, 4 rows per lane
+            if (seed_top != nullptr || L.excl > 0) return cudaErrorInvalidValue;
+            return near.rec != nullptr ? launch(k_plain<T, kPlainRowsShort, false, true>)
+                                       : launch(k_plain<T, kPlainRowsShort, false, false>);
+        }
         if (L.excl > 0) {
             // self-join (dictionary learning): tensor-core seeds and near-tie records
             if (seed_top == nullptr || near.rec == nullptr) return cudaErrorInvalidValue;
@@ -686,14 +695,18 @@ cudaError_t launch_plain_batched(const PlainRequest *reqs_dev, const BatchItem *
 }
 
 template <typename T>
-int plain_ctas_per_sm(int warps, int m)
+int plain_ctas_per_sm(int warps, int m, int rows_per_lane)
 {
     int n = 0;
-    const size_t smem = plain_smem_bytes<T>(warps, m);
     constexpr int R = plain_rows_per_lane<T>();
+    const bool short_form = sizeof(T) == 4 && rows_per_lane == kPlainRowsShort;
+    const size_t smem = plain_smem_bytes<T>(warps, m, short_form ? kPlainRowsShort : R);
     cudaError_t e;
     if constexpr (sizeof(T) == 8)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plain<T, R, false, false>, 32 * warps, smem);
+    else if (short_form)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plain<T, kPlainRowsShort, false, true>, 32 * warps,
+                                                          smem);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plain<T, R, true, true>, 32 * warps, smem);
     if (e != cudaSuccess) {
@@ -703,8 +716,8 @@ int plain_ctas_per_sm(int warps, int m)
     return n > 0 ? n : 1;
 }
 
-template int plain_ctas_per_sm<float>(int, int);
-template int plain_ctas_per_sm<double>(int, int);
+template int plain_ctas_per_sm<float>(int, int, int);
+template int plain_ctas_per_sm<double>(int, int, int);
 template size_t plain_smem_bytes<float>(int, int, int);
 template size_t plain_smem_bytes<double>(int, int, int);
 template cudaError_t launch_plain<float>(const PlainLaunch &, const float *, int64_t, const float4 *,

@@ -579,19 +579,20 @@ static FinalizeParams<T> fin_params(mp_ctx *ctx, int64_t nq, int32_t m, int n_gr
 // Launch geometry of the plain kernel for nq rows and W columns.
 struct Geometry {
     int warps, n_row_blocks, n_groups;
+    int rows_per_lane = 0;  // the geometry's rows per lane
 };
 
 // Resident CTAs per SM of the plain kernel, from the occupancy API, cached per
-// (dtype, warps, m): the serving scheduler sizes every request with it.
-static int plain_ctas_cached(bool f64, int warps, int m)
+// (dtype, warps, m, rows per lane): the serving scheduler sizes every request with it.
+static int plain_ctas_cached(bool f64, int warps, int m, int rows_per_lane)
 {
     static std::mutex mu;
-    static std::map<std::tuple<bool, int, int>, int> cache;
+    static std::map<std::tuple<bool, int, int, int>, int> cache;
     std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_tuple(f64, warps, m);
+    const auto key = std::make_tuple(f64, warps, m, rows_per_lane);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    const int n = f64 ? plain_ctas_per_sm<double>(warps, m) : plain_ctas_per_sm<float>(warps, m);
+    const int n = f64 ? plain_ctas_per_sm<double>(warps, m) : plain_ctas_per_sm<float>(warps, m, rows_per_lane);
     cache[key] = n;
     return n;
 }
@@ -623,7 +624,7 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
     const double span_cost = tc_seeds ? 8.0 : (double)std::max(m, 16) / 4.0;
     const int64_t min_cols = batched ? (int64_t)(4.0 * (fixed + span_cost)) : 16;
     const int64_t max_g = std::max<int64_t>(1, std::min<int64_t>(1024, W / min_cols));
-    const int per_sm = m > 0 ? plain_ctas_cached(dtype == MP_F64, g.warps, m) : 4;
+    const int per_sm = m > 0 ? plain_ctas_cached(dtype == MP_F64, g.warps, m, rows_per_lane) : 4;
     const double slots = (double)ctx->sm_count * per_sm;
     const double nseg = std::max<double>(1.0, (double)n_segments);
     auto cost = [&](int64_t k) {
@@ -643,6 +644,7 @@ static Geometry plain_geometry(const mp_ctx *ctx, int64_t nq, int64_t W, int row
     // at most one group per chunk's worth of windows (T >= kChunk: no group
     // without a chunk), also for a grouping taken from the tuning cache
     g.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(ng, W / kChunk));
+    g.rows_per_lane = rows_per_lane;
     return g;
 }
 
@@ -775,11 +777,14 @@ static int64_t grouping_spans(const DictStats *s, int n_groups)
 // to 4 (16-byte rows).
 static int64_t left_ld_for(int64_t crow) { return (crow + 3) & ~(int64_t)3; }
 
-// Geometry of the plain join of nq query windows (row chunks included).
+// Geometry of the plain join of nq query windows (row chunks included); seeds:
+// the tensor-core seeds are taken (join_device's decision). A short FP32 join
+// computing its seeds in the kernel takes the short form's rows per lane.
 static Geometry join_plain_geometry(const mp_ctx *ctx, const mp_dict *d, const DictStats *s, int32_t dtype,
                                     int64_t nq, int32_t m, bool seeds)
 {
-    const int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
+    int rpl = dtype == MP_F64 ? plain_rows_per_lane<double>() : plain_rows_per_lane<float>();
+    if (dtype == MP_F32 && !seeds && nq <= kPlainShortMaxRows) rpl = kPlainRowsShort;
     return plain_geometry(ctx, plain_chunk_rows(d, dtype, nq, m, seeds), std::max<int64_t>(1, s->n_windows), rpl,
                           dtype, m, (int64_t)s->seg_spans.size(), seeds && dtype == MP_F32);
 }
@@ -850,6 +855,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
     L.n_row_blocks = geo.n_row_blocks;
     L.n_groups = geo.n_groups;
     L.warps = geo.warps;
+    L.rows_per_lane = dtype == MP_F32 ? geo.rows_per_lane : 0;
     if (dtype == MP_F64) {
         const double *a = (const double *)dq;
         dvec4 *rs_a = (dvec4 *)(base + w.off_rs);
@@ -955,7 +961,7 @@ static int join_device(mp_ctx *ctx, mp_dict *d, DictStats *s, const void *dq, in
             }
             PhaseTimer t(ctx, MP_PHASE_JOIN, st);
             PlainLaunch Lc = L;
-            const int64_t rows_cta = (int64_t)geo.warps * 32 * kPlainRowsPerLane;
+            const int64_t rows_cta = (int64_t)geo.warps * 32 * geo.rows_per_lane;
             Lc.nq = rows;
             Lc.n_row_blocks = (int32_t)((rows + rows_cta - 1) / rows_cta);
             Lc.ld_part = nq;
