@@ -22,12 +22,14 @@
 // down, so each lane shifts its registers by one row and takes the top one
 // from the lane above with a warp shuffle. The first row of each warp has no
 // row above inside the warp: its value comes from a "top seed", the centred
-// covariance of that row with the column's window. FP32 joins take the top
-// seeds from the tensor-core kernel K2s (a dense product, computed once per
-// join); the other forms compute them here as direct dot products per column
-// block. At the first column of each span (a run of columns inside one
-// segment) every row gets a "left seed": from the tensor-core kernel K2l for
-// FP32 joins, else a direct dot product. Dictionary
+// covariance of that row with the column's window. FP32 joins of at least
+// 2^31 pairs take the top seeds from the tensor-core kernel K2s (a dense
+// product, computed once per join); the other joins compute them here as
+// direct dot products per column block. At the first column of each span (a
+// run of columns inside one segment) every row gets a "left seed": from the
+// tensor-core kernel K2l for those FP32 joins, else a direct dot product.
+// Short FP32 joins run with fewer rows per lane (kPlainRowsShort), which
+// shortens each warp's seed dot products. Dictionary
 // windows never cross a segment (Def. 8) because spans never do. Each lane
 // keeps, for its rows, the running maximum of q per 16-column chunk and the
 // chunk that raised it (plus near-tie records); the partial result per (row,
