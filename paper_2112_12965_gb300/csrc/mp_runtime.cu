@@ -1711,6 +1711,10 @@ int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int3
     if (m < kMinM || m > kMaxM || n < m) return fail(MP_E_ARG, "bad n/m (m in [%d, %d], n >= m)", kMinM, kMaxM);
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    // the context's stream is shared with the synchronous joins (which may be
+    // capturing it into a graph): enqueue on it under the context lock
+    std::unique_lock<std::mutex> lk(ctx->mu, std::defer_lock);
+    if (st == ctx->stream) lk.lock();
     if (dtype == MP_F64)
         CUDA_TRY(launch_window_stats<double>((const double *)d_x, n, m, d_mean, d_invstd, d_const, nullptr, nullptr,
                                              st));
