@@ -281,10 +281,9 @@ int mp_ab_join_device(mp_ctx *ctx, const mp_dict *dict, const void *d_query, int
  * The caller passes the device query and outputs as for mp_ab_join_device.
  *
  * The first call on a device resolves the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. Every call shares the array and it keeps the
- * last call's contents; everything a call reads from it is written by that
- * call first. Calls whose work overlaps on the GPU (other streams, other
+ * (cudaGetSymbolAddress, with that device current). Every call shares the
+ * array and it keeps the last call's contents; everything a call reads from
+ * it is written by that call first. Calls whose work overlaps on the GPU (other streams, other
  * contexts, other threads) race on the array and give undefined results:
  * serialise them.
  */
