@@ -32,6 +32,9 @@
  *     Algorithm 2.
  *   - Query and dictionary must have the same sample type. F32 data is joined
  *     in FP32 arithmetic with FP64 window statistics; F64 data in FP64.
+ *     Products of centred F32 samples must stay within float32 range: with
+ *     sample spreads near 1e17 or more they can overflow, and the distances
+ *     and indices of the windows concerned are then unspecified.
  *
  * Errors: every call returns MP_OK (0) or a negative MP_E_* code and, on
  * error, leaves a message for mp_last_error(). Invalid arguments (null

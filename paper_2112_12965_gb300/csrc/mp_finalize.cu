@@ -158,7 +158,11 @@ __device__ __forceinline__ void rescore_chunk(const T *__restrict__ pa, const T 
         const Split<T> mb = ms_b[gc];
         const T cov = acc[0] - T(m) * ma.lo * ((mb.hi - sb) + mb.lo);
         sc = cov * r.z;
+        ok = sc == sc;  // NaN (products that overflowed): not a candidate
+        sc = ok ? sc : T(-INFINITY);
     }
+    // with NaN out, better() is a total order and every lane ends with the
+    // same (score, window)
     int32_t gw = ok ? (int32_t)gc : -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -502,7 +506,12 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const Cand
     const bool ok = gc < npos_b && (excl == 0 || (gc - i >= excl || i - gc >= excl)) && ct.w == T(0);
     // sum_k (a - sa)(b - sb) = cov + m (mean_a - sa)(mean_b - sb)
     T sc = ok ? (acc[0] - T(m) * da * ((ct.mhi - sb) + ct.mlo)) * ct.z : T(-INFINITY);
-    int32_t gw = ok ? (int32_t)gc : -1;
+    // a NaN score (products that overflowed) is no candidate: better() is then
+    // a total order, so every lane ends with the same (score, window) and the
+    // branches on it below stay warp-uniform
+    const bool num = sc == sc;
+    sc = num ? sc : T(-INFINITY);
+    int32_t gw = ok && num ? (int32_t)gc : -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         if (o == 8) continue;  // the same candidate
@@ -645,10 +654,16 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
             const Split<T> ma{s_mhi[t], s_mlo[t]};
             CandTerms<T> ct = load_cand(p.rs_b, p.ms_b, p.npos_b, g0, lane);
             const T *ai = p.a + iw;
+            // 16 * KPL values over 32 lanes; qidx(lane + 32 u) = lane + 33 u
+            if (m == 16 * KPL) {
 #pragma unroll
-            for (int u = 0; u < KPL / 2; ++u) {  // 16 * KPL values over 32 lanes; qidx(lane + 32 u) = lane + 33 u
-                const int e = lane + 32 * u;
-                qa[lane + 33 * u] = e < m ? ai[e] - ma.hi : T(0);
+                for (int u = 0; u < KPL / 2; ++u) qa[lane + 33 * u] = ai[lane + 32 * u] - ma.hi;
+            } else {
+#pragma unroll
+                for (int u = 0; u < KPL / 2; ++u) {
+                    const int e = lane + 32 * u;
+                    qa[lane + 33 * u] = e < m ? ai[e] - ma.hi : T(0);
+                }
             }
             T sb = stage_chunk<T, KPL>(p.b, p.nb, p.ms_b, g0, lane, wb);
             T sc;
@@ -738,13 +753,39 @@ __global__ void __launch_bounds__(32 * fin_warps<T>(), sizeof(T) == 8 ? 4 : 8)
                 // taken before its scaling, so no large term is rounded (db, the
                 // mean difference within the chunk, can be far above the spread)
                 const T *wo = wb + qidx(gw - win + lane);  // value gw - win + lane + 32 u sits at wo[33 u]
-                T acc = T(0);
+                // the scalar form: (qa - lo) is_a - (wb - db) is_b, squared and summed
+                auto dist2 = [&]() {
+                    T a = T(0);
 #pragma unroll
-                for (int u = 0; u < KPL / 2; ++u) {
-                    if (lane + 32 * u < m) {
-                        const T dd = fma(qa[lane + 33 * u] - ma.lo, is_a, -((wo[33 * u] - db) * is_b));
-                        acc = fma(dd, dd, acc);
+                    for (int u = 0; u < KPL / 2; ++u) {
+                        if (lane + 32 * u < m) {
+                            const T dd = fma(qa[lane + 33 * u] - ma.lo, is_a, -((wo[33 * u] - db) * is_b));
+                            a = fma(dd, dd, a);
+                        }
                     }
+                    return a;
+                };
+                T acc;
+                if constexpr (sizeof(T) == 4) {
+                    if (m == 16 * KPL) {
+                        // every value in use: the same operations on pairs of them
+                        const float2 nlo = make_float2(-ma.lo, -ma.lo), ia = make_float2(is_a, is_a);
+                        const float2 ndb = make_float2(-db, -db), nib = make_float2(-is_b, -is_b);
+                        float2 a2 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < KPL / 2; u += 2) {
+                            const float2 q2 = make_float2(qa[lane + 33 * u], qa[lane + 33 * (u + 1)]);
+                            const float2 w2 = make_float2(wo[33 * u], wo[33 * (u + 1)]);
+                            const float2 wz = __fmul2_rn(__fadd2_rn(w2, ndb), nib);
+                            const float2 dd = __ffma2_rn(__fadd2_rn(q2, nlo), ia, wz);
+                            a2 = __ffma2_rn(dd, dd, a2);
+                        }
+                        acc = a2.x + a2.y;
+                    } else {
+                        acc = dist2();
+                    }
+                } else {
+                    acc = dist2();
                 }
 #pragma unroll
                 for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);

@@ -1676,7 +1676,9 @@ static int ab_join_host(mp_ctx *ctx, const mp_dict *dict, const void *query, int
     // The query is checked for NaN and Inf here, while the device joins it.
     // A join of such samples is wasted but harmless: the kernels take every
     // index from the launch geometry or from valid chunks, never from sample
-    // values. Nothing is copied out unless the check passes.
+    // values, and the finalisation's re-scoring drops NaN scores before its
+    // lane reductions, so its branches stay warp-uniform. Nothing is copied
+    // out unless the check passes.
     if (!host_all_finite(query, dtype, n)) {
         cudaStreamSynchronize(st);
         return fail(MP_E_ARG, "query has NaN or Inf samples");
