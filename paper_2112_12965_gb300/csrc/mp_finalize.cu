@@ -60,6 +60,35 @@ __device__ __forceinline__ bool better(T q1, int32_t g1, T q2, int32_t g2)
     return g1 >= 0 && (g2 < 0 || q1 > q2 || (q1 == q2 && g1 < g2));
 }
 
+// The warp's best (score, window) under better(), in every lane: the largest
+// score, then the lowest window; (-inf, -1) when no lane has a candidate. The
+// scores hold no NaN. FP32 scores take two reductions (redux.sync) of a key
+// whose unsigned order is the floats' order, with 0 for no candidate; FP64
+// scores a butterfly of shuffles.
+template <typename T>
+__device__ __forceinline__ void warp_best(T &sc, int32_t &gw)
+{
+    if constexpr (sizeof(T) == 4) {
+        const uint32_t u = __float_as_uint(sc);
+        const uint32_t key = gw < 0 ? 0u : ((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+        const int32_t gmin = __reduce_min_sync(0xffffffffu, key == kmax ? gw : 0x7fffffff);
+        const uint32_t ub = (kmax & 0x80000000u) ? (kmax & 0x7fffffffu) : ~kmax;
+        sc = kmax == 0u ? T(-INFINITY) : __uint_as_float(ub);
+        gw = kmax == 0u ? -1 : gmin;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+            const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
+            if (better(s2, g2, sc, gw)) {
+                sc = s2;
+                gw = g2;
+            }
+        }
+    }
+}
+
 // Self-join helpers (excl > 0; the dictionary is the one series, so every
 // position 0 .. npos_b - 1 is a valid window): the lowest constant window and
 // the lowest window outside query window i's exclusion zone, -1 if none.
@@ -164,15 +193,7 @@ __device__ __forceinline__ void rescore_chunk(const T *__restrict__ pa, const T 
     // with NaN out, better() is a total order and every lane ends with the
     // same (score, window)
     int32_t gw = ok ? (int32_t)gc : -1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
-        const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
-        if (better(s2, g2, sc, gw)) {
-            sc = s2;
-            gw = g2;
-        }
-    }
+    warp_best(sc, gw);
     sc_out = sc;
     g_out = gw;
 }
@@ -512,16 +533,7 @@ __device__ __forceinline__ void rescore_staged(int64_t npos_b, int m, const Cand
     const bool num = sc == sc;
     sc = num ? sc : T(-INFINITY);
     int32_t gw = ok && num ? (int32_t)gc : -1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        if (o == 8) continue;  // the same candidate
-        const T s2 = __shfl_xor_sync(0xffffffffu, sc, o);
-        const int32_t g2 = __shfl_xor_sync(0xffffffffu, gw, o);
-        if (better(s2, g2, sc, gw)) {
-            sc = s2;
-            gw = g2;
-        }
-    }
+    warp_best(sc, gw);
     sc_out = sc;
     g_out = gw;
 }
