@@ -194,12 +194,17 @@ struct mp_ctx {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
-    cudaStream_t sstreams[2] = {nullptr, nullptr};
+    // serving streams: 0 and 1 (the device's greatest priority) take the
+    // batches of small requests, 2 and 3 (its least) the large requests that
+    // run alone, so that a small request's kernels are dispatched as soon as
+    // SMs free up instead of after every CTA of a large join in flight
+    static constexpr int kServeStreams = 4;
+    cudaStream_t sstreams[kServeStreams] = {nullptr, nullptr, nullptr, nullptr};
     // the serving path's stream-ordered allocations; it keeps freed memory
     // for reuse (bounded by the admission budget) instead of returning it to
     // the driver at every synchronisation
     cudaMemPool_t pool = nullptr;
-    int next_stream = 0;
+    int next_small = 0, next_large = 0;
 
     // tracing
     bool profiling = false;
@@ -1039,11 +1044,12 @@ static Geometry serve_geometry(const mp_ctx *ctx, int64_t nq, const DictStats *s
 // Device bytes of a request: its query, its outputs (dist, idx) and a
 // workspace for either way it may run (alone through join_device, or in the
 // batched kernel).
-// Query windows from which a serving request of FP32 data runs alone on the
-// batch's stream, with the headline join's kernels (tensor-core top seeds and
-// the packed plain kernel at three CTAs per SM), rather than as items of the
-// batched kernel (its own scalar seeds, two CTAs per SM). Such a request fills
-// the GPU by itself: 2^16 windows are 26 row blocks in each column group.
+// Query windows from which a serving request of FP32 data runs alone, in a
+// batch of such requests on a low-priority stream, with the headline join's
+// kernels (tensor-core top seeds and the packed plain kernel at three CTAs per
+// SM), rather than as items of the batched kernel (its own scalar seeds, two
+// CTAs per SM). Such a request fills the GPU by itself: 2^16 windows are 26
+// row blocks in each column group.
 constexpr int64_t kServeAloneRows = (int64_t)1 << 16;
 static bool serve_alone(const Request &r) { return r.n - r.m + 1 >= kServeAloneRows; }
 
@@ -1277,14 +1283,19 @@ static void scheduler_loop(mp_ctx *ctx)
             ctx->inflight.erase(ctx->inflight.begin() + k);
         }
         if (ctx->stop && ctx->pending.empty() && ctx->inflight.empty()) break;
-        // 2. admit: FIFO, while a slot and the memory budget allow
-        Batch bt;
-        bt.stream = ctx->sstreams[ctx->next_stream];
-        while (!ctx->pending.empty() && (int)bt.reqs.size() < ctx->cfg.max_batch &&
+        // 2. admit: FIFO, while a slot and the memory budget allow. Large
+        // requests (they run alone, see serve_alone) go to a batch of their
+        // own on a low-priority stream, the rest to a batch on a high-priority
+        // stream.
+        Batch bs, bl;
+        bs.stream = ctx->sstreams[ctx->next_small];
+        bl.stream = ctx->sstreams[2 + ctx->next_large];
+        while (!ctx->pending.empty() && (int)(bs.reqs.size() + bl.reqs.size()) < ctx->cfg.max_batch &&
                ctx->n_inflight_reqs < ctx->cfg.max_inflight) {
             std::shared_ptr<Request> r = ctx->pending.front();
             if (ctx->mem_used + r->bytes > ctx->mem_budget && ctx->n_inflight_reqs > 0) break;
             ctx->pending.pop_front();
+            Batch &bt = serve_alone(*r) ? bl : bs;
             const bool injected = ctx->hook_fail_alloc > 0;  // a testing hook: fail as if out of memory
             if (injected) --ctx->hook_fail_alloc;
             if (injected || cudaMallocFromPoolAsync(&r->dmem, r->bytes, ctx->pool, bt.stream) != cudaSuccess) {
@@ -1300,8 +1311,12 @@ static void scheduler_loop(mp_ctx *ctx)
             ctx->n_inflight_reqs += 1;
             bt.reqs.push_back(r);
         }
-        if (!bt.reqs.empty()) {
-            ctx->next_stream ^= 1;
+        bool launched = false;
+        for (Batch *b : {&bs, &bl}) {  // the small requests' work is enqueued first
+            if (b->reqs.empty()) continue;
+            launched = true;
+            (b == &bs ? ctx->next_small : ctx->next_large) ^= 1;
+            Batch &bt = *b;
             cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
             lk.unlock();
             const int rc = launch_batch(ctx, bt);  // takes ctx->mu itself, for what needs it
@@ -1314,8 +1329,8 @@ static void scheduler_loop(mp_ctx *ctx)
             } else {
                 ctx->inflight.push_back(std::move(bt));
             }
-            continue;
         }
+        if (launched) continue;
         // 3. nothing to admit: wait for a submission or poll the device
         if (ctx->inflight.empty())
             ctx->scv.wait(lk, [&] { return ctx->stop || !ctx->pending.empty(); });
@@ -1368,8 +1383,12 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
     c->kernel = cfg.kernel;
     CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg.device));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[0], cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamCreateWithFlags(&c->sstreams[1], cudaStreamNonBlocking));
+    {
+        int least = 0, greatest = 0;
+        CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int k = 0; k < mp_ctx::kServeStreams; ++k)
+            CUDA_TRY(cudaStreamCreateWithPriority(&c->sstreams[k], cudaStreamNonBlocking, k < 2 ? greatest : least));
+    }
     {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -1379,6 +1398,12 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
         CUDA_TRY(cudaMemPoolCreate(&c->pool, &props));
         uint64_t keep = UINT64_MAX;
         CUDA_TRY(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        // reuse only memory whose free has completed: the pool may otherwise
+        // make an allocation's stream wait for the stream that freed the
+        // memory, and a small request on a high-priority stream would then
+        // wait for a large join on a low-priority one
+        int no = 0;
+        CUDA_TRY(cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no));
     }
     CUDA_TRY(cudaMalloc(&c->d_counters, kFinCounters * sizeof(unsigned long long)));
     CUDA_TRY(cudaMemset(c->d_counters, 0, kFinCounters * sizeof(unsigned long long)));
@@ -1419,12 +1444,10 @@ int mp_shutdown(mp_ctx *ctx)
     }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void *p : ctx->pinned_slabs) cudaFreeHost(p);
-    cudaStreamSynchronize(ctx->sstreams[0]);
-    cudaStreamSynchronize(ctx->sstreams[1]);
+    for (cudaStream_t st : ctx->sstreams) cudaStreamSynchronize(st);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     cudaStreamDestroy(ctx->stream);
-    cudaStreamDestroy(ctx->sstreams[0]);
-    cudaStreamDestroy(ctx->sstreams[1]);
+    for (cudaStream_t st : ctx->sstreams) cudaStreamDestroy(st);
     delete ctx;
     return MP_OK;
 }
