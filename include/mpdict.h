@@ -305,9 +305,13 @@ int mp_window_stats(mp_ctx *ctx, const void *d_x, int32_t dtype, int64_t n, int3
  * Serving: submit a join request. The query is copied before the call
  * returns. out_dist / out_idx are host buffers (n - m + 1 entries) that must
  * stay valid until mp_poll reports MP_DONE or MP_FAILED. Requests are admitted
- * to the device as slots and memory free up and are batched with other
- * requests into persistent launches; each result is identical to what
- * mp_ab_join returns for the same inputs. *ticket receives the request id.
+ * to the device in arrival order as slots and memory free up. Float32
+ * requests of at least 2^16 query windows run alone with the synchronous
+ * join's kernels, on streams of the device's least priority; the others are
+ * batched into persistent launches on streams of its greatest priority, so a
+ * short request is not held up by a long one already running. Each result is
+ * identical to what mp_ab_join returns for the same inputs. *ticket receives
+ * the request id.
  */
 int mp_submit(mp_ctx *ctx, const mp_dict *dict, const void *query, int32_t dtype, int64_t n, int32_t m,
               double *out_dist, int64_t *out_idx, uint64_t *ticket);
