@@ -204,6 +204,11 @@ struct mp_ctx {
     // for reuse (bounded by the admission budget) instead of returning it to
     // the driver at every synchronisation
     cudaMemPool_t pool = nullptr;
+    // requests' memory is returned to the pool on this stream, which has no
+    // other work: the host frees only memory whose work it has seen complete,
+    // so each free completes at once and the pool can reuse the memory for the
+    // next admission on any stream, without making that stream wait
+    cudaStream_t fstream = nullptr;
     int next_small = 0, next_large = 0;
 
     // tracing
@@ -1103,7 +1108,9 @@ static void pinned_give(mp_ctx *ctx, void *p, size_t bytes)
     if (p) ctx->pinned_free[pinned_class(bytes)].push_back(p);
 }
 
-static void finish_request(mp_ctx *ctx, Request &r, int32_t state, cudaStream_t st)
+// The request's work has completed (or failed) on the device: the caller
+// has seen its batch's event or synchronised its stream.
+static void finish_request(mp_ctx *ctx, Request &r, int32_t state)
 {
     if (state == MP_DONE) {
         // the result waits in the pinned staging buffer: dist then idx
@@ -1123,7 +1130,7 @@ static void finish_request(mp_ctx *ctx, Request &r, int32_t state, cudaStream_t 
     r.t_done = now_s();
     r.state = state;
     // stream-ordered free: no device-wide synchronisation in the serving loop
-    if (r.dmem) cudaFreeAsync(r.dmem, st);
+    if (r.dmem) cudaFreeAsync(r.dmem, ctx->fstream);
     r.dmem = nullptr;
     ctx->mem_used -= r.bytes;
     ctx->n_inflight_reqs -= 1;
@@ -1277,9 +1284,9 @@ static void scheduler_loop(mp_ctx *ctx)
             }
             const int32_t state = (q == cudaSuccess) ? MP_DONE : MP_FAILED;
             if (q != cudaSuccess) cudaGetLastError();
-            for (auto &r : bt.reqs) finish_request(ctx, *r, state, bt.stream);
+            for (auto &r : bt.reqs) finish_request(ctx, *r, state);
             cudaEventDestroy(bt.done);
-            if (bt.dmem) cudaFreeAsync(bt.dmem, bt.stream);
+            if (bt.dmem) cudaFreeAsync(bt.dmem, ctx->fstream);
             ctx->inflight.erase(ctx->inflight.begin() + k);
         }
         if (ctx->stop && ctx->pending.empty() && ctx->inflight.empty()) break;
@@ -1323,9 +1330,9 @@ static void scheduler_loop(mp_ctx *ctx)
             lk.lock();
             if (rc != MP_OK) {
                 cudaStreamSynchronize(bt.stream);
-                for (auto &r : bt.reqs) finish_request(ctx, *r, MP_FAILED, bt.stream);
+                for (auto &r : bt.reqs) finish_request(ctx, *r, MP_FAILED);
                 cudaEventDestroy(bt.done);
-                if (bt.dmem) cudaFreeAsync(bt.dmem, bt.stream);
+                if (bt.dmem) cudaFreeAsync(bt.dmem, ctx->fstream);
             } else {
                 ctx->inflight.push_back(std::move(bt));
             }
@@ -1389,6 +1396,7 @@ int mp_init(mp_ctx **out, const mp_config *cfg_in)
         for (int k = 0; k < mp_ctx::kServeStreams; ++k)
             CUDA_TRY(cudaStreamCreateWithPriority(&c->sstreams[k], cudaStreamNonBlocking, k < 2 ? greatest : least));
     }
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking));
     {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -1445,9 +1453,11 @@ int mp_shutdown(mp_ctx *ctx)
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void *p : ctx->pinned_slabs) cudaFreeHost(p);
     for (cudaStream_t st : ctx->sstreams) cudaStreamSynchronize(st);
+    cudaStreamSynchronize(ctx->fstream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     cudaStreamDestroy(ctx->stream);
     for (cudaStream_t st : ctx->sstreams) cudaStreamDestroy(st);
+    cudaStreamDestroy(ctx->fstream);
     delete ctx;
     return MP_OK;
 }
