@@ -69,7 +69,7 @@ template <typename T>
 __device__ __forceinline__ void warp_best(T &sc, int32_t &gw)
 {
     if constexpr (sizeof(T) == 4) {
-        const uint32_t u = __float_as_uint(sc);
+        const uint32_t u = __float_as_uint(sc + 0.0f);  // -0 becomes +0: the keys then order as better() does
         const uint32_t key = gw < 0 ? 0u : ((u & 0x80000000u) ? ~u : (u | 0x80000000u));
         const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
         const int32_t gmin = __reduce_min_sync(0xffffffffu, key == kmax ? gw : 0x7fffffff);
