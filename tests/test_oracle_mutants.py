@@ -22,6 +22,11 @@ MUTANTS = {
     "no_elementwise_min": ("if (seg_best < best)", "if (1)"),
     "constant_never_detected": ("            return 0;\n    return 1;", "            return 0;\n    return 0;"),
     "constant_mixed_zero": ("    if (cx || cy)\n        return sqrt((double)m);", "    if (cx || cy)\n        return 0.0;"),
+    "constant_both_sqrt_m": ("    if (cx && cy)\n        return 0.0;", "    if (cx && cy)\n        return sqrt((double)m);"),
+    "mean_over_m_minus_1": ("const double mu = s / (double)m;", "const double mu = s / (double)(m - 1);"),
+    "squared_distance": ("    return sqrt(acc);\n}", "    return acc;\n}"),
+    "exclusion_asymmetric": ("if (g > i - excl && g < i + excl)", "if (g > i - excl && g <= i + excl)"),
+    "exclusion_ignored": ("if (g > i - excl && g < i + excl)", "if (0)"),
 }
 
 
