@@ -1,7 +1,8 @@
 """Plant plausible mistakes in copies of the oracle and check that the pins catch each.
 
 Each mutant is a textual edit of ``oracle/mp_oracle.c`` compiled into a temporary
-directory; the committed oracle is never modified. A mutant "survives" if every
+directory, or of ``oracle/__init__.py`` run as a fresh module; the committed
+oracle is never modified. A mutant "survives" if every
 pin still passes -- that would mean the pins cannot tell it from the real oracle.
 """
 import os
@@ -48,3 +49,51 @@ def test_mutant_is_caught(name, tmp_path):
         except AssertionError:
             caught.append(pin.__name__)
     assert caught, f"mutant {name} passed every pin"
+
+
+# Mistakes planted in the Python half of the oracle (Algorithm 1 and the
+# correlation output). The edited source runs as a fresh module with the
+# original's file path (so that it finds the compiled C part), and the pins
+# use it in place of the committed module for the duration of the test.
+PY_MUTANTS = {
+    "learn_takes_argmax": ("j = int(np.argmin(np.where(finite, Pp, np.inf)))",
+                           "j = int(np.argmax(np.where(finite, Pp, -np.inf)))"),
+    "learn_excludes_one_window": ("excluded[max(0, j - half):min(nq, j + half)] = True", "excluded[j] = True"),
+    "learn_folds_with_max": ("S = Sp if it == 0 else np.minimum(S, Sp)", "S = Sp if it == 0 else np.maximum(S, Sp)"),
+    "learn_context_doubled": ("pad = int(np.floor((k_context - 1.0) * m / 2.0))",
+                              "pad = int(np.floor((k_context - 1.0) * m))"),
+    "corr_scale_m": ("1.0 - d * d / (2.0 * m)", "1.0 - d * d / m"),
+}
+
+
+def _pins_failed_by(src, monkeypatch):
+    import types
+
+    import numpy as np
+
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = oracle.__file__
+    exec(compile(src, oracle.__file__, "exec"), mod.__dict__)
+    monkeypatch.setattr(pins, "oracle", mod)
+    lib = oracle.load()
+    caught = []
+    for pin in pins.ALL_PINS:
+        try:
+            with np.errstate(all="ignore"):
+                pin(lib)
+        except AssertionError:
+            caught.append(pin.__name__)
+    return caught
+
+
+def test_python_oracle_loaded_this_way_passes_every_pin(monkeypatch):
+    # the control for the mutants below: the unedited source, run as a fresh module
+    assert _pins_failed_by(open(oracle.__file__).read(), monkeypatch) == []
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_mutant_is_caught(name, monkeypatch):
+    old, new = PY_MUTANTS[name]
+    src = open(oracle.__file__).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found"
+    assert _pins_failed_by(src.replace(old, new), monkeypatch), f"mutant {name} passed every pin"
