@@ -191,21 +191,24 @@ def run_reference(args, rank, world):
     oracle.build()
     nq = w.n_rows
     rows_per_step = 256
+    # every core of the host, whatever OMP_NUM_THREADS says (torchrun sets it to 1)
+    cores = os.cpu_count() or 1
     times = []
     for s in range(args.warmup + args.steps):
         rows = (np.arange(rows_per_step) * (nq // rows_per_step) + s) % nq
         t0 = time.perf_counter()
-        oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows)
+        oracle.ab_join(w.query, w.dict_samples, w.offsets, w.m, rows=rows, nthreads=cores)
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
     pairs = rows_per_step * w.n_dict_windows
     ms = 1e3 * float(np.mean(times))
     value = pairs / (ms / 1e3)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": 0,
+    # n_gpus is the launch's N, as in the other arm's line (this arm computes on the host's cores only)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "sample_rows_per_step": rows_per_step},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": f"{rows_per_step} query windows per step, all {w.n_dict_windows} "
                                        "dictionary windows"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
