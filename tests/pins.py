@@ -17,7 +17,9 @@ The independent references used here:
     Algorithm 2);
   * the paper's guarantees for a dictionary cut from T_B: Lemma 1
     (P_hat >= P) and Lemma 2 (P_hat - P <= e_max, e_max by its definition in
-    Sec. 3.3).
+    Sec. 3.3);
+  * what the paper's illustration of Algorithm 2 (Sec. 3.2) shows: repeated
+    patterns found exactly, the unique pattern as the profile's maximum.
 """
 from __future__ import annotations
 
@@ -343,6 +345,44 @@ def pin_learn_dictionary(lib):
     assert d.max() <= target + 1e-9
 
 
+def pin_dictionary_figure(lib):
+    """The illustration of Algorithm 2 (Sec. 3.2, the figure of the dictionary join).
+
+    T_A repeats three patterns and holds one unique pattern; the dictionary has
+    one element per repeated pattern. Expected from the method: every window
+    lying inside an occurrence of a repeated pattern is found exactly (distance
+    0, at the same offset of the element holding that pattern); P_hat is the
+    element-wise minimum of the per-element profiles P_AD[i]; and P_hat's
+    largest value falls on a window that overlaps the unique pattern. The
+    repeated patterns are smooth (random-walk bridges) and the unique one is
+    white noise, so its windows correlate with no dictionary window.
+    """
+    rng = np.random.default_rng(31)
+    L, m = 96, 16
+    ramp = np.linspace(0.0, 1.0, L)
+    pats = []
+    for _ in range(3):
+        w = rng.standard_normal(L).cumsum()
+        pats.append(w - w[0] - ramp * (w[-1] - w[0]))  # starts and ends at 0
+    unique = rng.standard_normal(L)
+    order = [0, 1, 2, 1, 0, 2, None, 2, 0, 1]
+    q = np.concatenate([unique if k is None else pats[k] for k in order])
+    b = np.concatenate(pats)
+    offs = np.array([0, L, 2 * L, 3 * L], dtype=np.int64)
+    d, i, _ = oracle.ab_join(q, b, offs, m, lib=lib)
+    for n, k in enumerate(order):
+        if k is None:
+            continue
+        for o in range(L - m + 1):
+            r = n * L + o
+            assert d[r] == 0.0 and i[r] == offs[k] + o, (n, k, o, d[r], i[r])
+    per = [oracle.ab_join(q, pats[k], np.array([0, L]), m, lib=lib)[0] for k in range(3)]
+    assert np.array_equal(np.minimum(np.minimum(per[0], per[1]), per[2]), d)
+    a0 = order.index(None) * L
+    top = int(np.argmax(d))
+    assert a0 - m + 1 <= top <= a0 + L - 1, (top, a0)
+
+
 ALL_PINS = (
     pin_brute_force,
     pin_closed_forms,
@@ -355,4 +395,5 @@ ALL_PINS = (
     pin_correlation_output,
     pin_self_join,
     pin_learn_dictionary,
+    pin_dictionary_figure,
 )
